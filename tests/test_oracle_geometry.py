@@ -1,0 +1,71 @@
+"""Pins for the oracle's patch maps and surface measure."""
+import numpy as np
+import pytest
+
+from oracle import geometry, galerkin
+
+
+def test_sphere_faces_lie_on_sphere_and_cover_it(sphere):
+    rng = np.random.default_rng(11)
+    u, v = rng.random(500), rng.random(500)
+    for face in sphere:
+        F, Fu, Fv = face.eval(u, v)
+        np.testing.assert_allclose(np.linalg.norm(F, axis=1), 1.0, atol=1e-15)
+        # outward orientation: (Fu x Fv) . F > 0
+        assert np.all(np.sum(np.cross(Fu, Fv) * F, axis=1) > 0)
+    # every direction is hit by exactly the face of its largest |coordinate|
+    d = rng.normal(size=(200, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    for x in d:
+        ax = np.argmax(np.abs(x))
+        face = 2 * ax + (0 if x[ax] > 0 else 1)
+        n, t1, t2 = (np.array(t) for t in geometry.SPHERE_FACE_FRAMES[face])
+        c = x / abs(x[ax])
+        uu, vv = (c @ t1 + 1) / 2, (c @ t2 + 1) / 2
+        F, _, _ = sphere[face].eval([uu], [vv])
+        np.testing.assert_allclose(F[0], x, atol=1e-14)
+
+
+def test_derivatives_against_finite_differences(sphere):
+    u = np.array([0.1, 0.37, 0.5, 0.93])
+    v = np.array([0.8, 0.21, 0.5, 0.07])
+    h = 1e-6
+    cyl = geometry.quarter_cylinder(1.3, 0.7)
+    for patch in list(sphere) + [cyl]:
+        _, Fu, Fv = patch.eval(u, v)
+        fdu = (patch.eval(u + h, v)[0] - patch.eval(u - h, v)[0]) / (2 * h)
+        fdv = (patch.eval(u, v + h)[0] - patch.eval(u, v - h)[0]) / (2 * h)
+        np.testing.assert_allclose(Fu, fdu, atol=1e-8)
+        np.testing.assert_allclose(Fv, fdv, atol=1e-8)
+
+
+def test_sphere_area_by_gauss(sphere):
+    # sum over elements of the 8 x 8 Gauss rule of k -> 4 pi (Sec. 3.2, surface measure)
+    disc = galerkin.Discretisation(sphere, 0, 3, galerkin.LaplaceKernel())
+    area = disc.rhs(lambda F: np.ones(len(F))).sum()
+    assert abs(area - 4 * np.pi) < 1e-12
+
+
+def test_sphere_area_radius_and_center():
+    pats = geometry.unit_sphere(radius=1.7, center=(0.3, -1.0, 2.0))
+    disc = galerkin.Discretisation(pats, 0, 2, galerkin.LaplaceKernel())
+    area = disc.rhs(lambda F: np.ones(len(F))).sum()
+    assert abs(area - 4 * np.pi * 1.7 ** 2) < 1e-9
+
+
+def test_nurbs_quarter_cylinder_exact():
+    # rational quadratic arcs are exact circles: |(x, y)| = R, area = (pi/2) R H
+    R, H = 1.3, 0.7
+    cyl = geometry.quarter_cylinder(R, H)
+    u = np.linspace(0, 1, 37)
+    F, Fu, Fv = cyl.eval(u, np.full_like(u, 0.4))
+    np.testing.assert_allclose(np.hypot(F[:, 0], F[:, 1]), R, atol=1e-15)
+    np.testing.assert_allclose(F[:, 2], 0.4 * H, atol=1e-15)
+    disc = galerkin.Discretisation([cyl], 0, 2, galerkin.LaplaceKernel())
+    area = disc.rhs(lambda F: np.ones(len(F))).sum()
+    assert abs(area - 0.5 * np.pi * R * H) < 1e-12
+
+
+def test_nurbs_rejects_nonpositive_weights():
+    with pytest.raises(ValueError):
+        geometry.NurbsPatch(1, 1, [0, 0, 1, 1], [0, 0, 1, 1], np.zeros((2, 2, 3)), np.array([[1, 1], [0, 1.0]]))

@@ -1,0 +1,54 @@
+"""Pins for the oracle's right-hand side, solvers and potential evaluation."""
+import numpy as np
+import pytest
+
+from conftest import seeded_ball_points
+from oracle import galerkin, solve
+
+X0 = np.array([0.9, 0.9, 0.9])
+
+
+def _point_source(F, src):
+    return 1.0 / (4 * np.pi * np.linalg.norm(F - src, axis=1))
+
+
+def test_interior_laplace_point_source(laplace_p2m2):
+    # Harmonic data from a source outside the unit ball: u = g inside (Eq. repform).
+    disc, A = laplace_p2m2
+    b = disc.rhs(lambda F: _point_source(F, X0))[:, 0]
+    w = solve.dense_solve(A, b)
+    P = seeded_ball_points(100, 0.5, 170809162)
+    u = solve.potential(disc, w, P)[:, 0]
+    assert np.max(np.abs(u - _point_source(P, X0))) < 2e-6
+
+
+def test_cg_matches_direct(laplace_p2m2):
+    disc, A = laplace_p2m2
+    b = disc.rhs(lambda F: _point_source(F, X0))[:, 0]
+    w0 = solve.dense_solve(A, b)
+    w, it = solve.cg(lambda v: A @ v, b, rtol=1e-10, diag=np.diag(A).copy())
+    assert it < 200
+    assert np.linalg.norm(b - A @ w) <= 1e-10 * np.linalg.norm(b) * 1.0001
+    assert np.linalg.norm(w - w0) < 1e-6 * np.linalg.norm(w0)
+
+
+def test_exterior_helmholtz_point_source(sphere):
+    k = 2.0
+    v = np.array([0.1, 0.2, -0.1])
+    disc = galerkin.Discretisation(sphere, 2, 1, galerkin.HelmholtzKernel(k))
+    A = disc.dense_matrix()
+
+    def g(F):
+        r = np.linalg.norm(F - v, axis=1)
+        return np.exp(1j * k * r) / (4 * np.pi * r)
+
+    b = disc.rhs(g)[:, 0]
+    w = solve.dense_solve(A, b)
+    rng = np.random.default_rng(5)
+    d = rng.normal(size=(40, 3))
+    P = 3.0 * d / np.linalg.norm(d, axis=1)[:, None]
+    u = solve.potential(disc, w, P)[:, 0]
+    assert np.max(np.abs(u - g(P))) < 2e-4 * np.max(np.abs(g(P)))
+    wg, it = solve.gmres(lambda x: A @ x, b, rtol=1e-10, restart=30, diag=np.diag(A).copy())
+    assert np.linalg.norm(b - A @ wg) <= 1.0001e-10 * np.linalg.norm(b)
+    assert np.linalg.norm(wg - w) < 1e-7 * np.linalg.norm(w)
