@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the FMM-compressed single-layer operator on one GB300.
+
+Workload: interior Laplace problem on the unit sphere (6 cube-sphere patches),
+degree-3 B-splines on level 5 (7,350 dofs, 98,304 superspace dofs), Chebyshev
+6 x 6 points per cluster, admissibility eta = 1.6, one right-hand side.
+
+A step is one application of y = T A T^T x (lift, upward pass, coupling,
+downward pass, near field, restriction), the operator applied in every Krylov
+iteration.  `value` is dofs x right-hand sides per second of the FP64 operator
+over all ranks (each rank runs an independent replica; no data-path
+collective).  Beside it: the FP32 operator (error against FP64 stated), the
+FP64 CG solve and the mixed-precision iterative-refinement solve to true
+relative residual 1e-8, the end-to-end time through ibem_matvec_host with host
+buffers, the roofline of the dominant kernel and the oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "laplace-sphere-p3-m5-q6-eta1.6", "p": 3, "m": 5, "q_cheb": 6, "eta": 1.6,
+            "nrhs": 1, "geometry": "unit sphere, 6 cube-sphere patches", "kernel": "laplace"}
+METRIC = "FMM single-layer matvec DOF*RHS/s (FP64), GMRES/CG solve time to 1e-8 vs plain FP64 GPU"
+UNIT = "DOF*RHS/s"
+SEED = 170809162
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "coupling64_kernel_laplace_sphere_p3_m5.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- oracle timing
+def oracle_worker(nrows):
+    """Runs in a child process with one BLAS thread: times nrows rows of the
+    oracle's FMM-mode operator on the benchmark workload; prints one JSON line."""
+    import numpy as np
+    from oracle import fmm, galerkin, geometry
+    t0 = time.perf_counter()
+    disc = galerkin.Discretisation(geometry.unit_sphere(), WORKLOAD["p"], WORKLOAD["m"], galerkin.LaplaceKernel())
+    op = fmm.FMMOperator(disc, WORKLOAD["q_cheb"], WORKLOAD["eta"])
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(SEED)
+    x = rng.normal(size=disc.mesh.n_dofs)
+    rows = rng.choice(disc.mesh.n_dofs, size=nrows, replace=False)
+    times = []
+    for r in rows:
+        op._near_blocks.clear()
+        t = time.perf_counter()
+        op.rows([int(r)], x)
+        times.append(time.perf_counter() - t)
+    print(json.dumps({"rows": int(nrows), "seconds": sum(times), "setup_s": setup}))
+
+
+def run_oracle(nrows):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(nrows)],
+                         capture_output=True, text=True, env=env, cwd=ROOT)
+    if out.returncode != 0:
+        raise RuntimeError("oracle worker failed: " + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, rank):
+    """The oracle, as it stands, on the host cores: each step computes 2 rows."""
+    if rank != 0:
+        return
+    per_step = 2
+    import numpy as np
+    from oracle import fmm, galerkin, geometry
+    disc = galerkin.Discretisation(geometry.unit_sphere(), WORKLOAD["p"], WORKLOAD["m"], galerkin.LaplaceKernel())
+    op = fmm.FMMOperator(disc, WORKLOAD["q_cheb"], WORKLOAD["eta"])
+    rng = np.random.default_rng(SEED)
+    x = rng.normal(size=disc.mesh.n_dofs)
+
+    def step():
+        op._near_blocks.clear()
+        op.rows([int(r) for r in rng.choice(disc.mesh.n_dofs, per_step, replace=False)], x)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    value = args.steps * per_step / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, l2="n/a (host)"), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d rows of the FMM-mode operator per step (one BLAS thread)" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary."""
+    try:
+        for line in open(PROFILE_SUMMARY):
+            if line.startswith("traffic_bytes_per_launch:"):
+                return float(line.split(":")[1])
+    except OSError:
+        pass
+    return None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    except OSError:
+        return 6800.0, 2070.0, "fallback"
+
+
+# ---------------------------------------------------------------- our arm
+def ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1708_09162_gb300 import build
+    build.build()
+    from paper_1708_09162_gb300 import ibem
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    def barrier():
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.Stream()
+    prm = ibem.make_params(WORKLOAD["p"], WORKLOAD["m"], q_cheb=WORKLOAD["q_cheb"], eta=WORKLOAD["eta"])
+    t0 = time.perf_counter()
+    h = ibem.ibem_create(ibem.sphere_patches(), prm, stream)
+    t_create = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ibem.ibem_assemble(h)
+    t_assemble = time.perf_counter() - t0
+    info = ibem.ibem_get_info(h)
+    N, R = info.ndof, WORKLOAD["nrhs"]
+    rng = np.random.default_rng(SEED + rank)
+    x = torch.from_numpy(rng.normal(size=(R, N))).cuda()
+    y = torch.empty_like(x)
+    y32 = torch.empty_like(x)
+
+    def run(steps, precision):
+        with torch.cuda.stream(stream):
+            for _ in range(steps):
+                ibem.ibem_matvec(h, x, y if precision == 0 else y32, R, precision)
+
+    # ---- FP64 operator: the headline ----
+    run(args.warmup, 0)
+    ibem.ibem_profile_read(h)
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ibem.ibem_profile_enable(h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    run(args.steps, 0)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = ibem.ibem_profile_read(h)
+    ibem.ibem_profile_enable(h, False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * R / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (coupling, stored FP64 K) ----
+    phase_ms = {k: v / args.steps for k, v in prof["ms"].items()}
+    q2 = WORKLOAD["q_cheb"] ** 2
+    kpt = (q2 + 3) // 4
+    coup_ms = phase_ms["coupling"]
+    flops = 2.0 * q2 * q2 * info.n_far * R
+    kbytes = info.n_far * kpt * 4 * q2 * 8 + 2 * info.n_clusters * q2 * R * 8
+    hbm_gbs, sm_max, peak_src = _peaks()
+    fp64_peak_tflops = 152 * 2 * 2 * sm_max * 1e6 / 1e12       # 2 FP64 FMA / clock / SM
+    alu_frac = (flops / (coup_ms * 1e-3) / 1e12) / fp64_peak_tflops
+    hbm_frac = (kbytes / (coup_ms * 1e-3) / 1e9) / hbm_gbs
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": flops / (coup_ms * 1e-3) / 1e12, "peak": fp64_peak_tflops,
+                "unit": "TFLOP/s", "frac": alu_frac,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x %.0f MHz (%s clock)" % (sm_max, peak_src)}
+    else:
+        roof = {"bound": "hbm", "achieved": kbytes / (coup_ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": hbm_frac, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % peak_src}
+    roof.update({"kernel": "coupling64_kernel", "ms_per_launch": coup_ms, "traffic": _profile_traffic(),
+                 "algorithmic_bytes": kbytes, "algorithmic_flops": flops,
+                 "hbm_frac_of_measured": hbm_frac, "fp64_alu_frac": alu_frac})
+
+    # ---- FP32 operator ----
+    run(args.warmup, 1)
+    barrier()
+    ev0.record(stream)
+    run(args.steps, 1)
+    ev1.record(stream)
+    barrier()
+    ms32 = ev0.elapsed_time(ev1) / args.steps
+    err32 = float((y32 - y).abs().max() / y.abs().max())
+
+    # ---- end to end through the host-buffer entry point ----
+    xh = torch.empty((R, N), dtype=torch.float64, pin_memory=True)
+    xh.copy_(x.cpu())
+    yh = torch.empty((R, N), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(3, args.steps // 10)
+    for _ in range(3):
+        ibem.ibem_matvec_host(h, xh, yh, R)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        ibem.ibem_matvec_host(h, xh, yh, R)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_s], device="cuda")
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    # ---- solves to 1e-8 ----
+    solve = None
+    if not args.no_solve:
+        x0 = np.array([0.9, 0.9, 0.9])
+        qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+        ibem.ibem_quad_points(h, qp)
+        torch.cuda.synchronize()
+        gq = torch.from_numpy(1.0 / (4 * np.pi * np.linalg.norm(qp.cpu().numpy() - x0, axis=1))).cuda()
+        b = torch.empty(N, dtype=torch.float64, device="cuda")
+        ibem.ibem_rhs(h, gq, 1, b)
+        w = torch.empty_like(b)
+        s64 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precision=0)
+        s32 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precision=1)
+        solve = {"rtol": 1e-8, "precond": "jacobi",
+                 "fp64": {"seconds": s64.seconds, "iterations": s64.iterations, "rel_residual": s64.rel_residual},
+                 "mixed": {"seconds": s32.seconds, "iterations": s32.iterations, "outer": s32.outer,
+                           "rel_residual": s32.rel_residual},
+                 "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}
+
+    # ---- oracle on the host cores (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = run_oracle(3)
+        cpu = {"value": o["rows"] / o["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d rows of the oracle's FMM-mode operator on the same workload (near blocks, "
+                         "far couplings and the moment pass included; tree setup %.1f s excluded)"
+                         % (o["rows"], o["setup_s"])}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(WORKLOAD, ndof=N, ndof_super=info.ndof_super, n_near=info.n_near, n_far=info.n_far,
+                           parallelism="replicas" if world > 1 else "single",
+                           l2="inputs larger than L2: %.1f GB of stored operator streamed per step"
+                              % ((info.bytes_near + info.bytes_far) / 1e9)),
+            "phase_ms": phase_ms,
+            "fp32": {"value": world * N * R / (ms32 * 1e-3), "ms_per_step": ms32, "rel_err_vs_fp64": err32},
+            "assemble_s": t_assemble, "create_s": t_create,
+            "solve": solve,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
+                    "d2h_bytes_per_step": N * R * 8},
+            "gpu_launches": prof["launches"],
+            "clocks": clk}
+    ibem.ibem_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * ibem.h - C ABI of the GB300 isogeometric single-layer BEM library (libibem).
+ *
+ * The library applies the Galerkin single-layer operator of the Laplace or
+ * Helmholtz equation on a multipatch surface, discretised by patchwise tensor
+ * B-splines S_{p,m} and compressed by an interpolation-based fast multipole
+ * method (Doelz, Harbrecht, Kurz, Schoeps, Wolf, "A fast isogeometric BEM for
+ * the three dimensional Laplace- and Helmholtz problems", Secs. 2-4).
+ *
+ * Conventions (all entry points):
+ *  - Ownership: the caller owns every pointer it passes; the library owns only
+ *    the device buffers inside a handle and frees them in ibem_destroy.
+ *  - Pointers named *_dev are device pointers (CUDA global memory of the device
+ *    that was current at ibem_create); every other pointer is host memory.
+ *  - Vectors with several right-hand sides are stored right-hand side by
+ *    right-hand side: element (r, i) of an [nrhs][n] array is at r * n + i.
+ *  - Complex values (Helmholtz) are interleaved (re, im) doubles, so a complex
+ *    [nrhs][n] array holds 2 * nrhs * n doubles.
+ *  - Dof order of S_{p,m}: dof(patch, j_u, j_v) = patch * n1^2 + j_v * n1 + j_u
+ *    with n1 = 2^m + p (j_u counts B-splines along the first parameter).
+ *  - All device work is enqueued on the stream given to ibem_create.  Calls
+ *    return after enqueueing, except where a comment says they synchronise.
+ *  - Errors are returned as ibem_status; no C++ exception crosses the ABI.  The
+ *    text of the last error of a handle is available from ibem_last_error.
+ *  - A handle must not be used from two host threads at the same time.
+ */
+#ifndef IBEM_H
+#define IBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibem_handle ibem_handle;
+
+typedef enum {
+    IBEM_OK = 0,
+    IBEM_ERR_ARG = 1,        /* invalid argument (null pointer, size, option) */
+    IBEM_ERR_GEOMETRY = 2,   /* invalid patch description or mesh topology   */
+    IBEM_ERR_CUDA = 3,       /* a CUDA call failed; see ibem_last_error       */
+    IBEM_ERR_OOM = 4,        /* device or host allocation failed             */
+    IBEM_ERR_NOCONV = 5,     /* iterative solver reached maxit                */
+    IBEM_ERR_BREAKDOWN = 6,  /* solver breakdown (p^T A p <= 0, NaN, ...)     */
+    IBEM_ERR_STATE = 7       /* call out of order (e.g. matvec before assemble) */
+} ibem_status;
+
+/* Patch kinds (Sec. 2.2, Eq. def::geom). */
+enum {
+    IBEM_PATCH_NURBS = 0,       /* rational tensor B-spline map F : [0,1]^2 -> R^3 */
+    IBEM_PATCH_SPHERE_FACE = 1  /* analytic cube-sphere face: F = c0 + R c/|c|,
+                                   c = n + (2u-1) t1 + (2v-1) t2 for face 0..5
+                                   (+x, -x, +y, -y, +z, -z)                      */
+};
+
+/* One patch, host memory; copied by ibem_create.
+ * NURBS: degrees deg_u, deg_v >= 1 (<= 7), ncp_u x ncp_v control points,
+ * knots_u has ncp_u + deg_u + 1 entries (open, non-decreasing, from 0 to 1),
+ * ctrl_xyz is [ncp_v][ncp_u][3], weights is [ncp_v][ncp_u] and positive.
+ * SPHERE_FACE: face in 0..5, radius > 0, center. */
+typedef struct {
+    int kind;
+    int deg_u, deg_v, ncp_u, ncp_v;
+    const double *knots_u, *knots_v, *ctrl_xyz, *weights;
+    int face;
+    double radius;
+    double center[3];
+} ibem_patch;
+
+enum { IBEM_LAPLACE = 0, IBEM_HELMHOLTZ = 1 };   /* Eqs. fundament1 / fundament2 */
+
+/* Arithmetic of the operator application. */
+enum {
+    IBEM_FP64 = 0,  /* stored FP64 near blocks and coupling matrices           */
+    IBEM_FP32 = 1   /* FP32 near blocks, coupling generated on the fly in FP32,
+                       FP32 accumulation (inputs and outputs stay FP64)        */
+};
+
+enum { IBEM_PRECOND_NONE = 0, IBEM_PRECOND_JACOBI = 1 };
+
+typedef struct {
+    int kernel;          /* IBEM_LAPLACE or IBEM_HELMHOLTZ                          */
+    double kappa;        /* wavenumber (Helmholtz)                                  */
+    int p;               /* spline degree, 0..4                                    */
+    int m;               /* refinement level, 0..10: 4^m elements per patch         */
+    int q_cheb;          /* Chebyshev points per direction per cluster (2..12); 0 =
+                            no compression: every element pair is near field        */
+    double eta;          /* admissible iff eta * max(diam) < dist (eta = 1/mu, Def. 4.1) */
+    int gauss_regular;   /* Gauss points per direction, regular pairs (default 8)   */
+    int gauss_singular;  /* Gauss points per variable, Duffy rules (default 8)      */
+} ibem_params;
+
+typedef struct {
+    int64_t ndof;          /* dim S_{p,m} = n (2^m + p)^2                          */
+    int64_t ndof_super;    /* dim S*_{p,m} = n (2^m (p+1))^2                       */
+    int64_t n_elements;    /* n 4^m                                                */
+    int64_t n_clusters;    /* n (4^{m+1} - 1) / 3                                  */
+    int64_t n_quad_points; /* n_elements * gauss_regular^2                          */
+    int64_t n_near;        /* near-field element pairs                              */
+    int64_t n_far;         /* far-field cluster pairs (all levels)                  */
+    int64_t n_near_singular[4]; /* near pairs by class: identical, edge, vertex, subdivided */
+    int64_t bytes_near;    /* device bytes of the stored FP64 near blocks           */
+    int64_t bytes_far;     /* device bytes of the stored FP64 coupling matrices     */
+    int assembled;         /* 1 after ibem_assemble                                 */
+} ibem_info;
+
+typedef struct {
+    int iterations;        /* Krylov iterations (inner iterations for mixed)       */
+    int outer;             /* iterative-refinement sweeps (mixed), else 1          */
+    double rel_residual;   /* |b - A w| / |b| with the FP64 operator, recomputed   */
+    double seconds;        /* wall time of the call                                 */
+} ibem_solve_info;
+
+/* Build the discretisation: patches, knot vectors, cluster tree and block
+ * cluster tree (admissibility, Def. 4.1), pair classes of the near field, the
+ * Bezier extraction operator T (Sec. 4.3), geometry tables at Gauss and
+ * interpolation points (Sec. 3.2).  `cuda_stream` is a cudaStream_t (NULL =
+ * legacy default stream).  Synchronises.  On error *out is NULL. */
+ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params* params,
+                        void* cuda_stream, ibem_handle** out);
+
+/* Free every device and host buffer of the handle.  NULL is accepted. */
+ibem_status ibem_destroy(ibem_handle* h);
+
+/* Sizes and counts (host call, no device work). */
+ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info);
+
+/* Assemble the near field (Galerkin blocks of element pairs in the Bernstein
+ * superspace, Gauss and Duffy rules, Sec. 4 item 4) and the FMM coupling
+ * matrices K of every far block (Sec. 4.2).  Synchronises. */
+ibem_status ibem_assemble(ibem_handle* h);
+
+/* Physical Gauss points where the caller samples boundary data:
+ * xyz_dev is [n_quad_points][3] doubles (element by element). */
+ibem_status ibem_quad_points(const ibem_handle* h, double* xyz_dev);
+
+/* Right-hand side b = T g*, b_i = int_Gamma g b_i (Sec. 3.2, Sec. 4.3):
+ * g_dev is [nrhs][n_quad_points] samples of g at ibem_quad_points (complex for
+ * Helmholtz), b_dev is [nrhs][ndof]. */
+ibem_status ibem_rhs(ibem_handle* h, const double* g_dev, int nrhs, double* b_dev);
+
+/* y = T A T^T x (Sec. 4.3): the FMM-compressed single-layer Galerkin matrix in
+ * S_{p,m}.  x_dev, y_dev are [nrhs][ndof] (complex for Helmholtz); they must
+ * not overlap.  precision is IBEM_FP64 or IBEM_FP32.  Requires ibem_assemble. */
+ibem_status ibem_matvec(ibem_handle* h, const double* x_dev, double* y_dev, int nrhs,
+                        int precision);
+
+/* Same as ibem_matvec with x and y in HOST memory: copies in, applies, copies
+ * out, synchronises.  For callers without device buffers. */
+ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrhs,
+                             int precision);
+
+/* Solve T A T^T w = b (Sec. 4 item 3): Jacobi-preconditioned conjugate
+ * gradients (Laplace) or GMRES(restart) (Helmholtz), one right-hand side at a
+ * time.  precision IBEM_FP64 runs the solver on the FP64 operator;
+ * IBEM_FP32 runs iterative refinement: FP64 residuals, FP32-operator inner
+ * solves.  Stops when |b - A w| / |b| <= rtol with A the FP64 operator.
+ * Synchronises; returns IBEM_ERR_NOCONV if maxit is reached. */
+ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int nrhs,
+                       double rtol, int maxit, int precond, int precision,
+                       ibem_solve_info* info);
+
+/* Potential u(x) = int_Gamma u*(x, y) w_h(y) dy (Eq. repform) at npts points
+ * (pts_dev [npts][3]) by Gauss quadrature on every element; w_dev [nrhs][ndof],
+ * u_dev [nrhs][npts] (complex for Helmholtz). */
+ibem_status ibem_potential(ibem_handle* h, const double* w_dev, int nrhs,
+                           const double* pts_dev, int64_t npts, double* u_dev);
+
+/* Per-phase timing of operator applications (tracing).  Phases: 0 lift (T^T),
+ * 1 upward pass (leaf moments, M2M), 2 far-field coupling, 3 downward pass
+ * (L2L, back-projection), 4 near-field product, 5 restriction (T).  While
+ * enabled, every ibem_matvec records a CUDA event pair around each phase on the
+ * handle's stream.  `launches` counts the library's kernel launches of all
+ * applications since the last read, enabled or not. */
+typedef struct {
+    int64_t applications;  /* operator applications recorded                    */
+    int64_t launches;      /* kernels launched by operator applications         */
+    double ms[6];          /* summed device time per phase                        */
+} ibem_profile_data;
+
+/* Enable (1) or disable (0) phase timing; clears the recorded data. */
+ibem_status ibem_profile_enable(ibem_handle* h, int enable);
+
+/* Synchronise the stream, return the sums since the last read/enable, clear. */
+ibem_status ibem_profile_read(ibem_handle* h, ibem_profile_data* out);
+
+/* Host-only: build the block cluster tree without a GPU and return its lists.
+ * Call once with null arrays to get the counts.  near: [n_near][8] int32 =
+ * (patch_t, ix_t, iy_t, patch_s, ix_s, iy_s, class, orientation) with class
+ * 0 identical, 1 common edge, 2 common vertex, 3 subdivided, 4 regular and
+ * orientation = 8 * k_target + k_source (symmetries of the square, in the fixed
+ * order documented in the design doc).  far: [n_far][8] int32 = (patch, level, ix, iy)
+ * of the target cluster then of the source cluster.  Lists are sorted. */
+ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_params* params,
+                            int64_t* n_near, int32_t* near, int64_t* n_far, int32_t* far);
+
+/* Text of the last error recorded on the handle ("" if none).  NULL handle:
+ * the last error of ibem_create / ibem_block_tree in this thread. */
+const char* ibem_last_error(const ibem_handle* h);
+
+/* Static name of a status code. */
+const char* ibem_status_string(ibem_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBEM_H */

@@ -51,10 +51,16 @@ class Mesh:
         return np.stack(((ix + st[:, 0]) * self.h, (iy + st[:, 1]) * self.h), axis=1)
 
     def local_basis(self, e, uv):
-        """Values of the (p+1)^2 local B-splines of element e at patch params uv."""
+        """Values of the (p+1)^2 local B-splines of element e at patch params uv.
+
+        b_{ix}..b_{ix+p} depend only on the knots xi_{ix}..xi_{ix+2p+1}, so the
+        recursion is run on that window; for points inside the element (all
+        quadrature points are) this is the same arithmetic as on the full
+        knot vector."""
         _, ix, iy = self.element(e)
-        bu = bspline.basis_values(self.knots, self.p, uv[:, 0])[:, ix:ix + self.p + 1]
-        bv = bspline.basis_values(self.knots, self.p, uv[:, 1])[:, iy:iy + self.p + 1]
+        w = 2 * self.p + 2
+        bu = bspline.basis_values(self.knots[ix:ix + w], self.p, uv[:, 0])
+        bv = bspline.basis_values(self.knots[iy:iy + w], self.p, uv[:, 1])
         return (bv[:, :, None] * bu[:, None, :]).reshape(len(uv), -1)
 
     def geometry(self, patch, uv):

@@ -1,0 +1,476 @@
+// C ABI of libibem (declared in include/ibem.h): handle life cycle, host-side
+// tables (Bezier extraction, Bernstein values, FMM transfer matrices) and the
+// thin argument checks around the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ibem_internal.cuh"
+
+using namespace ibem;
+
+static thread_local std::string g_last_error;
+
+namespace {
+
+ibem_status fail(ibem_handle* h, ibem_status s, const std::string& msg) {
+    if (h) h->err = msg; else g_last_error = msg;
+    return s;
+}
+
+ibem_status cuda_fail(ibem_handle* h, cudaError_t e, const char* where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(h, e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA, msg);
+}
+
+template <typename T>
+cudaError_t upload(T** dst, const std::vector<T>& src, cudaStream_t st) {
+    size_t n = src.empty() ? 1 : src.size();
+    cudaError_t e = cudaMalloc(dst, n * sizeof(T));
+    if (e) return e;
+    if (!src.empty()) e = cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// Solve the (p+1) x (p+1) system V c = rhs with partial pivoting (in place).
+void small_solve(int n, std::vector<double> V, std::vector<double>& rhs) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(V[r * n + c]) > std::fabs(V[piv * n + c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) std::swap(V[c * n + k], V[piv * n + k]);
+            std::swap(rhs[c], rhs[piv]);
+        }
+        for (int r = c + 1; r < n; ++r) {
+            double f = V[r * n + c] / V[c * n + c];
+            for (int k = c; k < n; ++k) V[r * n + k] -= f * V[c * n + k];
+            rhs[r] -= f * rhs[c];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        double s = rhs[c];
+        for (int k = c + 1; k < n; ++k) s -= V[c * n + k] * rhs[k];
+        rhs[c] = s / V[c * n + c];
+    }
+}
+
+// Bezier extraction of the uniform p-open knot vector Xi_{p,m} (Sec. 4.3): on
+// element ix, b_{ix+r}(x(t)) = sum_i ext[ix][r][i] B_{i,p}(t), found by
+// interpolation at p+1 interior points of the element.
+std::vector<double> bezier_extraction(int p, int m) {
+    int pp = p + 1, ne1 = 1 << m;
+    std::vector<double> knots;
+    for (int i = 0; i < pp; ++i) knots.push_back(0.0);
+    for (int i = 1; i < ne1; ++i) knots.push_back((double)i / ne1);
+    for (int i = 0; i < pp; ++i) knots.push_back(1.0);
+    std::vector<double> ext((size_t)ne1 * pp * pp);
+    std::vector<double> V(pp * pp), B(pp), val(IBEM_MAX_DEG + 1), der(IBEM_MAX_DEG + 1);
+    std::vector<std::vector<double>> rhs(pp, std::vector<double>(pp));
+    for (int ix = 0; ix < ne1; ++ix) {
+        for (int k = 0; k < pp; ++k) {
+            double t = (k + 0.5) / pp;
+            bernstein(p, t, B.data());
+            for (int i = 0; i < pp; ++i) V[k * pp + i] = B[i];
+            if (p == 0) {
+                rhs[0][k] = 1.0;
+                continue;
+            }
+            local_bsplines(knots.data(), p, ix + p, (ix + t) / ne1, val.data(), der.data());
+            for (int r = 0; r < pp; ++r) rhs[r][k] = val[r];
+        }
+        for (int r = 0; r < pp; ++r) {
+            std::vector<double> c = rhs[r];
+            small_solve(pp, V, c);
+            for (int i = 0; i < pp; ++i) ext[((size_t)ix * pp + r) * pp + i] = c[i];
+        }
+    }
+    return ext;
+}
+
+void free_handle(ibem_handle* h) {
+    void* ptrs[] = {h->d_patches, h->d_knots, h->d_cpw, h->d_ext, h->d_qgeo, h->d_igeo, h->d_igeo32, h->d_phi,
+                    h->d_phi_sub, h->d_rule[0], h->d_rule[1], h->d_rule[2], h->d_M, h->d_S, h->d_near_ptr,
+                    h->d_near_src, h->d_near_tgt, h->d_near_cls, h->d_near_orient, h->d_pairs_by_cls[0],
+                    h->d_pairs_by_cls[1], h->d_pairs_by_cls[2], h->d_pairs_by_cls[3], h->d_pairs_by_cls[4],
+                    h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_far_rows,
+                    h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
+                    h->d_solver, h->d_red};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_red) cudaFreeHost(h->h_red);
+    for (auto ev : h->ev_free) cudaEventDestroy(ev);
+    for (auto& u : h->ev_used) { cudaEventDestroy(u.second.first); cudaEventDestroy(u.second.second); }
+    h->ev_free.clear();
+    h->ev_used.clear();
+}
+
+ibem_status check_ready(ibem_handle* h) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (!h->assembled) return fail(h, IBEM_ERR_STATE, "call ibem_assemble first");
+    return IBEM_OK;
+}
+
+cudaError_t set_device(ibem_handle* h) { return cudaSetDevice(h->device); }
+
+}  // namespace
+
+extern "C" {
+
+const char* ibem_status_string(ibem_status s) {
+    switch (s) {
+        case IBEM_OK: return "IBEM_OK";
+        case IBEM_ERR_ARG: return "IBEM_ERR_ARG";
+        case IBEM_ERR_GEOMETRY: return "IBEM_ERR_GEOMETRY";
+        case IBEM_ERR_CUDA: return "IBEM_ERR_CUDA";
+        case IBEM_ERR_OOM: return "IBEM_ERR_OOM";
+        case IBEM_ERR_NOCONV: return "IBEM_ERR_NOCONV";
+        case IBEM_ERR_BREAKDOWN: return "IBEM_ERR_BREAKDOWN";
+        case IBEM_ERR_STATE: return "IBEM_ERR_STATE";
+    }
+    return "IBEM_UNKNOWN";
+}
+
+const char* ibem_last_error(const ibem_handle* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_params* params, int64_t* n_near,
+                            int32_t* near, int64_t* n_far, int32_t* far) {
+    if (!n_near || !n_far) return fail(nullptr, IBEM_ERR_ARG, "n_near / n_far must be non-null");
+    Plan P;
+    std::string msg;
+    try {
+        msg = build_plan(patches, npatch, params, P);
+    } catch (const std::bad_alloc&) {
+        return fail(nullptr, IBEM_ERR_OOM, "host allocation failed");
+    }
+    if (!msg.empty()) return fail(nullptr, msg.find("degenerate") != std::string::npos ? IBEM_ERR_GEOMETRY : IBEM_ERR_ARG, msg);
+    *n_near = P.n_near;
+    *n_far = P.n_far;
+    if (near) {
+        for (int64_t e = 0; e < P.E; ++e)
+            for (int64_t k = P.near_ptr[e]; k < P.near_ptr[e + 1]; ++k) {
+                int pt, xt, yt, ps, xs, ys;
+                element_of(P, e, &pt, &xt, &yt);
+                element_of(P, P.near_src[k], &ps, &xs, &ys);
+                int32_t* o = near + 8 * k;
+                o[0] = pt; o[1] = xt; o[2] = yt; o[3] = ps; o[4] = xs; o[5] = ys;
+                o[6] = P.near_cls[k]; o[7] = P.near_orient[k];
+            }
+    }
+    if (far) {
+        for (int64_t c = 0; c < P.C; ++c)
+            for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k) {
+                int32_t* o = far + 8 * k;
+                int a, b, x, y;
+                cluster_of(P, c, &a, &b, &x, &y);
+                o[0] = a; o[1] = b; o[2] = x; o[3] = y;
+                cluster_of(P, P.far_src[k], &a, &b, &x, &y);
+                o[4] = a; o[5] = b; o[6] = x; o[7] = y;
+            }
+    }
+    return IBEM_OK;
+}
+
+ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params* params, void* cuda_stream,
+                        ibem_handle** out) {
+    if (!out) return fail(nullptr, IBEM_ERR_ARG, "out must be non-null");
+    *out = nullptr;
+    ibem_handle* h = new (std::nothrow) ibem_handle();
+    if (!h) return fail(nullptr, IBEM_ERR_OOM, "host allocation failed");
+    std::string msg;
+    try {
+        msg = build_plan(patches, npatch, params, h->P);
+    } catch (const std::bad_alloc&) {
+        delete h;
+        return fail(nullptr, IBEM_ERR_OOM, "host allocation failed");
+    }
+    if (!msg.empty()) {
+        delete h;
+        return fail(nullptr, msg.find("degenerate") != std::string::npos ? IBEM_ERR_GEOMETRY : IBEM_ERR_ARG, msg);
+    }
+    Plan& P = h->P;
+    if (params->kernel != IBEM_LAPLACE) {
+        delete h;
+        return fail(nullptr, IBEM_ERR_ARG, "the GPU path implements the Laplace kernel only");
+    }
+    h->helm = false;
+    h->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
+    cudaStream_t st = h->stream;
+#define TRY(x, where)                                      \
+    do {                                                   \
+        cudaError_t _e = (x);                              \
+        if (_e) {                                          \
+            ibem_status _s = cuda_fail(nullptr, _e, where); \
+            free_handle(h);                                \
+            delete h;                                      \
+            return _s;                                     \
+        }                                                  \
+    } while (0)
+    TRY(upload(&h->d_patches, P.patches, st), "upload patches");
+    TRY(upload(&h->d_knots, P.knots, st), "upload knots");
+    TRY(upload(&h->d_cpw, P.cpw, st), "upload control points");
+    std::vector<double> ext = bezier_extraction(P.p, P.m);
+    TRY(upload(&h->d_ext, ext, st), "upload extraction");
+
+    // Bernstein products at the regular and the subdivided Gauss points
+    std::vector<double> gx, gw;
+    gauss_legendre(P.Q, gx, gw);
+    int QQ = P.Q * P.Q, nb = P.nb, pp = P.pp;
+    std::vector<double> phi((size_t)QQ * nb), phis((size_t)4 * QQ * nb);
+    double bu[IBEM_MAX_P + 1], bv[IBEM_MAX_P + 1];
+    for (int sub = -1; sub < 4; ++sub)
+        for (int g = 0; g < QQ; ++g) {
+            double s = gx[g % P.Q], t = gx[g / P.Q];
+            if (sub >= 0) { s = 0.5 * (sub & 1) + 0.5 * s; t = 0.5 * (sub >> 1) + 0.5 * t; }
+            bernstein(P.p, s, bu);
+            bernstein(P.p, t, bv);
+            for (int iv = 0; iv < pp; ++iv)
+                for (int iu = 0; iu < pp; ++iu) {
+                    double v = bu[iu] * bv[iv];
+                    if (sub < 0) phi[(size_t)g * nb + iv * pp + iu] = v;
+                    else phis[((size_t)sub * QQ + g) * nb + iv * pp + iu] = v;
+                }
+        }
+    TRY(upload(&h->d_phi, phi, st), "upload phi");
+    TRY(upload(&h->d_phi_sub, phis, st), "upload phi_sub");
+    for (int c = 0; c < 3; ++c) {
+        if (P.n_cls[c] == 0) continue;
+        std::vector<double> soa;
+        singular_rule(c, P.Qs, soa);
+        h->rule_n[c] = (int)(soa.size() / 5);
+        TRY(upload(&h->d_rule[c], soa, st), "upload singular rule");
+    }
+
+    // FMM transfer matrices (1D): leaf moments and M2M re-expansion
+    if (P.q > 0) {
+        std::vector<double> z, L(P.q);
+        chebyshev_nodes(P.q, z);
+        int ng = (P.q + P.p + 1) / 2 + 1;
+        std::vector<double> mx, mw;
+        gauss_legendre(ng, mx, mw);
+        std::vector<double> M((size_t)P.q * pp, 0.0), S((size_t)2 * P.q * P.q);
+        double h1 = 1.0 / P.ne1;
+        for (int k = 0; k < ng; ++k) {
+            lagrange_values(z, mx[k], L.data());
+            bernstein(P.p, mx[k], bu);
+            for (int a = 0; a < P.q; ++a)
+                for (int i = 0; i < pp; ++i) M[a * pp + i] += mw[k] * h1 * L[a] * bu[i];
+        }
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < P.q; ++b) {
+                lagrange_values(z, 0.5 * (c + z[b]), L.data());
+                for (int a = 0; a < P.q; ++a) S[((size_t)c * P.q + a) * P.q + b] = L[a];
+            }
+        TRY(upload(&h->d_M, M, st), "upload M");
+        TRY(upload(&h->d_S, S, st), "upload S");
+    }
+
+    // near and far lists
+    std::vector<int32_t> ntgt(P.n_near);
+    std::vector<std::vector<int32_t>> bycls(5);
+    for (int64_t t = 0; t < P.E; ++t)
+        for (int64_t k = P.near_ptr[t]; k < P.near_ptr[t + 1]; ++k) {
+            ntgt[k] = (int32_t)t;
+            bycls[P.near_cls[k]].push_back((int32_t)k);
+        }
+    TRY(upload(&h->d_near_ptr, P.near_ptr, st), "upload near ptr");
+    TRY(upload(&h->d_near_src, P.near_src, st), "upload near src");
+    TRY(upload(&h->d_near_tgt, ntgt, st), "upload near tgt");
+    TRY(upload(&h->d_near_cls, P.near_cls, st), "upload near cls");
+    TRY(upload(&h->d_near_orient, P.near_orient, st), "upload near orient");
+    for (int c = 0; c < 5; ++c) TRY(upload(&h->d_pairs_by_cls[c], bycls[c], st), "upload class lists");
+    std::vector<int32_t> ftgt(P.n_far);
+    for (int64_t c = 0; c < P.C; ++c) {
+        if (P.far_ptr[c + 1] > P.far_ptr[c]) h->far_rows.push_back((int32_t)c);
+        for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k) ftgt[k] = (int32_t)c;
+    }
+    TRY(upload(&h->d_far_ptr, P.far_ptr, st), "upload far ptr");
+    TRY(upload(&h->d_far_src, P.far_src, st), "upload far src");
+    TRY(upload(&h->d_far_tgt, ftgt, st), "upload far tgt");
+    TRY(upload(&h->d_far_rows, h->far_rows, st), "upload far rows");
+    h->kpt = (P.q2 + 3) / 4;
+
+    TRY(cudaMalloc(&h->d_qgeo, (size_t)P.nq * 4 * sizeof(double)), "alloc qgeo");
+    if (P.q > 0) {
+        TRY(cudaMalloc(&h->d_igeo, (size_t)P.C * P.q2 * 4 * sizeof(double)), "alloc igeo");
+        TRY(cudaMalloc(&h->d_igeo32, (size_t)P.C * P.q2 * 4 * sizeof(float)), "alloc igeo32");
+    }
+    TRY(cudaMalloc(&h->d_diag, (size_t)P.N * sizeof(double)), "alloc diag");
+    TRY(cudaMalloc(&h->d_red, 64 * sizeof(double)), "alloc red");
+    TRY(cudaMallocHost(&h->h_red, 64 * sizeof(double)), "alloc pinned");
+    TRY(launch_geometry_tables(h), "geometry tables");
+    TRY(cudaStreamSynchronize(st), "create sync");
+#undef TRY
+    *out = h;
+    return IBEM_OK;
+}
+
+ibem_status ibem_destroy(ibem_handle* h) {
+    if (!h) return IBEM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    free_handle(h);
+    delete h;
+    return IBEM_OK;
+}
+
+ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
+    if (!h || !info) return fail(nullptr, IBEM_ERR_ARG, "null handle or info");
+    const Plan& P = h->P;
+    info->ndof = P.N;
+    info->ndof_super = P.Nstar;
+    info->n_elements = P.E;
+    info->n_clusters = P.C;
+    info->n_quad_points = P.nq;
+    info->n_near = P.n_near;
+    info->n_far = P.n_far;
+    info->n_near_singular[0] = P.n_cls[CLS_IDENTICAL];
+    info->n_near_singular[1] = P.n_cls[CLS_EDGE];
+    info->n_near_singular[2] = P.n_cls[CLS_VERTEX];
+    info->n_near_singular[3] = P.n_cls[CLS_SUBDIV];
+    info->bytes_near = P.n_near * (int64_t)P.nb * P.nb * 8;
+    info->bytes_far = P.n_far * (int64_t)h->kpt * 4 * P.q2 * 8;
+    info->assembled = h->assembled ? 1 : 0;
+    return IBEM_OK;
+}
+
+ibem_status ibem_assemble(ibem_handle* h) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    Plan& P = h->P;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if (!h->d_near) {
+        size_t nn = (size_t)(P.n_near > 0 ? P.n_near : 1) * P.nb * P.nb;
+        if ((e = cudaMalloc(&h->d_near, nn * sizeof(double)))) return cuda_fail(h, e, "alloc near blocks");
+        if ((e = cudaMalloc(&h->d_near32, nn * sizeof(float)))) return cuda_fail(h, e, "alloc near blocks fp32");
+        if (P.n_far > 0) {
+            size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
+            if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
+        }
+    }
+    if ((e = launch_near_assembly(h))) return cuda_fail(h, e, "near assembly");
+    if ((e = launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");
+    h->assembled = true;
+    return IBEM_OK;
+}
+
+ibem_status ibem_quad_points(const ibem_handle* hc, double* xyz_dev) {
+    ibem_handle* h = const_cast<ibem_handle*>(hc);
+    if (!h || !xyz_dev) return fail(h, IBEM_ERR_ARG, "null handle or output");
+    cudaError_t e = cudaMemcpy2DAsync(xyz_dev, 3 * sizeof(double), h->d_qgeo, 4 * sizeof(double), 3 * sizeof(double),
+                                      (size_t)h->P.nq, cudaMemcpyDeviceToDevice, h->stream);
+    if (e) return cuda_fail(h, e, "quad points copy");
+    return IBEM_OK;
+}
+
+ibem_status ibem_rhs(ibem_handle* h, const double* g_dev, int nrhs, double* b_dev) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (nrhs < 0 || (nrhs > 0 && (!g_dev || !b_dev))) return fail(h, IBEM_ERR_ARG, "bad rhs arguments");
+    if (nrhs == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = launch_rhs(h, g_dev, nrhs, b_dev))) return cuda_fail(h, e, "rhs");
+    return IBEM_OK;
+}
+
+ibem_status ibem_matvec(ibem_handle* h, const double* x_dev, double* y_dev, int nrhs, int precision) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (nrhs < 0 || (nrhs > 0 && (!x_dev || !y_dev))) return fail(h, IBEM_ERR_ARG, "bad matvec arguments");
+    if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
+    if (x_dev == y_dev) return fail(h, IBEM_ERR_ARG, "x and y must not overlap");
+    if (nrhs == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = apply_operator(h, x_dev, y_dev, nrhs, precision))) return cuda_fail(h, e, "matvec");
+    return IBEM_OK;
+}
+
+ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrhs, int precision) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (nrhs < 0 || (nrhs > 0 && (!x || !y))) return fail(h, IBEM_ERR_ARG, "bad matvec arguments");
+    if (nrhs == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    size_t bytes = (size_t)nrhs * h->P.N * sizeof(double);
+    double *dx = nullptr, *dy = nullptr;
+    if ((e = cudaMallocAsync(&dx, bytes, h->stream))) return cuda_fail(h, e, "alloc x");
+    if ((e = cudaMallocAsync(&dy, bytes, h->stream))) { cudaFreeAsync(dx, h->stream); return cuda_fail(h, e, "alloc y"); }
+    e = cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (!e) e = apply_operator(h, dx, dy, nrhs, precision);
+    if (!e) e = cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, h->stream);
+    cudaFreeAsync(dx, h->stream);
+    cudaFreeAsync(dy, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    if (e) return cuda_fail(h, e, "matvec_host");
+    if (e2) return cuda_fail(h, e2, "matvec_host sync");
+    return IBEM_OK;
+}
+
+ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int nrhs, double rtol, int maxit,
+                       int precond, int precision, ibem_solve_info* info) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (nrhs < 0 || (nrhs > 0 && (!b_dev || !w_dev)) || !(rtol > 0.0) || maxit < 1)
+        return fail(h, IBEM_ERR_ARG, "bad solve arguments");
+    if (precond != IBEM_PRECOND_NONE && precond != IBEM_PRECOND_JACOBI) return fail(h, IBEM_ERR_ARG, "unknown preconditioner");
+    if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
+    if (nrhs == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    s = solve_impl(h, b_dev, w_dev, nrhs, rtol, maxit, precond, precision, info);
+    if (s == IBEM_ERR_NOCONV) h->err = "solver did not reach rtol within maxit";
+    else if (s == IBEM_ERR_BREAKDOWN) h->err = "solver breakdown";
+    else if (s != IBEM_OK) h->err = "solver failed (CUDA error)";
+    return s;
+}
+
+ibem_status ibem_profile_enable(ibem_handle* h, int enable) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    ibem_profile_data scratch;
+    ibem_status s = ibem_profile_read(h, &scratch);
+    if (s) return s;
+    h->prof = enable != 0;
+    return IBEM_OK;
+}
+
+ibem_status ibem_profile_read(ibem_handle* h, ibem_profile_data* out) {
+    if (!h || !out) return fail(nullptr, IBEM_ERR_ARG, "null handle or output");
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "profile sync");
+    std::memset(out, 0, sizeof(*out));
+    for (auto& u : h->ev_used) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess && u.first >= 0 && u.first < 6)
+            out->ms[u.first] += ms;
+        h->ev_free.push_back(u.second.first);
+        h->ev_free.push_back(u.second.second);
+    }
+    h->ev_used.clear();
+    out->applications = h->applications;
+    out->launches = h->launches;
+    h->applications = 0;
+    h->launches = 0;
+    return IBEM_OK;
+}
+
+ibem_status ibem_potential(ibem_handle* h, const double* w_dev, int nrhs, const double* pts_dev, int64_t npts,
+                           double* u_dev) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (nrhs < 0 || npts < 0 || (nrhs > 0 && npts > 0 && (!w_dev || !pts_dev || !u_dev)))
+        return fail(h, IBEM_ERR_ARG, "bad potential arguments");
+    if (nrhs == 0 || npts == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = launch_potential(h, w_dev, nrhs, pts_dev, npts, u_dev))) return cuda_fail(h, e, "potential");
+    return IBEM_OK;
+}
+
+}  // extern "C"

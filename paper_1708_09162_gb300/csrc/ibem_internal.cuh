@@ -1,0 +1,295 @@
+// Internal declarations of libibem: patch evaluation (host + device), the
+// handle, launch helpers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ibem.h"
+
+#define IBEM_MAX_DEG 7      // NURBS degree limit
+#define IBEM_MAX_P 4        // spline degree limit
+#define IBEM_MAX_NB 25      // (IBEM_MAX_P + 1)^2 Bernstein functions per element
+#define IBEM_MAX_Q 12       // Chebyshev points per direction
+#define IBEM_PI 3.14159265358979323846
+
+namespace ibem {
+
+// ---------------------------------------------------------------------------
+// Patch description usable on host and device (Sec. 2.2, Eq. def::geom).
+// ---------------------------------------------------------------------------
+struct PatchDesc {
+    int kind;                 // IBEM_PATCH_*
+    int deg_u, deg_v, ncp_u, ncp_v;
+    int knot_off_u, knot_off_v, cp_off;   // offsets into knots[] and cpw[] (x w, y w, z w, w)
+    double R, c0[3], n[3], t1[3], t2[3];  // sphere face
+};
+
+struct GeomView {
+    const PatchDesc* patches;
+    const double* knots;
+    const double* cpw;
+};
+
+// Index of the knot span [xi_s, xi_{s+1}) containing u for a p-open knot vector
+// with ncp control points; u = 1 belongs to the last non-empty span.
+__host__ __device__ inline int find_span(const double* xi, int deg, int ncp, double u) {
+    int s = deg;
+    for (int j = deg; j < ncp; ++j)
+        if (xi[j] <= u && xi[j] < xi[j + 1]) s = j;
+    return s;
+}
+
+// Non-zero B-splines b_{s-deg..s} of degree deg at u and their derivatives,
+// by the Cox-de Boor recursion (Def. 2.1) on the local triangle.
+__host__ __device__ inline void local_bsplines(const double* xi, int deg, int s, double u,
+                                               double* val, double* der) {
+    double b[IBEM_MAX_DEG + 2];
+    for (int k = 0; k <= deg + 1; ++k) b[k] = 0.0;
+    b[deg] = 1.0;                                   // degree 0: only b_s is non-zero
+    double lower[IBEM_MAX_DEG + 2];
+    for (int d = 1; d <= deg; ++d) {
+        if (d == deg)
+            for (int k = 0; k <= deg + 1; ++k) lower[k] = b[k];
+        double nb[IBEM_MAX_DEG + 2];
+        for (int k = 0; k <= deg; ++k) {
+            int j = s - deg + k;
+            double t = 0.0;
+            double den1 = xi[j + d] - xi[j];
+            double den2 = xi[j + d + 1] - xi[j + 1];
+            if (den1 > 0.0) t += (u - xi[j]) / den1 * b[k];
+            if (den2 > 0.0) t += (xi[j + d + 1] - u) / den2 * b[k + 1];
+            nb[k] = t;
+        }
+        nb[deg + 1] = 0.0;
+        for (int k = 0; k <= deg + 1; ++k) b[k] = nb[k];
+    }
+    if (deg == 0) {
+        for (int k = 0; k <= deg; ++k) { val[k] = b[k]; der[k] = 0.0; }
+        return;
+    }
+    for (int k = 0; k <= deg; ++k) {
+        int j = s - deg + k;
+        double dd = 0.0;
+        double den1 = xi[j + deg] - xi[j];
+        double den2 = xi[j + deg + 1] - xi[j + 1];
+        if (den1 > 0.0) dd += deg / den1 * lower[k];
+        if (den2 > 0.0) dd -= deg / den2 * lower[k + 1];
+        val[k] = b[k];
+        der[k] = dd;
+    }
+}
+
+// F(u, v), dF/du, dF/dv of one patch.
+__host__ __device__ inline void eval_patch(const GeomView& g, int ip, double u, double v,
+                                           double F[3], double Fu[3], double Fv[3]) {
+    const PatchDesc& P = g.patches[ip];
+    if (P.kind == IBEM_PATCH_SPHERE_FACE) {
+        double a = 2.0 * u - 1.0, b = 2.0 * v - 1.0;
+        double c[3];
+        for (int i = 0; i < 3; ++i) c[i] = P.n[i] + a * P.t1[i] + b * P.t2[i];
+        double r2 = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        double r = sqrt(r2);
+        double ct1 = c[0] * P.t1[0] + c[1] * P.t1[1] + c[2] * P.t1[2];
+        double ct2 = c[0] * P.t2[0] + c[1] * P.t2[1] + c[2] * P.t2[2];
+        for (int i = 0; i < 3; ++i) {
+            F[i] = P.c0[i] + (P.R * c[i]) / r;
+            Fu[i] = P.R * 2.0 * (P.t1[i] - c[i] * (ct1 / r2)) / r;
+            Fv[i] = P.R * 2.0 * (P.t2[i] - c[i] * (ct2 / r2)) / r;
+        }
+        return;
+    }
+    const double* xu = g.knots + P.knot_off_u;
+    const double* xv = g.knots + P.knot_off_v;
+    int su = find_span(xu, P.deg_u, P.ncp_u, u);
+    int sv = find_span(xv, P.deg_v, P.ncp_v, v);
+    double bu[IBEM_MAX_DEG + 1], du[IBEM_MAX_DEG + 1], bv[IBEM_MAX_DEG + 1], dv[IBEM_MAX_DEG + 1];
+    local_bsplines(xu, P.deg_u, su, u, bu, du);
+    local_bsplines(xv, P.deg_v, sv, v, bv, dv);
+    double S[4] = {0, 0, 0, 0}, Su[4] = {0, 0, 0, 0}, Sv[4] = {0, 0, 0, 0};
+    for (int kv = 0; kv <= P.deg_v; ++kv) {
+        int jv = sv - P.deg_v + kv;
+        for (int ku = 0; ku <= P.deg_u; ++ku) {
+            int ju = su - P.deg_u + ku;
+            const double* cp = g.cpw + P.cp_off + 4 * (jv * P.ncp_u + ju);
+            double w0 = bu[ku] * bv[kv], wu = du[ku] * bv[kv], wv = bu[ku] * dv[kv];
+            for (int i = 0; i < 4; ++i) {
+                S[i] += w0 * cp[i];
+                Su[i] += wu * cp[i];
+                Sv[i] += wv * cp[i];
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) {
+        F[i] = S[i] / S[3];
+        Fu[i] = (Su[i] - F[i] * Su[3]) / S[3];
+        Fv[i] = (Sv[i] - F[i] * Sv[3]) / S[3];
+    }
+}
+
+__host__ __device__ inline double surface_measure(const double Fu[3], const double Fv[3]) {
+    double n0 = Fu[1] * Fv[2] - Fu[2] * Fv[1];
+    double n1 = Fu[2] * Fv[0] - Fu[0] * Fv[2];
+    double n2 = Fu[0] * Fv[1] - Fu[1] * Fv[0];
+    return sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+}
+
+// Bernstein polynomials B_{i,p}(t) = C(p,i) t^i (1-t)^{p-i}, i = 0..p (Sec. 4.3).
+__host__ __device__ inline void bernstein(int p, double t, double* out) {
+    double s = 1.0 - t;
+    // de Casteljau-style build-up: degree d from degree d-1
+    out[0] = 1.0;
+    for (int d = 1; d <= p; ++d) {
+        double prev = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double cur = out[i];
+            out[i] = prev + s * cur;
+            prev = t * cur;
+        }
+        out[d] = prev;
+    }
+}
+
+// Morton (Z-order) interleave of (x, y), x in the even bits.
+__host__ __device__ inline uint32_t morton2(uint32_t x, uint32_t y) {
+    uint32_t r = 0;
+    for (int b = 0; b < 16; ++b) r |= ((x >> b) & 1u) << (2 * b) | ((y >> b) & 1u) << (2 * b + 1);
+    return r;
+}
+__host__ __device__ inline void morton2_inv(uint32_t z, uint32_t* x, uint32_t* y) {
+    uint32_t a = 0, b = 0;
+    for (int k = 0; k < 16; ++k) { a |= ((z >> (2 * k)) & 1u) << k; b |= ((z >> (2 * k + 1)) & 1u) << k; }
+    *x = a; *y = b;
+}
+
+// The eight symmetries rho_k(s,t) = (a0 + a1 s + a2 t, b0 + b1 s + b2 t) of the
+// unit square in a fixed order (identity, rotations by 90/180/270 degrees, the
+// four reflections).  The order decides which canonical orientation a touching
+// pair gets, so it is part of the quadrature rule.
+__host__ __device__ inline void dihedral(int k, double s, double t, double* x, double* y) {
+    switch (k) {
+        case 0: *x = s; *y = t; break;
+        case 1: *x = 1.0 - t; *y = s; break;
+        case 2: *x = 1.0 - s; *y = 1.0 - t; break;
+        case 3: *x = t; *y = 1.0 - s; break;
+        case 4: *x = t; *y = s; break;
+        case 5: *x = 1.0 - s; *y = t; break;
+        case 6: *x = 1.0 - t; *y = 1.0 - s; break;
+        default: *x = s; *y = 1.0 - t; break;
+    }
+}
+
+enum PairClass { CLS_IDENTICAL = 0, CLS_EDGE = 1, CLS_VERTEX = 2, CLS_SUBDIV = 3, CLS_REGULAR = 4 };
+
+// ---------------------------------------------------------------------------
+// Host-side discretisation and tree (setup.cu)
+// ---------------------------------------------------------------------------
+struct Plan {
+    ibem_params prm;
+    int npatch = 0, p = 0, m = 0, pp = 1, nb = 1, ne1 = 1, n1 = 1, Q = 8, Qs = 8, q = 0, q2 = 0;
+    int64_t E = 0, N = 0, Nstar = 0, C = 0, nq = 0;
+    std::vector<PatchDesc> patches;
+    std::vector<double> knots, cpw;
+    GeomView host_view() const { return GeomView{patches.data(), knots.data(), cpw.data()}; }
+    // element e = patch * 4^m + morton(ix, iy); cluster id = level_off[l] + patch * 4^l + morton
+    std::vector<int64_t> level_off;
+    // near field: CSR by target element (sources ascending)
+    std::vector<int64_t> near_ptr;
+    std::vector<int32_t> near_src, near_cls, near_orient;
+    // far field: CSR by target cluster id (sources ascending)
+    std::vector<int64_t> far_ptr;
+    std::vector<int32_t> far_src;
+    int64_t n_near = 0, n_far = 0, n_cls[5] = {0, 0, 0, 0, 0};
+};
+
+std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params* prm, Plan& P);
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+void chebyshev_nodes(int q, std::vector<double>& z);
+void lagrange_values(const std::vector<double>& z, double x, double* L);
+void element_of(const Plan& P, int64_t e, int* patch, int* ix, int* iy);
+void cluster_of(const Plan& P, int64_t c, int* patch, int* level, int* ix, int* iy);
+// Canonical rules (x1, x2, y1, y2, w) of the touching classes, SoA [5][n].
+void singular_rule(int cls, int n, std::vector<double>& soa);
+
+}  // namespace ibem
+
+// ---------------------------------------------------------------------------
+// The handle
+// ---------------------------------------------------------------------------
+struct ibem_handle {
+    ibem::Plan P;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    bool helm = false;
+    bool assembled = false;
+    std::string err;
+
+    // geometry and tables
+    ibem::PatchDesc* d_patches = nullptr;
+    double* d_knots = nullptr;
+    double* d_cpw = nullptr;
+    double* d_ext = nullptr;        // Bezier extraction [ne1][pp][pp]: b_{ix+r} = sum_i ext[ix][r][i] B_i
+    double* d_qgeo = nullptr;       // [E][Q*Q][4] = (x, y, z, gauss weight * k * h^2)
+    double* d_igeo = nullptr;       // [C][q2][4]  = (x, y, z, k) at interpolation points
+    float* d_igeo32 = nullptr;      // same in FP32
+    double* d_phi = nullptr;        // [Q*Q][nb] Bernstein products at the regular Gauss points
+    double* d_phi_sub = nullptr;    // [4][Q*Q][nb] at the 2x2-subdivided Gauss points
+    double* d_rule[3] = {nullptr, nullptr, nullptr};  // singular rules, SoA [5][n]
+    int rule_n[3] = {0, 0, 0};
+    double* d_M = nullptr;          // [q][pp] 1D leaf moments int L_a B_i (times h)
+    double* d_S = nullptr;          // [2][q][q] 1D M2M: S_c[a][b] = L_a((c + z_b) / 2)
+
+    // near field
+    int64_t* d_near_ptr = nullptr;
+    int32_t* d_near_src = nullptr;
+    int32_t* d_near_tgt = nullptr;
+    int32_t* d_near_cls = nullptr;
+    int32_t* d_near_orient = nullptr;
+    int32_t* d_pairs_by_cls[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double* d_near = nullptr;       // [n_near][nb][nb] (complex: [..][2])
+    float* d_near32 = nullptr;
+
+    // far field
+    int64_t* d_far_ptr = nullptr;
+    int32_t* d_far_src = nullptr;
+    int32_t* d_far_tgt = nullptr;
+    double* d_K = nullptr;          // [n_far][kpt][4 q2]: entry (a, b = s + 4k) at [k][4a + s]
+    int kpt = 0;
+    std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
+    int32_t* d_far_rows = nullptr;
+
+    // work vectors (sized for ws_nrhs right-hand sides)
+    int ws_nrhs = 0;
+    double *d_xs = nullptr, *d_ys = nullptr, *d_xh = nullptr, *d_yh = nullptr;
+    float *d_xs32 = nullptr, *d_ys32 = nullptr, *d_yh32 = nullptr;
+    float4* d_src32 = nullptr;
+    double* d_diag = nullptr;       // Jacobi diagonal of T A_near T^T
+    double* d_solver = nullptr;     // solver work space
+    size_t solver_len = 0;
+    double* d_red = nullptr;        // reduction scratch
+    double* h_red = nullptr;        // pinned host copy of reductions
+
+    // tracing: event pairs per phase while enabled, launch counter always
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    int64_t launches = 0, applications = 0;
+};
+
+namespace ibem {
+// kernels_*.cu entry points (launch on h->stream; return cudaError_t)
+cudaError_t launch_geometry_tables(ibem_handle* h);
+cudaError_t launch_near_assembly(ibem_handle* h);
+cudaError_t launch_far_assembly(ibem_handle* h);
+cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs, int precision);
+cudaError_t launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b);
+cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts,
+                             int64_t npts, double* u);
+cudaError_t launch_near_diagonal(ibem_handle* h, double* diag);
+ibem_status solve_impl(ibem_handle* h, const double* b, double* w, int nrhs, double rtol,
+                       int maxit, int precond, int precision, ibem_solve_info* info);
+cudaError_t ensure_workspace(ibem_handle* h, int nrhs);
+}  // namespace ibem

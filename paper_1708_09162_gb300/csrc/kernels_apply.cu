@@ -1,0 +1,496 @@
+// Operator application of libibem: y = T [A_near + U K V^T] T^T x (Sec. 4.2,
+// Sec. 4.3), plus right-hand side and potential evaluation.
+//
+// Steps of one application (each a kernel below):
+//   lift       x* = T^T x            Bezier extraction per element
+//   moments    x^_e = (M (x) M) x*_e  leaf moments int L_a B_i (geometry-free)
+//   M2M        x^_P = sum_c (S_c (x) S_c) x^_c   level by level, leaves to root
+//   coupling   y^_s = sum_t K_st x^_t             every far block, all levels
+//   L2L        y^_c += (S_c (x) S_c)^T y^_P       root to leaves
+//   back       y*_e = (M (x) M)^T y^_e
+//   near       y*_e += sum_{e'} B_{e e'} x*_{e'}  stored near-field blocks
+//   restrict   y = T y*
+// S_c[a][b] = L_a((c + z_b) / 2) re-expands a parent Lagrange polynomial in the
+// child's basis exactly (degree q-1), so nested and non-nested moments agree.
+#include "ibem_internal.cuh"
+
+namespace ibem {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ inline void elem_coords(int64_t e, int ne1, int* patch, int* ix, int* iy) {
+    int64_t per = (int64_t)ne1 * ne1;
+    *patch = (int)(e / per);
+    uint32_t x, y;
+    morton2_inv((uint32_t)(e % per), &x, &y);
+    *ix = (int)x;
+    *iy = (int)y;
+}
+
+// ---- T^T and T ---------------------------------------------------------------
+__global__ void lift_kernel(int R, int64_t E, int p, int ne1, const double* __restrict__ ext,
+                            const double* __restrict__ x, int64_t N, double* __restrict__ xs) {
+    int pp = p + 1, nb = pp * pp, n1 = ne1 + p;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * E * nb) return;
+    int64_t r = idx / (E * nb);
+    int64_t rem = idx % (E * nb);
+    int64_t e = rem / nb;
+    int i = (int)(rem % nb), iu = i % pp, iv = i / pp;
+    int patch, ix, iy;
+    elem_coords(e, ne1, &patch, &ix, &iy);
+    const double* xp = x + r * N + (int64_t)patch * n1 * n1;
+    double acc = 0.0;
+    for (int r2 = 0; r2 < pp; ++r2) {
+        double cv = ext[((int64_t)iy * pp + r2) * pp + iv];
+        double row = 0.0;
+        for (int r1 = 0; r1 < pp; ++r1) row += ext[((int64_t)ix * pp + r1) * pp + iu] * xp[(iy + r2) * n1 + ix + r1];
+        acc += cv * row;
+    }
+    xs[idx] = acc;
+}
+
+__global__ void restrict_kernel(int R, int64_t N, int p, int ne1, const double* __restrict__ ext,
+                                const double* __restrict__ ys, int64_t E, double* __restrict__ y) {
+    int pp = p + 1, nb = pp * pp, n1 = ne1 + p;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * N) return;
+    int64_t r = idx / N, dof = idx % N;
+    int patch = (int)(dof / ((int64_t)n1 * n1));
+    int rem = (int)(dof % ((int64_t)n1 * n1));
+    int jv = rem / n1, ju = rem % n1;
+    int64_t per = (int64_t)ne1 * ne1;
+    double acc = 0.0;
+    for (int iy = jv - p; iy <= jv; ++iy) {
+        if (iy < 0 || iy >= ne1) continue;
+        for (int ix = ju - p; ix <= ju; ++ix) {
+            if (ix < 0 || ix >= ne1) continue;
+            const double* v = ys + (r * E + patch * per + morton2(ix, iy)) * nb;
+            const double* cu = ext + ((int64_t)ix * pp + (ju - ix)) * pp;
+            const double* cv = ext + ((int64_t)iy * pp + (jv - iy)) * pp;
+            for (int iv = 0; iv < pp; ++iv) {
+                double row = 0.0;
+                for (int iu = 0; iu < pp; ++iu) row += cu[iu] * v[iv * pp + iu];
+                acc += cv[iv] * row;
+            }
+        }
+    }
+    y[idx] = acc;
+}
+
+// ---- upward pass -------------------------------------------------------------
+__global__ void leaf_moment_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                                   const double* __restrict__ xs, int64_t leaf_off, int64_t C,
+                                   double* __restrict__ xh) {
+    int q2 = q * q, nb = pp * pp;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * E * q2) return;
+    int64_t r = idx / (E * q2);
+    int64_t rem = idx % (E * q2);
+    int64_t e = rem / q2;
+    int a = (int)(rem % q2), au = a % q, av = a / q;
+    const double* v = xs + (r * E + e) * nb;
+    double acc = 0.0;
+    for (int iv = 0; iv < pp; ++iv) {
+        double row = 0.0;
+        for (int iu = 0; iu < pp; ++iu) row += M[au * pp + iu] * v[iv * pp + iu];
+        acc += M[av * pp + iv] * row;
+    }
+    xh[(r * C + leaf_off + e) * q2 + a] = acc;
+}
+
+__global__ void m2m_kernel(int R, int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                           int64_t C, double* __restrict__ xh) {
+    int q2 = q * q;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * nL * q2) return;
+    int64_t r = idx / (nL * q2);
+    int64_t rem = idx % (nL * q2);
+    int64_t pl = rem / q2;
+    int a = (int)(rem % q2), au = a % q, av = a / q;
+    double acc = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        const double* Su = S + (c & 1) * q2;
+        const double* Sv = S + (c >> 1) * q2;
+        const double* v = xh + (r * C + offL1 + 4 * pl + c) * q2;
+        for (int bv = 0; bv < q; ++bv) {
+            double row = 0.0;
+            for (int bu = 0; bu < q; ++bu) row += Su[au * q + bu] * v[bv * q + bu];
+            acc += Sv[av * q + bv] * row;
+        }
+    }
+    xh[(r * C + offL + pl) * q2 + a] = acc;
+}
+
+// ---- coupling, FP64, stored K ------------------------------------------------
+// One CTA per target cluster with far blocks; thread t = 4 a + s accumulates
+// row a over columns b = s + 4 kk of every block, then the 4 lanes of a row
+// are summed with shuffles.  K is laid out so that each kk step is one
+// contiguous 4 q2-double read across the CTA.
+__global__ void coupling64_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
+                                  const int32_t* __restrict__ fsrc, const double* __restrict__ K, int q2, int kpt,
+                                  int64_t C, const double* __restrict__ xh, double* __restrict__ yh) {
+    int sigma = rows[blockIdx.x];
+    int64_t r = blockIdx.y;
+    int t = threadIdx.x, s = t & 3, a = t >> 2;
+    bool active = t < 4 * q2;
+    double acc = 0.0;
+    if (active) {
+        int64_t b0 = fptr[sigma], b1 = fptr[sigma + 1];
+        const double* xr = xh + r * C * q2;
+        for (int64_t blk = b0; blk < b1; ++blk) {
+            const double* Kb = K + blk * (int64_t)kpt * 4 * q2 + t;
+            const double* xt = xr + (int64_t)fsrc[blk] * q2;
+            for (int kk = 0; kk < kpt; ++kk) {
+                int b = s + 4 * kk;
+                if (b < q2) acc += Kb[(int64_t)kk * 4 * q2] * xt[b];
+            }
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (active && s == 0) yh[(r * C + sigma) * q2 + a] = acc;
+}
+
+// ---- coupling, FP32, kernel generated on the fly ------------------------------
+// src32[t][b] = (x, y, z, k_b x^_b / (4 pi)) of every cluster; one CTA per target
+// cluster; thread (g, a) handles target point a against blocks g, g + NS, ...;
+// the per-block float sums are accumulated in double.
+__global__ void src32_kernel(int64_t n, const float* __restrict__ igeo32, const double* __restrict__ xh,
+                             float4* __restrict__ src) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* g = igeo32 + 4 * i;
+    src[i] = make_float4(g[0], g[1], g[2], (float)((double)g[3] * xh[i] * (1.0 / (4.0 * IBEM_PI))));
+}
+
+__global__ void coupling32_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
+                                  const int32_t* __restrict__ fsrc, const float* __restrict__ igeo32,
+                                  const float4* __restrict__ src, int q2, int ns, double* __restrict__ yh) {
+    extern __shared__ double red[];
+    int sigma = rows[blockIdx.x];
+    int t = threadIdx.x;
+    int g = t / q2, a = t % q2;
+    double acc = 0.0;
+    if (g < ns) {
+        const float* X = igeo32 + 4 * ((int64_t)sigma * q2 + a);
+        float x0 = X[0], x1 = X[1], x2 = X[2];
+        int64_t b0 = fptr[sigma], b1 = fptr[sigma + 1];
+        for (int64_t blk = b0 + g; blk < b1; blk += ns) {
+            const float4* Y = src + (int64_t)fsrc[blk] * q2;
+            float f = 0.0f;
+            for (int b = 0; b < q2; ++b) {
+                float4 y = Y[b];
+                float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+                f += y.w * rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            }
+            acc += (double)f;
+        }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < q2) {
+        double v = 0.0;
+        for (int k = 0; k < ns; ++k) v += red[k * q2 + t];
+        yh[(int64_t)sigma * q2 + t] = v * (double)igeo32[4 * ((int64_t)sigma * q2 + t) + 3];
+    }
+}
+
+// ---- downward pass -----------------------------------------------------------
+__global__ void l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                           int64_t C, double* __restrict__ yh) {
+    int q2 = q * q;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * nL1 * q2) return;
+    int64_t r = idx / (nL1 * q2);
+    int64_t rem = idx % (nL1 * q2);
+    int64_t cl = rem / q2;
+    int b = (int)(rem % q2), bu = b % q, bv = b / q;
+    int c = (int)(cl & 3);
+    const double* Su = S + (c & 1) * q2;
+    const double* Sv = S + (c >> 1) * q2;
+    const double* v = yh + (r * C + offL + cl / 4) * q2;
+    double acc = 0.0;
+    for (int av = 0; av < q; ++av) {
+        double row = 0.0;
+        for (int au = 0; au < q; ++au) row += Su[au * q + bu] * v[av * q + au];
+        acc += Sv[av * q + bv] * row;
+    }
+    yh[(r * C + offL1 + cl) * q2 + b] += acc;
+}
+
+__global__ void leaf_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                                 const double* __restrict__ yh, int64_t leaf_off, int64_t C,
+                                 double* __restrict__ ys) {
+    int q2 = q * q, nb = pp * pp;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * E * nb) return;
+    int64_t r = idx / (E * nb);
+    int64_t rem = idx % (E * nb);
+    int64_t e = rem / nb;
+    int i = (int)(rem % nb), iu = i % pp, iv = i / pp;
+    const double* v = yh + (r * C + leaf_off + e) * q2;
+    double acc = 0.0;
+    for (int av = 0; av < q; ++av) {
+        double row = 0.0;
+        for (int au = 0; au < q; ++au) row += M[au * pp + iu] * v[av * q + au];
+        acc += M[av * pp + iv] * row;
+    }
+    ys[idx] = acc;
+}
+
+// ---- near field product ------------------------------------------------------
+// One CTA per target element; thread t = i * nb + j accumulates B[i][j] x*_s[j]
+// over the row's blocks (one coalesced nb^2 read per block), then rows are
+// summed through shared memory.
+template <typename T>
+__global__ void near_apply_kernel(const int64_t* __restrict__ nptr, const int32_t* __restrict__ nsrc,
+                                  const T* __restrict__ blocks, int nb, int64_t E, const T* __restrict__ xs,
+                                  double* __restrict__ ys) {
+    extern __shared__ double red[];
+    int64_t e = blockIdx.x, r = blockIdx.y;
+    int t = threadIdx.x, nbb = nb * nb;
+    double acc = 0.0;
+    if (t < nbb) {
+        int j = t % nb;
+        const T* xr = xs + r * E * nb;
+        T part = (T)0;
+        for (int64_t k = nptr[e]; k < nptr[e + 1]; ++k)
+            part += blocks[k * nbb + t] * xr[(int64_t)nsrc[k] * nb + j];
+        acc = (double)part;
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < nb) {
+        double v = 0.0;
+        for (int j = 0; j < nb; ++j) v += red[t * nb + j];
+        ys[(r * E + e) * nb + t] += v;
+    }
+}
+
+__global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)in[i];
+}
+
+cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
+    if (nrhs <= h->ws_nrhs) return cudaSuccess;
+    Plan& P = h->P;
+    cudaFree(h->d_xs); cudaFree(h->d_ys); cudaFree(h->d_xh); cudaFree(h->d_yh);
+    cudaFree(h->d_xs32); cudaFree(h->d_src32);
+    h->d_xs = h->d_ys = h->d_xh = h->d_yh = nullptr;
+    h->d_xs32 = nullptr;
+    h->d_src32 = nullptr;
+    h->ws_nrhs = 0;
+    cudaError_t e;
+    size_t ns = (size_t)nrhs * P.Nstar, nh = (size_t)nrhs * P.C * (P.q2 > 0 ? P.q2 : 1);
+    if ((e = cudaMalloc(&h->d_xs, ns * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&h->d_ys, ns * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&h->d_xh, nh * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&h->d_yh, nh * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&h->d_xs32, ns * sizeof(float)))) return e;
+    if ((e = cudaMalloc(&h->d_src32, (size_t)P.C * (P.q2 > 0 ? P.q2 : 1) * sizeof(float4)))) return e;
+    h->ws_nrhs = nrhs;
+    return cudaSuccess;
+}
+
+namespace {
+// Phase timer: records an event pair on the stream while profiling is on.
+struct PhaseTimer {
+    ibem_handle* h;
+    int phase;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t take() {
+        cudaEvent_t ev = nullptr;
+        if (!h->ev_free.empty()) { ev = h->ev_free.back(); h->ev_free.pop_back(); }
+        else cudaEventCreate(&ev);
+        return ev;
+    }
+    PhaseTimer(ibem_handle* hh, int ph) : h(hh), phase(ph) {
+        if (!h->prof) return;
+        a = take();
+        b = take();
+        cudaEventRecord(a, h->stream);
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEventRecord(b, h->stream);
+        h->ev_used.push_back({phase, {a, b}});
+    }
+};
+}  // namespace
+
+cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs, int precision) {
+    Plan& P = h->P;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    if ((e = ensure_workspace(h, nrhs))) return e;
+    const int R = nrhs;
+    const int T = 256;
+    h->applications++;
+    {
+        PhaseTimer pt(h, 0);
+        lift_kernel<<<nblk(R * P.E * P.nb, T), T, 0, st>>>(R, P.E, P.p, P.ne1, h->d_ext, x, P.N, h->d_xs);
+        h->launches++;
+    }
+    if (P.q > 0) {
+        const int q2 = P.q2;
+        const int64_t leaf_off = P.level_off[P.m];
+        {
+            PhaseTimer pt(h, 1);
+            leaf_moment_kernel<<<nblk(R * P.E * q2, T), T, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, h->d_xs, leaf_off,
+                                                                     P.C, h->d_xh);
+            h->launches++;
+            for (int L = P.m - 1; L >= 0; --L) {
+                int64_t nL = P.level_off[L + 1] - P.level_off[L];
+                m2m_kernel<<<nblk(R * nL * q2, T), T, 0, st>>>(R, nL, P.level_off[L], P.level_off[L + 1], P.q,
+                                                               h->d_S, P.C, h->d_xh);
+                h->launches++;
+            }
+            if ((e = cudaMemsetAsync(h->d_yh, 0, (size_t)R * P.C * q2 * sizeof(double), st))) return e;
+        }
+        unsigned nrows = (unsigned)h->far_rows.size();
+        if (nrows > 0) {
+            PhaseTimer pt(h, 2);
+            if (precision == IBEM_FP32) {
+                int ns = 256 / q2 > 0 ? 256 / q2 : 1;
+                int threads = ((ns * q2 + 31) / 32) * 32;
+                for (int r = 0; r < R; ++r) {
+                    src32_kernel<<<nblk(P.C * q2, T), T, 0, st>>>(P.C * q2, h->d_igeo32, h->d_xh + (size_t)r * P.C * q2,
+                                                                  h->d_src32);
+                    coupling32_kernel<<<nrows, threads, threads * sizeof(double), st>>>(
+                        h->d_far_rows, h->d_far_ptr, h->d_far_src, h->d_igeo32, h->d_src32, q2, ns,
+                        h->d_yh + (size_t)r * P.C * q2);
+                    h->launches += 2;
+                }
+            } else {
+                int threads = ((4 * q2 + 31) / 32) * 32;
+                coupling64_kernel<<<dim3(nrows, R), threads, 0, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src, h->d_K,
+                                                                      q2, h->kpt, P.C, h->d_xh, h->d_yh);
+                h->launches++;
+            }
+        }
+        PhaseTimer pt(h, 3);
+        for (int L = 0; L < P.m; ++L) {
+            int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
+            l2l_kernel<<<nblk(R * nL1 * q2, T), T, 0, st>>>(R, nL1, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
+                                                             P.C, h->d_yh);
+            h->launches++;
+        }
+        leaf_back_kernel<<<nblk(R * P.E * P.nb, T), T, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, h->d_yh, leaf_off, P.C,
+                                                                 h->d_ys);
+        h->launches++;
+    } else {
+        if ((e = cudaMemsetAsync(h->d_ys, 0, (size_t)R * P.Nstar * sizeof(double), st))) return e;
+    }
+    int threads = ((P.nb * P.nb + 31) / 32) * 32;
+    {
+        PhaseTimer pt(h, 4);
+        if (precision == IBEM_FP32) {
+            d2f_kernel<<<nblk(R * P.Nstar, T), T, 0, st>>>(h->d_xs, h->d_xs32, R * P.Nstar);
+            near_apply_kernel<float><<<dim3((unsigned)P.E, R), threads, threads * sizeof(double), st>>>(
+                h->d_near_ptr, h->d_near_src, h->d_near32, P.nb, P.E, h->d_xs32, h->d_ys);
+            h->launches += 2;
+        } else {
+            near_apply_kernel<double><<<dim3((unsigned)P.E, R), threads, threads * sizeof(double), st>>>(
+                h->d_near_ptr, h->d_near_src, h->d_near, P.nb, P.E, h->d_xs, h->d_ys);
+            h->launches++;
+        }
+    }
+    {
+        PhaseTimer pt(h, 5);
+        restrict_kernel<<<nblk(R * P.N, T), T, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, h->d_ys, P.E, y);
+        h->launches++;
+    }
+    return cudaGetLastError();
+}
+
+// ---- right-hand side -----------------------------------------------------------
+// g*_e[i] = sum_g W_g Phi[g][i] g(x_g), then b = T g*.
+__global__ void rhs_super_kernel(int R, int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
+                                 const double* __restrict__ phi, const double* __restrict__ g, int64_t nq,
+                                 double* __restrict__ gs) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * E * nb) return;
+    int64_t r = idx / (E * nb);
+    int64_t rem = idx % (E * nb);
+    int64_t e = rem / nb;
+    int i = (int)(rem % nb);
+    double acc = 0.0;
+    for (int q = 0; q < QQ; ++q) acc += qgeo[4 * (e * QQ + q) + 3] * phi[q * nb + i] * g[r * nq + e * QQ + q];
+    gs[idx] = acc;
+}
+
+cudaError_t launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b) {
+    Plan& P = h->P;
+    cudaError_t e;
+    if ((e = ensure_workspace(h, nrhs))) return e;
+    const int T = 256;
+    int QQ = P.Q * P.Q;
+    rhs_super_kernel<<<nblk(nrhs * P.E * P.nb, T), T, 0, h->stream>>>(nrhs, P.E, QQ, P.nb, h->d_qgeo, h->d_phi, g,
+                                                                       P.nq, h->d_ys);
+    restrict_kernel<<<nblk(nrhs * P.N, T), T, 0, h->stream>>>(nrhs, P.N, P.p, P.ne1, h->d_ext, h->d_ys, P.E, b);
+    return cudaGetLastError();
+}
+
+// ---- potential -------------------------------------------------------------------
+// u(x) = sum_e sum_g W_g w_h(x_g) / (4 pi |x - x_g|).  The densities at the Gauss
+// points are formed first; then every thread owns one evaluation point and a
+// slice of the sources, and slices are combined with atomics.
+__global__ void density_kernel(int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
+                               const double* __restrict__ phi, const double* __restrict__ ws,
+                               double4_32a* __restrict__ srcs) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * QQ) return;
+    int64_t e = idx / QQ;
+    int q = (int)(idx % QQ);
+    double mu = 0.0;
+    for (int i = 0; i < nb; ++i) mu += phi[q * nb + i] * ws[e * nb + i];
+    const double* X = qgeo + 4 * idx;
+    srcs[idx] = make_double4_32a(X[0], X[1], X[2], X[3] * mu / (4.0 * IBEM_PI));
+}
+
+__global__ void potential_kernel(int64_t npts, const double* __restrict__ pts, int64_t nsrc,
+                                 const double4_32a* __restrict__ srcs, int64_t chunk, double* __restrict__ u) {
+    int64_t ip = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ip >= npts) return;
+    double x0 = pts[3 * ip], x1 = pts[3 * ip + 1], x2 = pts[3 * ip + 2];
+    int64_t s0 = blockIdx.y * chunk, s1 = s0 + chunk < nsrc ? s0 + chunk : nsrc;
+    double acc = 0.0;
+    for (int64_t s = s0; s < s1; ++s) {
+        double4_32a y = srcs[s];
+        double d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+        acc += y.w / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    atomicAdd(u + ip, acc);
+}
+
+cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
+                             double* u) {
+    Plan& P = h->P;
+    cudaError_t e;
+    if ((e = ensure_workspace(h, 1))) return e;
+    const int T = 256;
+    int QQ = P.Q * P.Q;
+    double4_32a* srcs = nullptr;
+    if ((e = cudaMallocAsync(&srcs, (size_t)P.E * QQ * sizeof(double4_32a), h->stream))) return e;
+    if ((e = cudaMemsetAsync(u, 0, (size_t)nrhs * npts * sizeof(double), h->stream))) return e;
+    int64_t nsrc = P.E * QQ;
+    int64_t nsplit = (608 * 128) / (npts > 0 ? npts : 1);
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 65535) nsplit = 65535;
+    int64_t chunk = (nsrc + nsplit - 1) / nsplit;
+    nsplit = (nsrc + chunk - 1) / chunk;
+    for (int r = 0; r < nrhs && npts > 0; ++r) {
+        lift_kernel<<<nblk(P.E * P.nb, T), T, 0, h->stream>>>(1, P.E, P.p, P.ne1, h->d_ext, w + (size_t)r * P.N, P.N,
+                                                              h->d_xs);
+        density_kernel<<<nblk(nsrc, T), T, 0, h->stream>>>(P.E, QQ, P.nb, h->d_qgeo, h->d_phi, h->d_xs, srcs);
+        potential_kernel<<<dim3(nblk(npts, 128), (unsigned)nsplit), 128, 0, h->stream>>>(npts, pts, nsrc, srcs, chunk,
+                                                                                         u + (size_t)r * npts);
+    }
+    cudaError_t le = cudaGetLastError();
+    cudaFreeAsync(srcs, h->stream);
+    return le;
+}
+
+}  // namespace ibem

@@ -1,0 +1,417 @@
+// Host-side setup of libibem: validation, patch tables, Gauss and Chebyshev
+// rules, cluster tree, block cluster tree and near-pair classification.
+//
+// Cluster tree (Sec. 4.1): every patch is refined uniformly; a cluster is a
+// square (patch, level, ix, iy) of a patch parameter domain.  Elements are the
+// level-m clusters, numbered e = patch * 4^m + morton(ix, iy), so every cluster
+// owns a contiguous range of elements.  Cluster ids are level-major:
+// id = level_off[level] + patch * 4^level + morton(ix, iy).
+//
+// Admissibility (Def. 4.1, read with eta = 1/mu): a block (s, t) is admissible
+// iff eta * max(diam s, diam t) < dist(s, t), with diam = 2 r, dist =
+// max(0, |c_s - c_t| - r_s - r_t), c = F(midpoint) and r the largest distance
+// from c to F on a 5 x 5 uniform parameter grid.  Starting from all patch pairs,
+// admissible blocks are far field, non-admissible element pairs near field, and
+// every other block is split into its 4 x 4 child pairs.
+//
+// Near pairs are classified for the quadrature (Sec. 4 item 4): identical,
+// common edge, common vertex (corners equal to 1e-10 * diam), "subdivided"
+// (dist < diam / 2: 2 x 2 split of both elements), otherwise regular.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "ibem_internal.cuh"
+
+namespace ibem {
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+    // roots of P_n by Newton's method; P_n, P_n' by the three-term recurrence
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(IBEM_PI * (i + 0.75) / (n + 0.5));
+        double p0 = 1.0, p1 = t, dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            p0 = 1.0;
+            p1 = t;
+            for (int k = 1; k < n; ++k) {
+                double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = t; p0 = 1.0; }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        p0 = 1.0;
+        p1 = t;
+        for (int k = 1; k < n; ++k) {
+            double p2 = ((2.0 * k + 1.0) * t * p1 - k * p0) / (k + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (t * p1 - p0) / (t * t - 1.0);
+        // ascending order on [0, 1]
+        x[n - 1 - i] = 0.5 * (t + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+void chebyshev_nodes(int q, std::vector<double>& z) {
+    z.resize(q);
+    for (int a = 0; a < q; ++a) z[a] = 0.5 * (1.0 - std::cos((2.0 * a + 1.0) * IBEM_PI / (2.0 * q)));
+}
+
+void lagrange_values(const std::vector<double>& z, double x, double* L) {
+    int q = (int)z.size();
+    for (int a = 0; a < q; ++a) {
+        double v = 1.0;
+        for (int b = 0; b < q; ++b)
+            if (b != a) v *= (x - z[b]) / (z[a] - z[b]);
+        L[a] = v;
+    }
+}
+
+void element_of(const Plan& P, int64_t e, int* patch, int* ix, int* iy) {
+    int64_t per = (int64_t)P.ne1 * P.ne1;
+    *patch = (int)(e / per);
+    uint32_t x, y;
+    morton2_inv((uint32_t)(e % per), &x, &y);
+    *ix = (int)x;
+    *iy = (int)y;
+}
+
+void cluster_of(const Plan& P, int64_t c, int* patch, int* level, int* ix, int* iy) {
+    int l = 0;
+    while (l + 1 < (int)P.level_off.size() && P.level_off[l + 1] <= c) ++l;
+    int64_t r = c - P.level_off[l];
+    int64_t per = (int64_t)1 << (2 * l);
+    *patch = (int)(r / per);
+    *level = l;
+    uint32_t x, y;
+    morton2_inv((uint32_t)(r % per), &x, &y);
+    *ix = (int)x;
+    *iy = (int)y;
+}
+
+static int64_t cluster_id(const Plan& P, int patch, int level, int ix, int iy) {
+    return P.level_off[level] + (int64_t)patch * ((int64_t)1 << (2 * level)) + morton2(ix, iy);
+}
+
+void singular_rule(int cls, int n, std::vector<double>& soa) {
+    std::vector<double> g, w;
+    gauss_legendre(n, g, w);
+    std::vector<double> X1, X2, Y1, Y2, W;
+    auto split = [](double z, double s, int o, double* x, double* y) {
+        double a = (1.0 - z) * s;
+        if (o == 0) { *x = a; *y = a + z; } else { *x = a + z; *y = a; }
+    };
+    for (int i0 = 0; i0 < n; ++i0)
+        for (int i1 = 0; i1 < n; ++i1)
+            for (int i2 = 0; i2 < n; ++i2)
+                for (int i3 = 0; i3 < n; ++i3) {
+                    double xi = g[i0], e1 = g[i1], e2 = g[i2], e3 = g[i3];
+                    double Wq = w[i0] * w[i1] * w[i2] * w[i3];
+                    if (cls == CLS_IDENTICAL) {
+                        // e1 = eta, e2 = s1, e3 = s2
+                        for (int tri = 0; tri < 2; ++tri) {
+                            double z1 = tri == 0 ? xi : xi * e1;
+                            double z2 = tri == 0 ? xi * e1 : xi;
+                            for (int o1 = 0; o1 < 2; ++o1)
+                                for (int o2 = 0; o2 < 2; ++o2) {
+                                    double x1, y1, x2, y2;
+                                    split(z1, e2, o1, &x1, &y1);
+                                    split(z2, e3, o2, &x2, &y2);
+                                    X1.push_back(x1); X2.push_back(x2);
+                                    Y1.push_back(y1); Y2.push_back(y2);
+                                    W.push_back(Wq * xi * (1.0 - z1) * (1.0 - z2));
+                                }
+                        }
+                    } else if (cls == CLS_EDGE) {
+                        // pyramids of the cube (x1, y1, z); e3 = s along the edge
+                        for (int pyr = 0; pyr < 3; ++pyr) {
+                            double x1, y1, z;
+                            if (pyr == 0) { x1 = xi; y1 = xi * e1; z = xi * e2; }
+                            else if (pyr == 1) { x1 = xi * e1; y1 = xi; z = xi * e2; }
+                            else { x1 = xi * e1; y1 = xi * e2; z = xi; }
+                            for (int o = 0; o < 2; ++o) {
+                                double x2, y2;
+                                split(z, e3, o, &x2, &y2);
+                                X1.push_back(x1); X2.push_back(x2);
+                                Y1.push_back(y1); Y2.push_back(y2);
+                                W.push_back(Wq * xi * xi * (1.0 - z));
+                            }
+                        }
+                    } else {
+                        // pyramids of the 4-cube (x1, x2, y1, y2)
+                        for (int pyr = 0; pyr < 4; ++pyr) {
+                            double c[4];
+                            double rest[3] = {xi * e1, xi * e2, xi * e3};
+                            int k = 0;
+                            for (int d = 0; d < 4; ++d) c[d] = (d == pyr) ? xi : rest[k++];
+                            X1.push_back(c[0]); X2.push_back(c[1]);
+                            Y1.push_back(c[2]); Y2.push_back(c[3]);
+                            W.push_back(Wq * xi * xi * xi);
+                        }
+                    }
+                }
+    size_t np = W.size();
+    soa.resize(5 * np);
+    std::copy(X1.begin(), X1.end(), soa.begin());
+    std::copy(X2.begin(), X2.end(), soa.begin() + np);
+    std::copy(Y1.begin(), Y1.end(), soa.begin() + 2 * np);
+    std::copy(Y2.begin(), Y2.end(), soa.begin() + 3 * np);
+    std::copy(W.begin(), W.end(), soa.begin() + 4 * np);
+}
+
+namespace {
+
+struct Ball { double c[3]; double r; };
+
+Ball ball_of(const GeomView& g, int patch, int level, int ix, int iy) {
+    double h = 1.0 / (double)(1 << level);
+    double F[3], Fu[3], Fv[3];
+    Ball b;
+    eval_patch(g, patch, (ix + 0.5) * h, (iy + 0.5) * h, b.c, Fu, Fv);
+    double mx = 0.0;
+    for (int j = 0; j < 5; ++j)
+        for (int i = 0; i < 5; ++i) {
+            eval_patch(g, patch, (ix + 0.25 * i) * h, (iy + 0.25 * j) * h, F, Fu, Fv);
+            double d0 = F[0] - b.c[0], d1 = F[1] - b.c[1], d2 = F[2] - b.c[2];
+            double d = d0 * d0 + d1 * d1 + d2 * d2;
+            if (d > mx) mx = d;
+        }
+    b.r = std::sqrt(mx);
+    return b;
+}
+
+double ball_dist(const Ball& a, const Ball& b) {
+    double d0 = a.c[0] - b.c[0], d1 = a.c[1] - b.c[1], d2 = a.c[2] - b.c[2];
+    double d = std::sqrt(d0 * d0 + d1 * d1 + d2 * d2) - a.r - b.r;
+    return d > 0.0 ? d : 0.0;
+}
+
+int dihedral_corner(int k, int s, int t) {
+    double x, y;
+    dihedral(k, (double)s, (double)t, &x, &y);
+    int ix = (int)std::lround(x), iy = (int)std::lround(y);
+    if (ix == 0 && iy == 0) return 0;
+    if (ix == 1 && iy == 0) return 1;
+    if (ix == 1 && iy == 1) return 2;
+    return 3;
+}
+
+double corner_gap(const double* a, const double* b) {
+    double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+    return std::sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+
+}  // namespace
+
+std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params* prm, Plan& P) {
+    if (!patches || !prm || npatch <= 0) return "null patches/params or npatch <= 0";
+    const ibem_params& q = *prm;
+    if (q.kernel != IBEM_LAPLACE && q.kernel != IBEM_HELMHOLTZ) return "unknown kernel";
+    if (q.kernel == IBEM_HELMHOLTZ && !(q.kappa > 0.0)) return "Helmholtz needs kappa > 0";
+    if (q.p < 0 || q.p > IBEM_MAX_P) return "p must be in 0..4";
+    if (q.m < 0 || q.m > 10) return "m must be in 0..10";
+    if (q.q_cheb != 0 && (q.q_cheb < 2 || q.q_cheb > IBEM_MAX_Q)) return "q_cheb must be 0 or 2..12";
+    if (q.q_cheb != 0 && !(q.eta > 0.0)) return "eta must be > 0";
+    if (q.gauss_regular < 1 || q.gauss_regular > 16) return "gauss_regular must be in 1..16";
+    if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
+    P.prm = q;
+    P.npatch = npatch;
+    P.p = q.p;
+    P.m = q.m;
+    P.pp = q.p + 1;
+    P.nb = P.pp * P.pp;
+    P.ne1 = 1 << q.m;
+    P.n1 = P.ne1 + q.p;
+    P.Q = q.gauss_regular;
+    P.Qs = q.gauss_singular;
+    P.q = q.q_cheb;
+    P.q2 = P.q * P.q;
+    P.E = (int64_t)npatch * P.ne1 * P.ne1;
+    P.N = (int64_t)npatch * P.n1 * P.n1;
+    P.Nstar = P.E * P.nb;
+    P.nq = P.E * P.Q * P.Q;
+    P.level_off.assign(q.m + 2, 0);
+    for (int l = 0; l <= q.m; ++l) P.level_off[l + 1] = P.level_off[l] + (int64_t)npatch * ((int64_t)1 << (2 * l));
+    P.C = P.level_off[q.m + 1];
+
+    // patches
+    P.patches.clear();
+    P.knots.clear();
+    P.cpw.clear();
+    for (int i = 0; i < npatch; ++i) {
+        const ibem_patch& s = patches[i];
+        PatchDesc d;
+        std::memset(&d, 0, sizeof(d));
+        d.kind = s.kind;
+        if (s.kind == IBEM_PATCH_SPHERE_FACE) {
+            static const double frames[6][3][3] = {
+                {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},  {{-1, 0, 0}, {0, 0, 1}, {0, 1, 0}},
+                {{0, 1, 0}, {0, 0, 1}, {1, 0, 0}},  {{0, -1, 0}, {1, 0, 0}, {0, 0, 1}},
+                {{0, 0, 1}, {1, 0, 0}, {0, 1, 0}},  {{0, 0, -1}, {0, 1, 0}, {1, 0, 0}}};
+            if (s.face < 0 || s.face > 5) return "sphere face must be in 0..5";
+            if (!(s.radius > 0.0)) return "sphere radius must be > 0";
+            d.R = s.radius;
+            for (int k = 0; k < 3; ++k) {
+                d.c0[k] = s.center[k];
+                d.n[k] = frames[s.face][0][k];
+                d.t1[k] = frames[s.face][1][k];
+                d.t2[k] = frames[s.face][2][k];
+            }
+        } else if (s.kind == IBEM_PATCH_NURBS) {
+            if (s.deg_u < 1 || s.deg_u > IBEM_MAX_DEG || s.deg_v < 1 || s.deg_v > IBEM_MAX_DEG)
+                return "NURBS degree must be in 1..7";
+            if (s.ncp_u <= s.deg_u || s.ncp_v <= s.deg_v) return "NURBS needs ncp > degree";
+            if (!s.knots_u || !s.knots_v || !s.ctrl_xyz || !s.weights) return "NURBS arrays must be non-null";
+            int nku = s.ncp_u + s.deg_u + 1, nkv = s.ncp_v + s.deg_v + 1;
+            for (int k = 0; k + 1 < nku; ++k)
+                if (!(s.knots_u[k] <= s.knots_u[k + 1])) return "knots_u must be non-decreasing";
+            for (int k = 0; k + 1 < nkv; ++k)
+                if (!(s.knots_v[k] <= s.knots_v[k + 1])) return "knots_v must be non-decreasing";
+            if (s.knots_u[0] != 0.0 || s.knots_u[nku - 1] != 1.0 || s.knots_v[0] != 0.0 || s.knots_v[nkv - 1] != 1.0)
+                return "knot vectors must run from 0 to 1";
+            d.deg_u = s.deg_u; d.deg_v = s.deg_v; d.ncp_u = s.ncp_u; d.ncp_v = s.ncp_v;
+            d.knot_off_u = (int)P.knots.size();
+            P.knots.insert(P.knots.end(), s.knots_u, s.knots_u + nku);
+            d.knot_off_v = (int)P.knots.size();
+            P.knots.insert(P.knots.end(), s.knots_v, s.knots_v + nkv);
+            d.cp_off = (int)P.cpw.size();
+            for (int j = 0; j < s.ncp_u * s.ncp_v; ++j) {
+                double wt = s.weights[j];
+                if (!(wt > 0.0)) return "NURBS weights must be positive";
+                P.cpw.push_back(s.ctrl_xyz[3 * j] * wt);
+                P.cpw.push_back(s.ctrl_xyz[3 * j + 1] * wt);
+                P.cpw.push_back(s.ctrl_xyz[3 * j + 2] * wt);
+                P.cpw.push_back(wt);
+            }
+        } else {
+            return "unknown patch kind";
+        }
+        P.patches.push_back(d);
+    }
+    if (P.knots.empty()) P.knots.push_back(0.0);
+    if (P.cpw.empty()) P.cpw.push_back(0.0);
+    GeomView g = P.host_view();
+
+    // bounding balls of every cluster
+    std::vector<Ball> balls(P.C);
+    for (int patch = 0; patch < npatch; ++patch)
+        for (int l = 0; l <= P.m; ++l)
+            for (int iy = 0; iy < (1 << l); ++iy)
+                for (int ix = 0; ix < (1 << l); ++ix)
+                    balls[cluster_id(P, patch, l, ix, iy)] = ball_of(g, patch, l, ix, iy);
+    for (int64_t c = 0; c < P.C; ++c)
+        if (!std::isfinite(balls[c].r) || !(balls[c].r > 0.0)) return "degenerate patch (zero-size cluster)";
+
+    // block cluster tree
+    std::vector<std::pair<int32_t, int32_t>> near, far;
+    const bool compress = P.q > 0;
+    const double eta = q.eta;
+    std::vector<std::pair<int64_t, int64_t>> stack;
+    for (int i = 0; i < npatch; ++i)
+        for (int j = 0; j < npatch; ++j) stack.push_back({cluster_id(P, i, 0, 0, 0), cluster_id(P, j, 0, 0, 0)});
+    while (!stack.empty()) {
+        auto st = stack.back();
+        stack.pop_back();
+        int ps, ls, xs, ys, pt, lt, xt, yt;
+        cluster_of(P, st.first, &ps, &ls, &xs, &ys);
+        cluster_of(P, st.second, &pt, &lt, &xt, &yt);
+        const Ball &bs = balls[st.first], &bt = balls[st.second];
+        bool adm = false;
+        if (compress) {
+            double dist = ball_dist(bs, bt);
+            double diam = 2.0 * (bs.r > bt.r ? bs.r : bt.r);
+            adm = eta * diam < dist;
+        }
+        if (adm) {
+            far.push_back({(int32_t)st.first, (int32_t)st.second});
+        } else if (ls == P.m) {
+            near.push_back({(int32_t)(st.first - P.level_off[P.m]), (int32_t)(st.second - P.level_off[P.m])});
+        } else {
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b)
+                    stack.push_back({cluster_id(P, ps, ls + 1, 2 * xs + (a & 1), 2 * ys + (a >> 1)),
+                                     cluster_id(P, pt, lt + 1, 2 * xt + (b & 1), 2 * yt + (b >> 1))});
+        }
+    }
+    std::sort(near.begin(), near.end());
+    std::sort(far.begin(), far.end());
+    P.n_near = (int64_t)near.size();
+    P.n_far = (int64_t)far.size();
+
+    // near-pair classes
+    auto corners = [&](int64_t e, double out[4][3]) {
+        int patch, ix, iy;
+        element_of(P, e, &patch, &ix, &iy);
+        double h = 1.0 / P.ne1, Fu[3], Fv[3];
+        const int cs[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+        for (int k = 0; k < 4; ++k) eval_patch(g, patch, (ix + cs[k][0]) * h, (iy + cs[k][1]) * h, out[k], Fu, Fv);
+    };
+    P.near_ptr.assign(P.E + 1, 0);
+    P.near_src.resize(P.n_near);
+    P.near_cls.resize(P.n_near);
+    P.near_orient.resize(P.n_near);
+    for (int k = 0; k < 5; ++k) P.n_cls[k] = 0;
+    for (int64_t k = 0; k < P.n_near; ++k) {
+        int64_t t = near[k].first, s = near[k].second;
+        P.near_ptr[t + 1]++;
+        P.near_src[k] = (int32_t)s;
+        int cls = CLS_REGULAR, orient = 0;
+        if (t == s) {
+            cls = CLS_IDENTICAL;
+        } else {
+            const Ball &bA = balls[P.level_off[P.m] + t], &bB = balls[P.level_off[P.m] + s];
+            double diam = 2.0 * (bA.r > bB.r ? bA.r : bB.r);
+            double tol = 1e-10 * diam;
+            double CA[4][3], CB[4][3];
+            corners(t, CA);
+            corners(s, CB);
+            int matches = 0;
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    if (corner_gap(CA[i], CB[j]) <= tol) ++matches;
+            if (matches >= 1) {
+                cls = matches >= 2 ? CLS_EDGE : CLS_VERTEX;
+                const int need[2][2] = {{0, 0}, {0, 1}};
+                int nneed = cls == CLS_EDGE ? 2 : 1;
+                bool found = false;
+                for (int ka = 0; ka < 8 && !found; ++ka)
+                    for (int kb = 0; kb < 8 && !found; ++kb) {
+                        bool ok = true;
+                        for (int r = 0; r < nneed; ++r) {
+                            int ca = dihedral_corner(ka, need[r][0], need[r][1]);
+                            int cb = dihedral_corner(kb, need[r][0], need[r][1]);
+                            if (corner_gap(CA[ca], CB[cb]) > tol) { ok = false; break; }
+                        }
+                        if (ok) { orient = 8 * ka + kb; found = true; }
+                    }
+                if (!found) return "touching element pair without a canonical orientation";
+            } else {
+                double dist = ball_dist(bA, bB);
+                cls = dist < 0.5 * diam ? CLS_SUBDIV : CLS_REGULAR;
+            }
+        }
+        P.near_cls[k] = cls;
+        P.near_orient[k] = orient;
+        P.n_cls[cls]++;
+    }
+    for (int64_t e = 0; e < P.E; ++e) P.near_ptr[e + 1] += P.near_ptr[e];
+    P.far_ptr.assign(P.C + 1, 0);
+    P.far_src.resize(P.n_far);
+    for (int64_t k = 0; k < P.n_far; ++k) {
+        P.far_ptr[far[k].first + 1]++;
+        P.far_src[k] = far[k].second;
+    }
+    for (int64_t c = 0; c < P.C; ++c) P.far_ptr[c + 1] += P.far_ptr[c];
+    return "";
+}
+
+}  // namespace ibem

@@ -1,0 +1,249 @@
+"""ctypes binding of libibem (declared in include/ibem.h).
+
+Argument marshalling only: every function below has the name of the C entry
+point it calls, checks nothing beyond what ctypes needs, and raises
+``IbemError`` (with the library's last-error text) when the call does not
+return IBEM_OK.  Device buffers are passed as ``torch.Tensor`` objects (their
+``data_ptr()`` is handed to the library); host buffers as numpy arrays.
+
+Loading fails loudly: if libibem.so has not been built (see ``build.py``) the
+import raises, and there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+IBEM_OK = 0
+IBEM_ERR_NOCONV = 5
+IBEM_PATCH_NURBS, IBEM_PATCH_SPHERE_FACE = 0, 1
+IBEM_LAPLACE, IBEM_HELMHOLTZ = 0, 1
+IBEM_FP64, IBEM_FP32 = 0, 1
+IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI = 0, 1
+
+EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
+            "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
+            "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
+            "ibem_profile_read")
+
+
+class IbemError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status, message))
+        self.status = status
+
+
+class ibem_patch(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("deg_u", ctypes.c_int), ("deg_v", ctypes.c_int),
+                ("ncp_u", ctypes.c_int), ("ncp_v", ctypes.c_int),
+                ("knots_u", ctypes.POINTER(ctypes.c_double)), ("knots_v", ctypes.POINTER(ctypes.c_double)),
+                ("ctrl_xyz", ctypes.POINTER(ctypes.c_double)), ("weights", ctypes.POINTER(ctypes.c_double)),
+                ("face", ctypes.c_int), ("radius", ctypes.c_double), ("center", ctypes.c_double * 3)]
+
+
+class ibem_params(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("kappa", ctypes.c_double), ("p", ctypes.c_int), ("m", ctypes.c_int),
+                ("q_cheb", ctypes.c_int), ("eta", ctypes.c_double), ("gauss_regular", ctypes.c_int),
+                ("gauss_singular", ctypes.c_int)]
+
+
+class ibem_info(ctypes.Structure):
+    _fields_ = [("ndof", ctypes.c_int64), ("ndof_super", ctypes.c_int64), ("n_elements", ctypes.c_int64),
+                ("n_clusters", ctypes.c_int64), ("n_quad_points", ctypes.c_int64), ("n_near", ctypes.c_int64),
+                ("n_far", ctypes.c_int64), ("n_near_singular", ctypes.c_int64 * 4),
+                ("bytes_near", ctypes.c_int64), ("bytes_far", ctypes.c_int64), ("assembled", ctypes.c_int)]
+
+
+class ibem_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+class ibem_profile_data(ctypes.Structure):
+    _fields_ = [("applications", ctypes.c_int64), ("launches", ctypes.c_int64), ("ms", ctypes.c_double * 6)]
+
+
+PHASES = ("lift", "upward", "coupling", "downward", "near", "restrict")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libibem.so is not built; run paper_1708_09162_gb300/build.py (no fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "ibem_create": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params), P, ctypes.POINTER(P)]),
+        "ibem_destroy": (I32, [P]),
+        "ibem_get_info": (I32, [P, ctypes.POINTER(ibem_info)]),
+        "ibem_assemble": (I32, [P]),
+        "ibem_quad_points": (I32, [P, P]),
+        "ibem_rhs": (I32, [P, P, I32, P]),
+        "ibem_matvec": (I32, [P, P, P, I32, I32]),
+        "ibem_matvec_host": (I32, [P, P, P, I32, I32]),
+        "ibem_solve": (I32, [P, P, P, I32, ctypes.c_double, I32, I32, I32, ctypes.POINTER(ibem_solve_info)]),
+        "ibem_potential": (I32, [P, P, I32, P, I64, P]),
+        "ibem_block_tree": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
+                                  ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
+        "ibem_profile_enable": (I32, [P, I32]),
+        "ibem_profile_read": (I32, [P, ctypes.POINTER(ibem_profile_data)]),
+        "ibem_last_error": (ctypes.c_char_p, [P]),
+        "ibem_status_string": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status, handle=None):
+    if status != IBEM_OK:
+        msg = _lib.ibem_last_error(handle).decode()
+        raise IbemError(_lib.ibem_status_string(status).decode(), msg)
+
+
+def _dptr(t):
+    """Device pointer of a CUDA tensor (must be contiguous float64)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a):
+    """Host pointer of a float64 numpy array or a CPU (e.g. pinned) torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("expected a C-contiguous float64 numpy array")
+        return a.ctypes.data_as(ctypes.c_void_p)
+    if a.is_cuda or not a.is_contiguous() or str(a.dtype) != "torch.float64":
+        raise ValueError("expected a contiguous float64 host tensor")
+    return ctypes.c_void_p(a.data_ptr())
+
+
+# ---- patch and parameter builders -------------------------------------------------
+def sphere_patches(radius=1.0, center=(0.0, 0.0, 0.0)):
+    """The six analytic cube-sphere faces of a sphere."""
+    arr = (ibem_patch * 6)()
+    for f in range(6):
+        arr[f].kind = IBEM_PATCH_SPHERE_FACE
+        arr[f].face = f
+        arr[f].radius = radius
+        for k in range(3):
+            arr[f].center[k] = center[k]
+    return arr
+
+
+def nurbs_patches(specs):
+    """specs: list of (deg_u, deg_v, knots_u, knots_v, ctrl [ncp_v][ncp_u][3], weights [ncp_v][ncp_u])."""
+    arr = (ibem_patch * len(specs))()
+    keep = []
+    for i, (du, dv, ku, kv, ctrl, w) in enumerate(specs):
+        ku, kv = np.ascontiguousarray(ku, np.float64), np.ascontiguousarray(kv, np.float64)
+        ctrl, w = np.ascontiguousarray(ctrl, np.float64), np.ascontiguousarray(w, np.float64)
+        keep += [ku, kv, ctrl, w]
+        arr[i].kind = IBEM_PATCH_NURBS
+        arr[i].deg_u, arr[i].deg_v = du, dv
+        arr[i].ncp_u, arr[i].ncp_v = ctrl.shape[1], ctrl.shape[0]
+        arr[i].knots_u = ku.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].knots_v = kv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].ctrl_xyz = ctrl.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr[i].weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    arr._keep = keep
+    return arr
+
+
+def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8):
+    return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular)
+
+
+# ---- entry points --------------------------------------------------------------------
+def ibem_create(patches, params, stream=None):
+    """Returns an opaque handle (ctypes.c_void_p).  ``stream``: a torch.cuda.Stream or None."""
+    h = ctypes.c_void_p()
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.ibem_create(patches, len(patches), ctypes.byref(params), sp, ctypes.byref(h)))
+    return h
+
+
+def ibem_destroy(h):
+    _check(_lib.ibem_destroy(h), h)
+
+
+def ibem_get_info(h):
+    info = ibem_info()
+    _check(_lib.ibem_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def ibem_assemble(h):
+    _check(_lib.ibem_assemble(h), h)
+
+
+def ibem_quad_points(h, xyz):
+    _check(_lib.ibem_quad_points(h, _dptr(xyz)), h)
+
+
+def ibem_rhs(h, g, nrhs, b):
+    _check(_lib.ibem_rhs(h, _dptr(g), nrhs, _dptr(b)), h)
+
+
+def ibem_matvec(h, x, y, nrhs, precision=IBEM_FP64):
+    _check(_lib.ibem_matvec(h, _dptr(x), _dptr(y), nrhs, precision), h)
+
+
+def ibem_matvec_host(h, x, y, nrhs, precision=IBEM_FP64):
+    _check(_lib.ibem_matvec_host(h, _hptr(x), _hptr(y), nrhs, precision), h)
+
+
+def ibem_solve(h, b, w, nrhs, rtol=1e-8, maxit=1000, precond=IBEM_PRECOND_JACOBI, precision=IBEM_FP64,
+               check=True):
+    info = ibem_solve_info()
+    s = _lib.ibem_solve(h, _dptr(b), _dptr(w), nrhs, rtol, maxit, precond, precision, ctypes.byref(info))
+    if check:
+        _check(s, h)
+    return info if check else (s, info)
+
+
+def ibem_potential(h, w, nrhs, pts, u):
+    _check(_lib.ibem_potential(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
+
+
+def ibem_block_tree(patches, params):
+    """Host only.  Returns (near [n_near, 8] int32, far [n_far, 8] int32)."""
+    nn, nf = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.ibem_block_tree(patches, len(patches), ctypes.byref(params), ctypes.byref(nn), None,
+                                ctypes.byref(nf), None))
+    near = np.zeros((nn.value, 8), dtype=np.int32)
+    far = np.zeros((nf.value, 8), dtype=np.int32)
+    _check(_lib.ibem_block_tree(patches, len(patches), ctypes.byref(params), ctypes.byref(nn),
+                                near.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf),
+                                far.ctypes.data_as(ctypes.c_void_p)))
+    return near, far
+
+
+def ibem_profile_enable(h, enable=True):
+    _check(_lib.ibem_profile_enable(h, 1 if enable else 0), h)
+
+
+def ibem_profile_read(h):
+    """Returns dict(applications, launches, ms={phase: summed ms})."""
+    d = ibem_profile_data()
+    _check(_lib.ibem_profile_read(h, ctypes.byref(d)), h)
+    return {"applications": d.applications, "launches": d.launches,
+            "ms": {name: d.ms[i] for i, name in enumerate(PHASES)}}
+
+
+def ibem_last_error(h=None):
+    return _lib.ibem_last_error(h).decode()
+
+
+def ibem_status_string(s):
+    return _lib.ibem_status_string(s).decode()

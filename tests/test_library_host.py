@@ -1,0 +1,87 @@
+"""CPU tests of libibem: it builds, loads, exports every symbol of
+include/ibem.h, and its host-side block cluster tree and pair classification
+equal the oracle's exactly (no device calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ibem():
+    from paper_1708_09162_gb300 import build
+    build.build()
+    from paper_1708_09162_gb300 import ibem as mod
+    return mod
+
+
+def test_exports_every_declared_symbol(ibem):
+    import ctypes
+    hdr = open(os.path.join(ROOT, "include", "ibem.h")).read()
+    declared = set(re.findall(r"\b(ibem_[a-z_]+)\s*\(", hdr))
+    assert declared == set(ibem.EXPORTED)
+    lib = ctypes.CDLL(ibem.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _oracle_lists(patches_py, p, m, eta):
+    from oracle import galerkin, tree
+    disc = galerkin.Discretisation(patches_py, p, m, galerkin.LaplaceKernel())
+    near, far = tree.block_cluster_tree(patches_py, m, eta)
+    cls_code = {"identical": 0, "edge": 1, "vertex": 2, "nearsing": 3, "regular": 4}
+    rows = []
+    for s, t in near:
+        eA, eB = tree.element_index(s, m), tree.element_index(t, m)
+        c, ka, kb = disc.pair_class(eA, eB)
+        rows.append((s[0], s[2], s[3], t[0], t[2], t[3], cls_code[c], 8 * ka + kb))
+    frows = [tuple(s) + tuple(t) for s, t in far]
+    return sorted(rows), sorted(frows)
+
+
+@pytest.mark.parametrize("p,m", [(2, 2), (1, 3)])
+def test_block_tree_equals_oracle_sphere(ibem, sphere, p, m):
+    near, far = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=6, eta=1.6))
+    onear, ofar = _oracle_lists(sphere, p, m, 1.6)
+    assert sorted(map(tuple, near.tolist())) == onear
+    assert sorted(map(tuple, far.tolist())) == ofar
+
+
+def test_block_tree_dense_mode_has_all_pairs(ibem):
+    near, far = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(1, 1, q_cheb=0))
+    assert far.shape[0] == 0 and near.shape[0] == 24 * 24
+
+
+def test_block_tree_nurbs_cylinder(ibem):
+    # two rational-quadratic quarter cylinders side by side (a half cylinder)
+    from oracle import geometry
+    R, H = 1.0, 1.5
+    a = geometry.quarter_cylinder(R, H)
+    ctrl2 = a.ctrl.copy()
+    ctrl2[:, :, 0], ctrl2[:, :, 1] = -a.ctrl[:, :, 1], a.ctrl[:, :, 0]   # rotate by 90 degrees
+    b = geometry.NurbsPatch(2, 1, a.knots_u, a.knots_v, ctrl2, a.weights)
+    specs = [(2, 1, a.knots_u, a.knots_v, a.ctrl, a.weights), (2, 1, b.knots_u, b.knots_v, b.ctrl, b.weights)]
+    pats = ibem.nurbs_patches(specs)
+    near, far = ibem.ibem_block_tree(pats, ibem.make_params(1, 3, q_cheb=4, eta=1.0))
+    onear, ofar = _oracle_lists([a, b], 1, 3, 1.0)
+    assert sorted(map(tuple, far.tolist())) == ofar
+    # classes must agree; orientation codes too
+    assert sorted(map(tuple, near.tolist())) == onear
+
+
+def test_invalid_arguments_rejected(ibem):
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(9, 2))
+    assert "p must be" in str(ei.value)
+    pats = ibem.sphere_patches()
+    pats[0].face = 7
+    with pytest.raises(ibem.IbemError):
+        ibem.ibem_block_tree(pats, ibem.make_params(1, 1))
+    bad = ibem.nurbs_patches([(2, 1, [0, 0, 0, 1, 1, 1], [0, 0, 1, 1], np.zeros((2, 3, 3)), -np.ones((2, 3)))])
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_block_tree(bad, ibem.make_params(1, 1))
+    assert "weights" in str(ei.value)
+    assert ibem.ibem_status_string(5) == "IBEM_ERR_NOCONV"

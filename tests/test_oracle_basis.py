@@ -115,3 +115,18 @@ def test_space_dimensions_match_table():
     assert bspline.space_dimension(6, 3, 5) == 7350
     assert bspline.space_dimension(6, 2, 6) == 26136
     assert bspline.space_dimension(6, 2, 7) == 101400
+
+
+def test_local_window_equals_full_knot_vector(sphere):
+    # the element-local evaluation used by the mesh equals the full recursion
+    from oracle.mesh import Mesh
+    me = Mesh(sphere, 3, 3)
+    rng = np.random.default_rng(9)
+    for e in (0, 5, 27, 63):
+        st = rng.random((40, 2))
+        uv = me.to_patch(e, st)
+        _, ix, iy = me.element(e)
+        full_u = bspline.basis_values(me.knots, 3, uv[:, 0])[:, ix:ix + 4]
+        full_v = bspline.basis_values(me.knots, 3, uv[:, 1])[:, iy:iy + 4]
+        want = (full_v[:, :, None] * full_u[:, None, :]).reshape(40, -1)
+        assert np.array_equal(me.local_basis(e, uv), want)
