@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -341,6 +342,10 @@ def ours(args, rank, world, local_rank):
 
 def main():
     args = parse()
+    if args.m is not None:
+        WORKLOAD["m"] = args.m
+        WORKLOAD["workload"] = "laplace-sphere-p%d-m%d-q%d-eta%g" % (WORKLOAD["p"], args.m, WORKLOAD["q_cheb"],
+                                                                    WORKLOAD["eta"])
     if args.oracle_worker:
         oracle_worker(args.oracle_worker)
         return
