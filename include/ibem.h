@@ -89,7 +89,17 @@ typedef struct {
     double eta;          /* admissible iff eta * max(diam) < dist (eta = 1/mu, Def. 4.1) */
     int gauss_regular;   /* Gauss points per direction, regular pairs (default 8)   */
     int gauss_singular;  /* Gauss points per variable, Duffy rules (default 8)      */
+    int fp64_coupling;   /* storage and arithmetic of the FP64 operator's coupling:
+                            IBEM_COUPLING_DF (0, default) or IBEM_COUPLING_NATIVE (1) */
 } ibem_params;
+
+/* FP64 coupling variants.  GB300 executes FP64 FMA at 1/64 of the FP32 rate, so
+ * by default the coupling matrices are stored as unevaluated float pairs
+ * (hi + lo, 8 bytes per entry) and applied with exact FP32 products and
+ * compensated sums (about 48 significant bits, relative error ~1e-14);
+ * NATIVE stores doubles and uses FP64 FMA.  Both reproduce the FP64 oracle to
+ * 1e-12. */
+enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1 };
 
 typedef struct {
     int64_t ndof;          /* dim S_{p,m} = n (2^m + p)^2                          */
@@ -184,6 +194,19 @@ ibem_status ibem_profile_enable(ibem_handle* h, int enable);
 
 /* Synchronise the stream, return the sums since the last read/enable, clear. */
 ibem_status ibem_profile_read(ibem_handle* h, ibem_profile_data* out);
+
+/* Device-side waits.  Kernels that wait on asynchronous copies poll an
+ * mbarrier at most `limit` times (default 2^26); a wait that runs out makes the
+ * kernel record IBEM_DEVICE_TIMEOUT in the handle's status word, wait (bounded)
+ * for its copies in flight and return without finishing its output, so the
+ * CUDA context stays usable.  limit = 0 makes every such wait fail at once
+ * (used to test the failure path). */
+enum { IBEM_DEVICE_OK = 0, IBEM_DEVICE_TIMEOUT = 1 };
+ibem_status ibem_set_wait_limit(ibem_handle* h, long long limit);
+
+/* Synchronise the stream, return the status word (IBEM_DEVICE_* bits) that the
+ * kernels recorded since the last call, and clear it. */
+ibem_status ibem_device_status(ibem_handle* h, int* status);
 
 /* Host-only: build the block cluster tree without a GPU and return its lists.
  * Call once with null arrays to get the counts.  near: [n_near][8] int32 =

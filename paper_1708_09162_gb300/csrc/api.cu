@@ -94,9 +94,9 @@ void free_handle(ibem_handle* h) {
                     h->d_phi_sub, h->d_rule[0], h->d_rule[1], h->d_rule[2], h->d_M, h->d_S, h->d_near_ptr,
                     h->d_near_src, h->d_near_tgt, h->d_near_cls, h->d_near_orient, h->d_pairs_by_cls[0],
                     h->d_pairs_by_cls[1], h->d_pairs_by_cls[2], h->d_pairs_by_cls[3], h->d_pairs_by_cls[4],
-                    h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_far_rows,
+                    h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_Kdf, h->d_xh2, h->d_far_rows,
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
-                    h->d_solver, h->d_red};
+                    h->d_solver, h->d_red, h->d_status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -285,6 +285,7 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
     std::vector<int32_t> ftgt(P.n_far);
     for (int64_t c = 0; c < P.C; ++c) {
         if (P.far_ptr[c + 1] > P.far_ptr[c]) h->far_rows.push_back((int32_t)c);
+        if (P.far_ptr[c + 1] - P.far_ptr[c] > h->max_far_row) h->max_far_row = (int)(P.far_ptr[c + 1] - P.far_ptr[c]);
         for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k) ftgt[k] = (int32_t)c;
     }
     TRY(upload(&h->d_far_ptr, P.far_ptr, st), "upload far ptr");
@@ -300,6 +301,8 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
     }
     TRY(cudaMalloc(&h->d_diag, (size_t)P.N * sizeof(double)), "alloc diag");
     TRY(cudaMalloc(&h->d_red, 64 * sizeof(double)), "alloc red");
+    TRY(cudaMalloc(&h->d_status, sizeof(int)), "alloc status");
+    TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int), st), "clear status");
     TRY(cudaMallocHost(&h->h_red, 64 * sizeof(double)), "alloc pinned");
     TRY(launch_geometry_tables(h), "geometry tables");
     TRY(cudaStreamSynchronize(st), "create sync");
@@ -349,7 +352,11 @@ ibem_status ibem_assemble(ibem_handle* h) {
         if ((e = cudaMalloc(&h->d_near32, nn * sizeof(float)))) return cuda_fail(h, e, "alloc near blocks fp32");
         if (P.n_far > 0) {
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
-            if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
+            if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
+                if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
+            } else {
+                if ((e = cudaMalloc(&h->d_Kdf, nk * sizeof(float2)))) return cuda_fail(h, e, "alloc coupling matrices");
+            }
         }
     }
     if ((e = launch_near_assembly(h))) return cuda_fail(h, e, "near assembly");
@@ -458,6 +465,23 @@ ibem_status ibem_profile_read(ibem_handle* h, ibem_profile_data* out) {
     out->launches = h->launches;
     h->applications = 0;
     h->launches = 0;
+    return IBEM_OK;
+}
+
+ibem_status ibem_set_wait_limit(ibem_handle* h, long long limit) {
+    if (!h || limit < 0) return fail(h, IBEM_ERR_ARG, "null handle or negative limit");
+    h->wait_limit = limit;
+    return IBEM_OK;
+}
+
+ibem_status ibem_device_status(ibem_handle* h, int* status) {
+    if (!h || !status) return fail(h, IBEM_ERR_ARG, "null handle or output");
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaMemcpyAsync(status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream)))
+        return cuda_fail(h, e, "status read");
+    if ((e = cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream))) return cuda_fail(h, e, "status clear");
+    if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "status sync");
     return IBEM_OK;
 }
 

@@ -256,9 +256,12 @@ struct ibem_handle {
     int64_t* d_far_ptr = nullptr;
     int32_t* d_far_src = nullptr;
     int32_t* d_far_tgt = nullptr;
-    double* d_K = nullptr;          // [n_far][kpt][4 q2]: entry (a, b = s + 4k) at [k][4a + s]
+    double* d_K = nullptr;          // [n_far][kpt][4 q2]: entry (a, b = s + 4k) at [k][4a + s] (native)
+    float2* d_Kdf = nullptr;        // same layout, (hi, lo) float pairs (double-float coupling)
+    float2* d_xh2 = nullptr;        // forward moments split into (hi, lo) float pairs
     int kpt = 0;
     std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
+    int max_far_row = 0;            // longest far list
     int32_t* d_far_rows = nullptr;
 
     // work vectors (sized for ws_nrhs right-hand sides)
@@ -277,6 +280,10 @@ struct ibem_handle {
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches = 0, applications = 0;
+
+    // device-side waits: bound (polls) and status word (IBEM_DEVICE_* bits)
+    long long wait_limit = 1LL << 26;
+    int* d_status = nullptr;
 };
 
 namespace ibem {

@@ -152,6 +152,154 @@ __global__ void coupling64_kernel(const int32_t* __restrict__ rows, const int64_
     if (active && s == 0) yh[(r * C + sigma) * q2 + a] = acc;
 }
 
+// ---- coupling, FP64-accurate in double-float arithmetic on the FP32 pipe -------
+// Same thread layout and K layout as coupling64_kernel.  K = kh + kl and
+// x^ = xh + xl are float pairs; kh*xh is formed exactly (p + e, e from an FMA),
+// the cross terms kh*xl + kl*xh are added to e, and (p, e) is accumulated with
+// Knuth's TwoSum.  Each block's double-float partial sum is folded into an FP64
+// accumulator, so FP64 work is a few operations per block instead of one FMA
+// per matrix entry.
+// x^ (rows of q2 doubles) -> (hi, lo) float pairs in rows of q2p >= q2 (q2p even,
+// so every row starts on a 16-byte boundary for the bulk copies).
+__global__ void split_kernel(int64_t rows, int q2, int q2p, const double* __restrict__ x, float2* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * q2p) return;
+    int64_t row = i / q2p;
+    int c = (int)(i % q2p);
+    double v = c < q2 ? x[row * q2 + c] : 0.0;
+    float hi = (float)v;
+    out[i] = make_float2(hi, (float)(v - (double)hi));
+}
+
+// The CTA of target cluster sigma streams the coupling matrices of its row -
+// contiguous in HBM - through a ring of NST shared-memory stages with 1-D bulk
+// copies (cp.async.bulk, one elected thread) completed on mbarriers; all
+// threads compute from shared memory, so the copies of the next NST blocks are
+// in flight while one block is consumed.  Every wait is bounded by
+// `wait_limit` polls; on a timeout the CTA records IBEM_DEVICE_TIMEOUT in
+// *status, waits (bounded) for its copies in flight and returns.
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ inline bool mbar_wait(uint64_t* bar, unsigned parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int KPT, int NST>
+__global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
+                                   const int32_t* __restrict__ fsrc, const float2* __restrict__ K, int q2,
+                                   int q2p, int maxrow, int64_t C, const float2* __restrict__ xh,
+                                   double* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    // [0, 128): mbarriers; then the row's source clusters; then NST stages of
+    // (coupling block, source moments)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    int32_t* srcs = reinterpret_cast<int32_t*>(smem + 128);
+    const int stride = 4 * q2;
+    const int belems = KPT * stride;
+    const int selems = belems + q2p;
+    float2* stage = reinterpret_cast<float2*>(smem + 128 + (((size_t)maxrow * 4 + 15) / 16) * 16);
+    const unsigned kbytes = (unsigned)belems * 8u, xbytes = (unsigned)q2p * 8u;
+    const int sigma = rows[blockIdx.x];
+    const int64_t r = blockIdx.y;
+    const int t = threadIdx.x, s = t & 3, a = t >> 2;
+    const bool active = t < stride;
+    const int64_t b0 = fptr[sigma];
+    const int n = (int)(fptr[sigma + 1] - b0);
+    const float2* xr = xh + r * C * q2p;
+    for (int j = t; j < n; j += blockDim.x) srcs[j] = fsrc[b0 + j];
+    if (t == 0) {
+        for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int i = 0; i < NST && i < n; ++i) {
+            float2* dst = stage + (size_t)i * selems;
+            mbar_expect_tx(&full[i], kbytes + xbytes);
+            bulk_load(dst, K + (b0 + i) * (int64_t)belems, kbytes, &full[i]);
+            bulk_load(dst + belems, xr + (int64_t)srcs[i] * q2p, xbytes, &full[i]);
+        }
+    }
+    double acc = 0.0;
+    int i = 0;
+    bool failed = false;
+    for (; i < n; ++i) {
+        const int st = i % NST;
+        const bool ok = mbar_wait(&full[st], (unsigned)((i / NST) & 1), wait_limit);
+        if (ok && active) {
+            const float2* Kb = stage + (size_t)st * selems + t;
+            const float2* xt = stage + (size_t)st * selems + belems;
+            float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int kk = 0; kk < KPT; ++kk) {
+                int b = s + 4 * kk;
+                if (b < q2) {
+                    float2 kv = Kb[kk * stride];
+                    float2 x = xt[b];
+                    float p = kv.x * x.x;
+                    float e = fmaf(kv.x, x.x, -p);
+                    e = fmaf(kv.x, x.y, e);
+                    e = fmaf(kv.y, x.x, e);
+                    float tsum = hi + p;
+                    float z = tsum - hi;
+                    float err = (hi - (tsum - z)) + (p - z);
+                    hi = tsum;
+                    lo += err + e;
+                }
+            }
+            acc += (double)hi + (double)lo;
+        }
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        if (t == 0 && i + NST < n) {
+            float2* dst = stage + (size_t)st * selems;
+            mbar_expect_tx(&full[st], kbytes + xbytes);
+            bulk_load(dst, K + (b0 + i + NST) * (int64_t)belems, kbytes, &full[st]);
+            bulk_load(dst + belems, xr + (int64_t)srcs[i + NST] * q2p, xbytes, &full[st]);
+        }
+    }
+    if (failed) {
+        if (t == 0) {
+            atomicOr(status, 1);
+            // drain: every issued copy must land before the CTA's shared memory is released
+            for (int j = i; j < n && j < i + NST; ++j) mbar_wait(&full[j % NST], (unsigned)((j / NST) & 1), 1LL << 24);
+        }
+        __syncthreads();
+        return;
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (active && s == 0) yh[(r * C + sigma) * q2 + a] = acc;
+}
+
 // ---- coupling, FP32, kernel generated on the fly ------------------------------
 // src32[t][b] = (x, y, z, k_b x^_b / (4 pi)) of every cluster; one CTA per target
 // cluster; thread (g, a) handles target point a against blocks g, g + NS, ...;
@@ -277,7 +425,8 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     if (nrhs <= h->ws_nrhs) return cudaSuccess;
     Plan& P = h->P;
     cudaFree(h->d_xs); cudaFree(h->d_ys); cudaFree(h->d_xh); cudaFree(h->d_yh);
-    cudaFree(h->d_xs32); cudaFree(h->d_src32);
+    cudaFree(h->d_xs32); cudaFree(h->d_src32); cudaFree(h->d_xh2);
+    h->d_xh2 = nullptr;
     h->d_xs = h->d_ys = h->d_xh = h->d_yh = nullptr;
     h->d_xs32 = nullptr;
     h->d_src32 = nullptr;
@@ -288,6 +437,7 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     if ((e = cudaMalloc(&h->d_ys, ns * sizeof(double)))) return e;
     if ((e = cudaMalloc(&h->d_xh, nh * sizeof(double)))) return e;
     if ((e = cudaMalloc(&h->d_yh, nh * sizeof(double)))) return e;
+    if ((e = cudaMalloc(&h->d_xh2, (size_t)nrhs * P.C * ((P.q2 + 1) & ~1) * sizeof(float2) + 16))) return e;
     if ((e = cudaMalloc(&h->d_xs32, ns * sizeof(float)))) return e;
     if ((e = cudaMalloc(&h->d_src32, (size_t)P.C * (P.q2 > 0 ? P.q2 : 1) * sizeof(float4)))) return e;
     h->ws_nrhs = nrhs;
@@ -363,11 +513,45 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
                         h->d_yh + (size_t)r * P.C * q2);
                     h->launches += 2;
                 }
-            } else {
+            } else if (h->d_K) {
                 int threads = ((4 * q2 + 31) / 32) * 32;
                 coupling64_kernel<<<dim3(nrows, R), threads, 0, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src, h->d_K,
                                                                       q2, h->kpt, P.C, h->d_xh, h->d_yh);
                 h->launches++;
+            } else {
+                int threads = ((4 * q2 + 31) / 32) * 32;
+                const int q2p = (q2 + 1) & ~1;
+                split_kernel<<<nblk(R * P.C * q2p, T), T, 0, st>>>(R * P.C, q2, q2p, h->d_xh, h->d_xh2);
+                dim3 grid(nrows, R);
+                const size_t sbytes = ((size_t)h->kpt * 4 * q2 + q2p) * sizeof(float2);
+                const size_t head = 128 + (((size_t)h->max_far_row * 4 + 15) / 16) * 16;
+#define IBEM_DF_LAUNCH(K_, N_)                                                                                   \
+    {                                                                                                            \
+        size_t sm = head + (size_t)(N_)*sbytes;                                                                  \
+        if ((e = cudaFuncSetAttribute(coupling_df_kernel<K_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                      (int)sm)))                                                                 \
+            return e;                                                                                            \
+        coupling_df_kernel<K_, N_><<<grid, threads, sm, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src,         \
+                                                              h->d_Kdf, q2, q2p, h->max_far_row, P.C, h->d_xh2, \
+                                                              h->d_yh, h->wait_limit, h->d_status);              \
+    }                                                                                                            \
+    break;
+                switch (h->kpt) {
+                    case 1: IBEM_DF_LAUNCH(1, 8)
+                    case 3: IBEM_DF_LAUNCH(3, 8)
+                    case 4: IBEM_DF_LAUNCH(4, 6)
+                    case 7: IBEM_DF_LAUNCH(7, 4)
+                    case 9: IBEM_DF_LAUNCH(9, 4)
+                    case 13: IBEM_DF_LAUNCH(13, 3)
+                    case 16: IBEM_DF_LAUNCH(16, 2)
+                    case 21: IBEM_DF_LAUNCH(21, 2)
+                    case 25: IBEM_DF_LAUNCH(25, 2)
+                    case 31: IBEM_DF_LAUNCH(31, 1)
+                    case 36: IBEM_DF_LAUNCH(36, 1)
+                    default: return cudaErrorInvalidValue;
+                }
+#undef IBEM_DF_LAUNCH
+                h->launches += 2;
             }
         }
         PhaseTimer pt(h, 3);

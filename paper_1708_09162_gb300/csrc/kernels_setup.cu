@@ -260,9 +260,10 @@ __global__ void near_singular_kernel(GeomView g, const int32_t* __restrict__ lis
 }
 
 // ---- far field: coupling matrices -----------------------------------------
+// Stored as doubles (native) or as float pairs hi = fl(K), lo = fl(K - hi).
 __global__ void far_assemble_kernel(int64_t n_far, const int32_t* __restrict__ ftgt,
                                     const int32_t* __restrict__ fsrc, const double* __restrict__ igeo,
-                                    int q2, int kpt, double* __restrict__ K) {
+                                    int q2, int kpt, double* __restrict__ K, float2* __restrict__ Kdf) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t per = (int64_t)kpt * 4 * q2;
     if (idx >= n_far * per) return;
@@ -277,7 +278,12 @@ __global__ void far_assemble_kernel(int64_t n_far, const int32_t* __restrict__ f
         double d0 = A[0] - B[0], d1 = A[1] - B[1], d2 = A[2] - B[2];
         v = A[3] * B[3] / (4.0 * IBEM_PI * sqrt(d0 * d0 + d1 * d1 + d2 * d2));
     }
-    K[idx] = v;
+    if (K) {
+        K[idx] = v;
+    } else {
+        float hi = (float)v;
+        Kdf[idx] = make_float2(hi, (float)(v - (double)hi));
+    }
 }
 
 // ---- Jacobi diagonal of T A_near T^T ---------------------------------------
@@ -396,7 +402,7 @@ cudaError_t launch_far_assembly(ibem_handle* h) {
     if (P.n_far == 0) return cudaSuccess;
     int64_t total = P.n_far * (int64_t)h->kpt * 4 * P.q2;
     far_assemble_kernel<<<nblk(total, 256), 256, 0, h->stream>>>(P.n_far, h->d_far_tgt, h->d_far_src, h->d_igeo,
-                                                                 P.q2, h->kpt, h->d_K);
+                                                                 P.q2, h->kpt, h->d_K, h->d_Kdf);
     return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI = 0, 1
 EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
             "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
-            "ibem_profile_read")
+            "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status")
 
 
 class IbemError(RuntimeError):
@@ -48,7 +48,7 @@ class ibem_patch(ctypes.Structure):
 class ibem_params(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("kappa", ctypes.c_double), ("p", ctypes.c_int), ("m", ctypes.c_int),
                 ("q_cheb", ctypes.c_int), ("eta", ctypes.c_double), ("gauss_regular", ctypes.c_int),
-                ("gauss_singular", ctypes.c_int)]
+                ("gauss_singular", ctypes.c_int), ("fp64_coupling", ctypes.c_int)]
 
 
 class ibem_info(ctypes.Structure):
@@ -90,6 +90,8 @@ def _load():
                                   ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
         "ibem_profile_enable": (I32, [P, I32]),
         "ibem_profile_read": (I32, [P, ctypes.POINTER(ibem_profile_data)]),
+        "ibem_set_wait_limit": (I32, [P, ctypes.c_longlong]),
+        "ibem_device_status": (I32, [P, ctypes.POINTER(I32)]),
         "ibem_last_error": (ctypes.c_char_p, [P]),
         "ibem_status_string": (ctypes.c_char_p, [I32]),
     }
@@ -160,8 +162,12 @@ def nurbs_patches(specs):
     return arr
 
 
-def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8):
-    return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular)
+IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE = 0, 1
+
+
+def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8,
+                fp64_coupling=IBEM_COUPLING_DF):
+    return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular, fp64_coupling)
 
 
 # ---- entry points --------------------------------------------------------------------
@@ -239,6 +245,19 @@ def ibem_profile_read(h):
     _check(_lib.ibem_profile_read(h, ctypes.byref(d)), h)
     return {"applications": d.applications, "launches": d.launches,
             "ms": {name: d.ms[i] for i, name in enumerate(PHASES)}}
+
+
+IBEM_DEVICE_OK, IBEM_DEVICE_TIMEOUT = 0, 1
+
+
+def ibem_set_wait_limit(h, limit):
+    _check(_lib.ibem_set_wait_limit(h, limit), h)
+
+
+def ibem_device_status(h):
+    st = ctypes.c_int()
+    _check(_lib.ibem_device_status(h, ctypes.byref(st)), h)
+    return st.value
 
 
 def ibem_last_error(h=None):

@@ -12,9 +12,10 @@ def lib():
     return ibem
 
 
-def handle(p, m, q, eta=1.6, assemble=True):
+def handle(p, m, q, eta=1.6, assemble=True, fp64_coupling=0):
     ibem = lib()
-    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=eta))
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=eta,
+                                                                 fp64_coupling=fp64_coupling))
     if assemble:
         ibem.ibem_assemble(h)
     return h

@@ -39,13 +39,25 @@ def test_dense_matvec_minimal_mesh():
         lib().ibem_destroy(h)
 
 
-def test_fmm_matvec_p2_m2():
+@pytest.mark.parametrize("coupling", [0, 1], ids=["double-float", "native-fp64"])
+def test_fmm_matvec_p2_m2(coupling):
     op = oracle_fmm(2, 2, 6, 1.6)
-    h = handle(2, 2, q=6)
+    h = handle(2, 2, q=6, fp64_coupling=coupling)
     x = _x(op.mesh.n_dofs, 2, 5)
     y0 = np.stack([op.matvec(xi) for xi in x])
     assert rel_err(gpu_matvec(h, x), y0) < TOL64
     lib().ibem_destroy(h)
+
+
+def test_native_and_double_float_coupling_agree_config2():
+    hd = handle(3, 5, q=6, fp64_coupling=0)
+    x = _x(7350, 1, 19)
+    yd = gpu_matvec(hd, x)
+    lib().ibem_destroy(hd)
+    hn = handle(3, 5, q=6, fp64_coupling=1)
+    yn = gpu_matvec(hn, x)
+    lib().ibem_destroy(hn)
+    assert rel_err(yd, yn) < 1e-13
 
 
 def test_fmm_rows_p3_m3():
@@ -187,3 +199,23 @@ def test_argument_and_state_errors():
     ibem.ibem_destroy(h)
     with pytest.raises(ibem.IbemError):
         ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(2, 2, kernel=1, kappa=4.0))
+
+
+def test_bounded_wait_failure_path_and_recovery():
+    # A wait limit of 0 makes every mbarrier wait of the streaming coupling
+    # kernel fail at once: the kernel must record the timeout, drain its copies
+    # and return; the context stays usable and the next application is exact.
+    ibem = lib()
+    h = handle(2, 3, q=6)
+    N = ibem.ibem_get_info(h).ndof
+    x = _x(N, 1, 23)
+    y_ok = gpu_matvec(h, x)
+    assert ibem.ibem_device_status(h) == ibem.IBEM_DEVICE_OK
+    ibem.ibem_set_wait_limit(h, 0)
+    gpu_matvec(h, x)
+    assert ibem.ibem_device_status(h) == ibem.IBEM_DEVICE_TIMEOUT
+    ibem.ibem_set_wait_limit(h, 1 << 26)
+    y2 = gpu_matvec(h, x)
+    assert ibem.ibem_device_status(h) == ibem.IBEM_DEVICE_OK
+    assert np.array_equal(y2, y_ok)
+    ibem.ibem_destroy(h)
