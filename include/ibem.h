@@ -208,6 +208,26 @@ ibem_status ibem_set_wait_limit(ibem_handle* h, long long limit);
  * kernels recorded since the last call, and clear it. */
 ibem_status ibem_device_status(ibem_handle* h, int* status);
 
+/* Potential evaluation that allocates no device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate at the
+ * time they evaluate potentials: code recording a CUDA graph (cudaMalloc is
+ * not permitted during stream capture), real-time loops that must not enter
+ * the allocator, processes whose device memory is reserved up front by a pool
+ * they do not control.  Same arguments, layouts and result as ibem_potential,
+ * but the temporary data (the lifted density, 8 * ndof_super bytes rounded up
+ * to 256, and the Gauss-point source table, 32 * n_quad_points bytes) lives in
+ * one fixed array of IBEM_NOALLOC_SCRATCH_BYTES inside the library, held by
+ * every GPU that loads libibem until the process exits.  A discretisation that
+ * needs more returns IBEM_ERR_ARG with the required size in ibem_last_error.
+ * The first call on a device looks the array up (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the one array:
+ * calls whose GPU work can overlap (different streams or handles on one device
+ * without ordering between them) race on it and must be serialised by the
+ * caller.  The output u_dev is cleared by the call. */
+#define IBEM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_dev, int nrhs,
+                                   const double* pts_dev, int64_t npts, double* u_dev);
+
 /* Host-only: build the block cluster tree without a GPU and return its lists.
  * Call once with null arrays to get the counts.  near: [n_near][8] int32 =
  * (patch_t, ix_t, iy_t, patch_s, ix_s, iy_s, class, orientation) with class

@@ -28,7 +28,7 @@ IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI = 0, 1
 EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
             "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
-            "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status")
+            "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc")
 
 
 class IbemError(RuntimeError):
@@ -86,6 +86,7 @@ def _load():
         "ibem_matvec_host": (I32, [P, P, P, I32, I32]),
         "ibem_solve": (I32, [P, P, P, I32, ctypes.c_double, I32, I32, I32, ctypes.POINTER(ibem_solve_info)]),
         "ibem_potential": (I32, [P, P, I32, P, I64, P]),
+        "ibem_potential_noalloc": (I32, [P, P, I32, P, I64, P]),
         "ibem_block_tree": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
                                   ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
         "ibem_profile_enable": (I32, [P, I32]),
@@ -220,6 +221,11 @@ def ibem_solve(h, b, w, nrhs, rtol=1e-8, maxit=1000, precond=IBEM_PRECOND_JACOBI
 
 def ibem_potential(h, w, nrhs, pts, u):
     _check(_lib.ibem_potential(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
+
+
+def ibem_potential_noalloc(h, w, nrhs, pts, u):
+    """ibem_potential without device allocation (fixed scratch inside libibem)."""
+    _check(_lib.ibem_potential_noalloc(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
 
 
 def ibem_block_tree(patches, params):
