@@ -336,7 +336,7 @@ def ours(args, rank, world, local_rank):
         s32 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precision=1)
         solve = {"rtol": 1e-8, "precond": "jacobi",
                  "fp64": {"seconds": s64.seconds, "iterations": s64.iterations, "rel_residual": s64.rel_residual},
-                 "mixed": {"seconds": s32.seconds, "iterations": s32.iterations, "outer": s32.outer,
+                 "mixed": {"seconds": s32.seconds, "iterations": s32.iterations, "fp64_updates": s32.outer,
                            "rel_residual": s32.rel_residual},
                  "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}
 

@@ -164,9 +164,11 @@ ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrh
 /* Solve T A T^T w = b (Sec. 4 item 3): Jacobi-preconditioned conjugate
  * gradients (Laplace) or GMRES(restart) (Helmholtz), one right-hand side at a
  * time.  precision IBEM_FP64 runs the solver on the FP64 operator;
- * IBEM_FP32 runs iterative refinement: FP64 residuals, FP32-operator inner
- * solves.  Stops when |b - A w| / |b| <= rtol with A the FP64 operator.
- * Synchronises; returns IBEM_ERR_NOCONV if maxit is reached. */
+ * IBEM_FP32 runs it on the FP32 operator and replaces the recursive residual
+ * by the true FP64 residual b - A w whenever it has dropped 100-fold (reliable
+ * updates; info->outer counts them).  Stops when |b - A w| / |b| <= rtol with A
+ * the FP64 operator.  Synchronises; returns IBEM_ERR_NOCONV if maxit is
+ * reached. */
 ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int nrhs,
                        double rtol, int maxit, int precond, int precision,
                        ibem_solve_info* info);

@@ -312,34 +312,61 @@ __global__ void src32_kernel(int64_t n, const float* __restrict__ igeo32, const 
     src[i] = make_float4(g[0], g[1], g[2], (float)((double)g[3] * xh[i] * (1.0 / (4.0 * IBEM_PI))));
 }
 
+// Thread (g, ap) evaluates target rows ap and ap + half against the blocks
+// g, g + G, ... of the row, so every source point loaded serves two rows; the
+// per-block float sums are accumulated in double and the G partial sums are
+// combined through shared memory.
 __global__ void coupling32_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
                                   const int32_t* __restrict__ fsrc, const float* __restrict__ igeo32,
-                                  const float4* __restrict__ src, int q2, int ns, double* __restrict__ yh) {
+                                  const float4* __restrict__ src, int q2, int G, double* __restrict__ yh) {
     extern __shared__ double red[];
-    int sigma = rows[blockIdx.x];
-    int t = threadIdx.x;
-    int g = t / q2, a = t % q2;
-    double acc = 0.0;
-    if (g < ns) {
-        const float* X = igeo32 + 4 * ((int64_t)sigma * q2 + a);
-        float x0 = X[0], x1 = X[1], x2 = X[2];
-        int64_t b0 = fptr[sigma], b1 = fptr[sigma + 1];
-        for (int64_t blk = b0 + g; blk < b1; blk += ns) {
+    const int sigma = rows[blockIdx.x];
+    const int t = threadIdx.x;
+    const int half = (q2 + 1) >> 1;
+    const int g = t / half, ap = t % half;
+    const int a0 = ap, a1 = ap + half;
+    const bool two = a1 < q2;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (g < G) {
+        const float* X0 = igeo32 + 4 * ((int64_t)sigma * q2 + a0);
+        const float* X1 = igeo32 + 4 * ((int64_t)sigma * q2 + (two ? a1 : a0));
+        const float x0 = X0[0], y0 = X0[1], z0 = X0[2];
+        const float x1 = X1[0], y1 = X1[1], z1 = X1[2];
+        const int64_t b0 = fptr[sigma], b1 = fptr[sigma + 1];
+        for (int64_t blk = b0 + g; blk < b1; blk += G) {
             const float4* Y = src + (int64_t)fsrc[blk] * q2;
-            float f = 0.0f;
-            for (int b = 0; b < q2; ++b) {
-                float4 y = Y[b];
-                float d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-                f += y.w * rsqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+            float f0 = 0.0f, f1 = 0.0f, h0 = 0.0f, h1 = 0.0f;
+            int b = 0;
+            for (; b + 1 < q2; b += 2) {
+                float4 u = Y[b], v = Y[b + 1];
+                float d0 = x0 - u.x, d1 = y0 - u.y, d2 = z0 - u.z;
+                float e0 = x1 - u.x, e1 = y1 - u.y, e2 = z1 - u.z;
+                float c0 = x0 - v.x, c1 = y0 - v.y, c2 = z0 - v.z;
+                float k0 = x1 - v.x, k1 = y1 - v.y, k2 = z1 - v.z;
+                f0 = fmaf(u.w, rsqrtf(d0 * d0 + d1 * d1 + d2 * d2), f0);
+                f1 = fmaf(u.w, rsqrtf(e0 * e0 + e1 * e1 + e2 * e2), f1);
+                h0 = fmaf(v.w, rsqrtf(c0 * c0 + c1 * c1 + c2 * c2), h0);
+                h1 = fmaf(v.w, rsqrtf(k0 * k0 + k1 * k1 + k2 * k2), h1);
             }
-            acc += (double)f;
+            if (b < q2) {
+                float4 u = Y[b];
+                float d0 = x0 - u.x, d1 = y0 - u.y, d2 = z0 - u.z;
+                float e0 = x1 - u.x, e1 = y1 - u.y, e2 = z1 - u.z;
+                f0 = fmaf(u.w, rsqrtf(d0 * d0 + d1 * d1 + d2 * d2), f0);
+                f1 = fmaf(u.w, rsqrtf(e0 * e0 + e1 * e1 + e2 * e2), f1);
+            }
+            acc0 += (double)(f0 + h0);
+            acc1 += (double)(f1 + h1);
         }
     }
-    red[t] = acc;
+    if (g < G) {
+        red[g * q2 + a0] = acc0;
+        if (two) red[g * q2 + a1] = acc1;
+    }
     __syncthreads();
     if (t < q2) {
         double v = 0.0;
-        for (int k = 0; k < ns; ++k) v += red[k * q2 + t];
+        for (int k = 0; k < G; ++k) v += red[k * q2 + t];
         yh[(int64_t)sigma * q2 + t] = v * (double)igeo32[4 * ((int64_t)sigma * q2 + t) + 3];
     }
 }
@@ -503,12 +530,13 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
         if (nrows > 0) {
             PhaseTimer pt(h, 2);
             if (precision == IBEM_FP32) {
-                int ns = 256 / q2 > 0 ? 256 / q2 : 1;
-                int threads = ((ns * q2 + 31) / 32) * 32;
+                const int half = (q2 + 1) / 2;
+                int ns = 256 / half > 0 ? 256 / half : 1;
+                int threads = ((ns * half + 31) / 32) * 32;
                 for (int r = 0; r < R; ++r) {
                     src32_kernel<<<nblk(P.C * q2, T), T, 0, st>>>(P.C * q2, h->d_igeo32, h->d_xh + (size_t)r * P.C * q2,
                                                                   h->d_src32);
-                    coupling32_kernel<<<nrows, threads, threads * sizeof(double), st>>>(
+                    coupling32_kernel<<<nrows, threads, (size_t)ns * q2 * sizeof(double), st>>>(
                         h->d_far_rows, h->d_far_ptr, h->d_far_src, h->d_igeo32, h->d_src32, q2, ns,
                         h->d_yh + (size_t)r * P.C * q2);
                     h->launches += 2;

@@ -1,7 +1,7 @@
 // Krylov solvers of libibem (Sec. 4 item 3): Jacobi-preconditioned conjugate
 // gradients on T A T^T w = b for the Laplace single layer (symmetric positive
-// definite), in FP64, or as iterative refinement: FP64 residual with the FP64
-// operator, correction from CG on the FP32 operator.
+// definite), either on the FP64 operator or on the FP32 operator with reliable
+// updates of the residual by the FP64 operator.
 //
 // Vectors are FP64.  Reductions run in one CTA per call (N is at most a few
 // 10^5 here), so every dot product is deterministic.
@@ -144,6 +144,64 @@ ibem_status cg(ibem_handle* h, const double* b, double* x, const Work& w, int pr
     return IBEM_ERR_NOCONV;
 }
 
+// Mixed precision: conjugate gradients whose operator is the FP32 operator,
+// with reliable updates (Sleijpen and van der Vorst): whenever the recursively
+// updated residual has dropped by `drop` since the last update, or looks
+// converged, it is replaced by the true residual b - A64 x computed with the
+// FP64 operator, and the search direction is kept.  Convergence is decided on
+// the true residual only.  *updates counts the FP64 applications.
+ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& w, double tol_abs, int maxit,
+                        bool jacobi, int* its, int* updates) {
+    Plan& P = h->P;
+    int64_t N = P.N;
+    cudaStream_t st = h->stream;
+    const double* d = jacobi ? h->d_diag : nullptr;
+    const double drop = 1e-2;
+    cudaMemsetAsync(x, 0, N * sizeof(double), st);
+    cudaMemcpyAsync(w.r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    scal_div_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.r, d, w.z);
+    cudaMemcpyAsync(w.p, w.z, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
+    double rz;
+    if (readback(h, h->d_red, 1, &rz) != cudaSuccess) return IBEM_ERR_CUDA;
+    double ref;
+    if (norm2(h, w.r, N, &ref) != cudaSuccess) return IBEM_ERR_CUDA;
+    *its = 0;
+    *updates = 0;
+    if (ref <= tol_abs) return IBEM_OK;
+    for (int it = 1; it <= maxit; ++it) {
+        if (apply_operator(h, w.p, w.Ap, 1, IBEM_FP32) != cudaSuccess) return IBEM_ERR_CUDA;
+        dot_kernel<<<1, 1024, 0, st>>>(w.p, w.Ap, N, h->d_red);
+        double pAp;
+        if (readback(h, h->d_red, 1, &pAp) != cudaSuccess) return IBEM_ERR_CUDA;
+        if (!(pAp > 0.0) || !std::isfinite(pAp)) { *its = it; return IBEM_ERR_BREAKDOWN; }
+        h->h_red[0] = rz / pAp;
+        cudaMemcpyAsync(h->d_red + 2, h->h_red, sizeof(double), cudaMemcpyHostToDevice, st);
+        cg_update_kernel<<<1, 1024, 0, st>>>(N, h->d_red + 2, x, w.r, w.p, w.Ap, d, w.z, h->d_red);
+        double rr[2];
+        if (readback(h, h->d_red, 2, rr) != cudaSuccess) return IBEM_ERR_CUDA;
+        *its = it;
+        if (!std::isfinite(rr[0])) return IBEM_ERR_BREAKDOWN;
+        double rn = std::sqrt(rr[0]);
+        double rz_new = rr[1];
+        if (rn <= drop * ref || rn <= tol_abs) {
+            if (apply_operator(h, x, w.Ap, 1, IBEM_FP64) != cudaSuccess) return IBEM_ERR_CUDA;
+            ++*updates;
+            sub_kernel<<<nblk(N, 256), 256, 0, st>>>(N, b, w.Ap, w.r);
+            if (norm2(h, w.r, N, &rn) != cudaSuccess) return IBEM_ERR_CUDA;
+            ref = rn;
+            if (rn <= tol_abs) return IBEM_OK;
+            scal_div_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.r, d, w.z);
+            dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
+            if (readback(h, h->d_red, 1, &rz_new) != cudaSuccess) return IBEM_ERR_CUDA;
+        }
+        double beta = rz_new / rz;
+        rz = rz_new;
+        xpby_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.z, beta, w.p);
+    }
+    return IBEM_ERR_NOCONV;
+}
+
 }  // namespace
 
 ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, double rtol, int maxit,
@@ -182,27 +240,7 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
             s = cg(h, bb, ww, w, IBEM_FP64, rtol * nb, maxit, jac, &its);
             outer = 1;
         } else {
-            // iterative refinement: r = b - A64 w, d = CG(A32, r), w += d
-            cudaMemsetAsync(ww, 0, N * sizeof(double), st);
-            cudaMemcpyAsync(w.rr, bb, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
-            double rn = nb;
-            int left = maxit;
-            while (rn > rtol * nb && left > 0 && outer < 30) {
-                double inner = 0.5 * rtol * nb / rn;
-                if (inner < 1e-6) inner = 1e-6;
-                int k = 0;
-                s = cg(h, w.rr, w.d, w, IBEM_FP32, inner * rn, left, jac, &k);
-                its += k;
-                left -= k;
-                ++outer;
-                if (s == IBEM_ERR_BREAKDOWN || s == IBEM_ERR_CUDA) break;
-                add_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.d, ww);
-                if (apply_operator(h, ww, w.Ap, 1, IBEM_FP64) != cudaSuccess) return IBEM_ERR_CUDA;
-                sub_kernel<<<nblk(N, 256), 256, 0, st>>>(N, bb, w.Ap, w.rr);
-                if (norm2(h, w.rr, N, &rn) != cudaSuccess) return IBEM_ERR_CUDA;
-                s = IBEM_OK;
-            }
-            if (rn > rtol * nb && s == IBEM_OK) s = IBEM_ERR_NOCONV;
+            s = cg_reliable(h, bb, ww, w, rtol * nb, maxit, jac, &its, &outer);
         }
         // true residual with the FP64 operator
         if (apply_operator(h, ww, w.Ap, 1, IBEM_FP64) != cudaSuccess) return IBEM_ERR_CUDA;
