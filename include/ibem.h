@@ -95,10 +95,12 @@ typedef struct {
 
 /* FP64 coupling variants.  GB300 executes FP64 FMA at 1/64 of the FP32 rate, so
  * by default the coupling matrices are stored as unevaluated float pairs
- * (hi + lo, 8 bytes per entry) and applied with exact FP32 products and
- * compensated sums (about 48 significant bits, relative error ~1e-14);
- * NATIVE stores doubles and uses FP64 FMA.  Both reproduce the FP64 oracle to
- * 1e-12. */
+ * (hi + lo, 8 bytes per real entry, 16 per complex one) and applied with exact
+ * FP32 products and compensated sums (about 48 significant bits, relative
+ * error ~1e-14).  NATIVE: Laplace stores doubles and uses FP64 FMA; Helmholtz
+ * generates the coupling on the fly in FP64 (also chosen automatically when the
+ * stored complex matrices would exceed half of the free device memory).  All
+ * variants reproduce the FP64 oracle to 1e-12. */
 enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1 };
 
 typedef struct {
@@ -147,7 +149,7 @@ ibem_status ibem_quad_points(const ibem_handle* h, double* xyz_dev);
 
 /* Right-hand side b = T g*, b_i = int_Gamma g b_i (Sec. 3.2, Sec. 4.3):
  * g_dev is [nrhs][n_quad_points] samples of g at ibem_quad_points (complex for
- * Helmholtz), b_dev is [nrhs][ndof]. */
+ * Helmholtz), b_dev is [nrhs][ndof] (complex for Helmholtz). */
 ibem_status ibem_rhs(ibem_handle* h, const double* g_dev, int nrhs, double* b_dev);
 
 /* y = T A T^T x (Sec. 4.3): the FMM-compressed single-layer Galerkin matrix in
@@ -162,7 +164,7 @@ ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrh
                              int precision);
 
 /* Solve T A T^T w = b (Sec. 4 item 3): Jacobi-preconditioned conjugate
- * gradients (Laplace) or GMRES(restart) (Helmholtz), one right-hand side at a
+ * gradients (Laplace) or GMRES(100) (Helmholtz), one right-hand side at a
  * time.  precision IBEM_FP64 runs the solver on the FP64 operator;
  * IBEM_FP32 runs it on the FP32 operator and replaces the recursive residual
  * by the true FP64 residual b - A w whenever it has dropped 100-fold (reliable
@@ -225,7 +227,8 @@ ibem_status ibem_device_status(ibem_handle* h, int* status);
  * that first call before any stream capture.  All calls share the one array:
  * calls whose GPU work can overlap (different streams or handles on one device
  * without ordering between them) race on it and must be serialised by the
- * caller.  The output u_dev is cleared by the call. */
+ * caller.  The output u_dev is cleared by the call.  Laplace handles only
+ * (a Helmholtz handle gets IBEM_ERR_ARG). */
 #define IBEM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_dev, int nrhs,
                                    const double* pts_dev, int64_t npts, double* u_dev);

@@ -96,7 +96,7 @@ void free_handle(ibem_handle* h) {
                     h->d_pairs_by_cls[1], h->d_pairs_by_cls[2], h->d_pairs_by_cls[3], h->d_pairs_by_cls[4],
                     h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_Kdf, h->d_xh2, h->d_far_rows,
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
-                    h->d_solver, h->d_red, h->d_status};
+                    h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -190,11 +190,7 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
         return fail(nullptr, msg.find("degenerate") != std::string::npos ? IBEM_ERR_GEOMETRY : IBEM_ERR_ARG, msg);
     }
     Plan& P = h->P;
-    if (params->kernel != IBEM_LAPLACE) {
-        delete h;
-        return fail(nullptr, IBEM_ERR_ARG, "the GPU path implements the Laplace kernel only");
-    }
-    h->helm = false;
+    h->helm = params->kernel == IBEM_HELMHOLTZ;
     h->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e) { delete h; return cuda_fail(nullptr, e, "cudaGetDevice"); }
@@ -299,7 +295,7 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
         TRY(cudaMalloc(&h->d_igeo, (size_t)P.C * P.q2 * 4 * sizeof(double)), "alloc igeo");
         TRY(cudaMalloc(&h->d_igeo32, (size_t)P.C * P.q2 * 4 * sizeof(float)), "alloc igeo32");
     }
-    TRY(cudaMalloc(&h->d_diag, (size_t)P.N * sizeof(double)), "alloc diag");
+    TRY(cudaMalloc(&h->d_diag, (size_t)P.N * (h->helm ? 2 : 1) * sizeof(double)), "alloc diag");
     TRY(cudaMalloc(&h->d_red, 64 * sizeof(double)), "alloc red");
     TRY(cudaMalloc(&h->d_status, sizeof(int)), "alloc status");
     TRY(cudaMemsetAsync(h->d_status, 0, sizeof(int), st), "clear status");
@@ -335,8 +331,8 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     info->n_near_singular[1] = P.n_cls[CLS_EDGE];
     info->n_near_singular[2] = P.n_cls[CLS_VERTEX];
     info->n_near_singular[3] = P.n_cls[CLS_SUBDIV];
-    info->bytes_near = P.n_near * (int64_t)P.nb * P.nb * 8;
-    info->bytes_far = P.n_far * (int64_t)h->kpt * 4 * P.q2 * 8;
+    info->bytes_near = P.n_near * (int64_t)P.nb * P.nb * (h->helm ? 16 : 8);
+    info->bytes_far = h->far_on_the_fly ? 0 : P.n_far * (int64_t)h->kpt * 4 * P.q2 * (h->helm ? 16 : 8);
     info->assembled = h->assembled ? 1 : 0;
     return IBEM_OK;
 }
@@ -347,10 +343,19 @@ ibem_status ibem_assemble(ibem_handle* h) {
     cudaError_t e;
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
     if (!h->d_near) {
-        size_t nn = (size_t)(P.n_near > 0 ? P.n_near : 1) * P.nb * P.nb;
+        size_t nn = (size_t)(P.n_near > 0 ? P.n_near : 1) * P.nb * P.nb * (h->helm ? 2 : 1);
         if ((e = cudaMalloc(&h->d_near, nn * sizeof(double)))) return cuda_fail(h, e, "alloc near blocks");
         if ((e = cudaMalloc(&h->d_near32, nn * sizeof(float)))) return cuda_fail(h, e, "alloc near blocks fp32");
-        if (P.n_far > 0) {
+        if (P.n_far > 0 && h->helm) {
+            // stored complex coupling (16 B per entry) if it fits in half of the free memory
+            size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
+            size_t free_b = 0, total_b = 0;
+            cudaMemGetInfo(&free_b, &total_b);
+            h->far_on_the_fly =
+                P.prm.fp64_coupling == IBEM_COUPLING_NATIVE || nk * sizeof(float4) > free_b / 2;
+            if (!h->far_on_the_fly)
+                if ((e = cudaMalloc(&h->d_Kc, nk * sizeof(float4)))) return cuda_fail(h, e, "alloc coupling matrices");
+        } else if (P.n_far > 0) {
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
                 if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
@@ -359,8 +364,13 @@ ibem_status ibem_assemble(ibem_handle* h) {
             }
         }
     }
-    if ((e = launch_near_assembly(h))) return cuda_fail(h, e, "near assembly");
-    if ((e = launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
+    if (h->helm) {
+        if ((e = helm_launch_near_assembly(h))) return cuda_fail(h, e, "near assembly");
+        if ((e = helm_launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
+    } else {
+        if ((e = launch_near_assembly(h))) return cuda_fail(h, e, "near assembly");
+        if ((e = launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
+    }
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");
     h->assembled = true;
     return IBEM_OK;

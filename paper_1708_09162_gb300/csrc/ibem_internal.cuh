@@ -259,6 +259,11 @@ struct ibem_handle {
     double* d_K = nullptr;          // [n_far][kpt][4 q2]: entry (a, b = s + 4k) at [k][4a + s] (native)
     float2* d_Kdf = nullptr;        // same layout, (hi, lo) float pairs (double-float coupling)
     float2* d_xh2 = nullptr;        // forward moments split into (hi, lo) float pairs
+    float4* d_Kc = nullptr;         // Helmholtz: double-float complex coupling (re_hi, re_lo, im_hi, im_lo)
+    float4* d_xh4 = nullptr;        // Helmholtz: forward moments as double-float complex
+    double* d_hsx = nullptr;        // Helmholtz: split-layout input  [2R][max(N, nq)]
+    double* d_hsy = nullptr;        // Helmholtz: split-layout output [2R][N]
+    bool far_on_the_fly = false;    // Helmholtz FP64 coupling generated on the fly (stored K too large)
     int kpt = 0;
     std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
     int max_far_row = 0;            // longest far list
@@ -287,6 +292,31 @@ struct ibem_handle {
 };
 
 namespace ibem {
+// real kernels of kernels_apply.cu reused by the complex (Helmholtz) path
+__global__ void lift_kernel(int R, int64_t E, int p, int ne1, const double* __restrict__ ext,
+                            const double* __restrict__ x, int64_t N, double* __restrict__ xs);
+__global__ void restrict_kernel(int R, int64_t N, int p, int ne1, const double* __restrict__ ext,
+                                const double* __restrict__ ys, int64_t E, double* __restrict__ y);
+__global__ void leaf_moment_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                                   const double* __restrict__ xs, int64_t leaf_off, int64_t C, double* __restrict__ xh);
+__global__ void m2m_kernel(int R, int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                           int64_t C, double* __restrict__ xh);
+__global__ void l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                           int64_t C, double* __restrict__ yh);
+__global__ void leaf_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                                 const double* __restrict__ yh, int64_t leaf_off, int64_t C, double* __restrict__ ys);
+__global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n);
+__global__ void rhs_super_kernel(int R, int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
+                                 const double* __restrict__ phi, const double* __restrict__ g, int64_t nq,
+                                 double* __restrict__ gs);
+// Helmholtz (kernels_helm.cu)
+cudaError_t helm_launch_near_assembly(ibem_handle* h);
+cudaError_t helm_launch_far_assembly(ibem_handle* h);
+cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int nrhs, int precision, double* xsplit,
+                                double* ysplit);
+cudaError_t helm_launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b, double* gsplit, double* bsplit);
+cudaError_t helm_launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
+                                  double* u, double* wsplit);
 // kernels_*.cu entry points (launch on h->stream; return cudaError_t)
 cudaError_t launch_geometry_tables(ibem_handle* h);
 cudaError_t launch_near_assembly(ibem_handle* h);

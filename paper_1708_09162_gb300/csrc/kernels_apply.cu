@@ -449,8 +449,14 @@ __global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ ou
 }
 
 cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
+    // nrhs counts real right-hand sides (a complex one counts twice)
     if (nrhs <= h->ws_nrhs) return cudaSuccess;
     Plan& P = h->P;
+    if (h->helm) {
+        cudaFree(h->d_hsx); cudaFree(h->d_hsy); cudaFree(h->d_xh4);
+        h->d_hsx = h->d_hsy = nullptr;
+        h->d_xh4 = nullptr;
+    }
     cudaFree(h->d_xs); cudaFree(h->d_ys); cudaFree(h->d_xh); cudaFree(h->d_yh);
     cudaFree(h->d_xs32); cudaFree(h->d_src32); cudaFree(h->d_xh2);
     h->d_xh2 = nullptr;
@@ -467,6 +473,13 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     if ((e = cudaMalloc(&h->d_xh2, (size_t)nrhs * P.C * ((P.q2 + 1) & ~1) * sizeof(float2) + 16))) return e;
     if ((e = cudaMalloc(&h->d_xs32, ns * sizeof(float)))) return e;
     if ((e = cudaMalloc(&h->d_src32, (size_t)P.C * (P.q2 > 0 ? P.q2 : 1) * sizeof(float4)))) return e;
+    if (h->helm) {
+        size_t n = (size_t)(P.N > P.nq ? P.N : P.nq);
+        if ((e = cudaMalloc(&h->d_hsx, (size_t)nrhs * n * sizeof(double)))) return e;
+        if ((e = cudaMalloc(&h->d_hsy, (size_t)nrhs * P.N * sizeof(double)))) return e;
+        if ((e = cudaMalloc(&h->d_xh4, (size_t)(nrhs / 2 + 1) * P.C * ((P.q2 + 1) & ~1) * sizeof(float4) + 32)))
+            return e;
+    }
     h->ws_nrhs = nrhs;
     return cudaSuccess;
 }
@@ -501,6 +514,11 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
     Plan& P = h->P;
     cudaStream_t st = h->stream;
     cudaError_t e;
+    if (h->helm) {
+        if ((e = ensure_workspace(h, 2 * nrhs))) return e;
+        h->applications++;
+        return helm_apply_operator(h, x, y, nrhs, precision, h->d_hsx, h->d_hsy);
+    }
     if ((e = ensure_workspace(h, nrhs))) return e;
     const int R = nrhs;
     const int T = 256;
@@ -636,6 +654,10 @@ __global__ void rhs_super_kernel(int R, int64_t E, int QQ, int nb, const double*
 cudaError_t launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b) {
     Plan& P = h->P;
     cudaError_t e;
+    if (h->helm) {
+        if ((e = ensure_workspace(h, 2 * nrhs))) return e;
+        return helm_launch_rhs(h, g, nrhs, b, h->d_hsx, h->d_hsy);
+    }
     if ((e = ensure_workspace(h, nrhs))) return e;
     const int T = 256;
     int QQ = P.Q * P.Q;
@@ -681,6 +703,10 @@ cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const do
                              double* u) {
     Plan& P = h->P;
     cudaError_t e;
+    if (h->helm) {
+        if ((e = ensure_workspace(h, 2 * nrhs))) return e;
+        return helm_launch_potential(h, w, nrhs, pts, npts, u, h->d_hsx);
+    }
     if ((e = ensure_workspace(h, 1))) return e;
     const int T = 256;
     int QQ = P.Q * P.Q;

@@ -60,6 +60,10 @@ extern "C" ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_de
         h->err = "ibem_potential_noalloc: bad arguments";
         return IBEM_ERR_ARG;
     }
+    if (h->helm) {
+        h->err = "ibem_potential_noalloc: Laplace handles only; use ibem_potential for Helmholtz";
+        return IBEM_ERR_ARG;
+    }
     if (nrhs == 0 || npts == 0) return IBEM_OK;
     const Plan& P = h->P;
     const int QQ = P.Q * P.Q;

@@ -84,6 +84,93 @@ __global__ void add_kernel(int64_t n, const double* __restrict__ x, double* __re
     if (i < n) y[i] += x[i];
 }
 
+// ---- complex vectors (interleaved re, im) for GMRES ---------------------------------
+// out[2k], out[2k+1] = sum_i conj(V[k][i]) w[i] for k = 0..nk-1 (one CTA per k)
+__global__ void zdots_kernel(const double* __restrict__ V, int64_t N, const double* __restrict__ w, int nk,
+                             double* __restrict__ out) {
+    __shared__ double sr[256], si[256];
+    const double* v = V + (int64_t)blockIdx.x * 2 * N;
+    double ar = 0.0, ai = 0.0;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+        double vr = v[2 * i], vi = v[2 * i + 1], xr = w[2 * i], xi = w[2 * i + 1];
+        ar += vr * xr + vi * xi;
+        ai += vr * xi - vi * xr;
+    }
+    sr[threadIdx.x] = ar;
+    si[threadIdx.x] = ai;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sr[threadIdx.x] += sr[threadIdx.x + s];
+            si[threadIdx.x] += si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = sr[0];
+        out[2 * blockIdx.x + 1] = si[0];
+    }
+}
+
+// w -= sum_k V[k] h[k]   (complex)
+__global__ void zgemv_sub_kernel(const double* __restrict__ V, int64_t N, const double* __restrict__ h, int nk,
+                                 double* __restrict__ w) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double ar = w[2 * i], ai = w[2 * i + 1];
+    for (int k = 0; k < nk; ++k) {
+        double vr = V[(int64_t)k * 2 * N + 2 * i], vi = V[(int64_t)k * 2 * N + 2 * i + 1];
+        double hr = h[2 * k], hi = h[2 * k + 1];
+        ar -= vr * hr - vi * hi;
+        ai -= vr * hi + vi * hr;
+    }
+    w[2 * i] = ar;
+    w[2 * i + 1] = ai;
+}
+
+// out = (sum_k V[k] y[k]) / d   (complex; d = Jacobi diagonal or null)
+__global__ void zcombine_kernel(const double* __restrict__ V, int64_t N, const double* __restrict__ y, int nk,
+                                const double* __restrict__ d, double* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double ar = 0.0, ai = 0.0;
+    for (int k = 0; k < nk; ++k) {
+        double vr = V[(int64_t)k * 2 * N + 2 * i], vi = V[(int64_t)k * 2 * N + 2 * i + 1];
+        ar += vr * y[2 * k] - vi * y[2 * k + 1];
+        ai += vr * y[2 * k + 1] + vi * y[2 * k];
+    }
+    if (d) {
+        double dr = d[2 * i], di = d[2 * i + 1], den = dr * dr + di * di;
+        double br = (ar * dr + ai * di) / den, bi = (ai * dr - ar * di) / den;
+        ar = br;
+        ai = bi;
+    }
+    out[2 * i] = ar;
+    out[2 * i + 1] = ai;
+}
+
+// z = v / d (complex), or copy
+__global__ void zdiv_kernel(int64_t N, const double* __restrict__ v, const double* __restrict__ d,
+                            double* __restrict__ z) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double vr = v[2 * i], vi = v[2 * i + 1];
+    if (d) {
+        double dr = d[2 * i], di = d[2 * i + 1], den = dr * dr + di * di;
+        z[2 * i] = (vr * dr + vi * di) / den;
+        z[2 * i + 1] = (vi * dr - vr * di) / den;
+    } else {
+        z[2 * i] = vr;
+        z[2 * i + 1] = vi;
+    }
+}
+
+// y = alpha * x (real alpha), n doubles
+__global__ void dscal_copy_kernel(int64_t n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = alpha * x[i];
+}
+
 namespace {
 
 struct Work {
@@ -202,6 +289,133 @@ ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& 
     return IBEM_ERR_NOCONV;
 }
 
+// Restarted GMRES with right Jacobi preconditioning for the complex-symmetric
+// Helmholtz matrix.  Arnoldi with two passes of classical Gram-Schmidt in FP64;
+// Givens rotations on the host.  The Arnoldi operator has precision `prec`;
+// every restart recomputes the residual b - A x with the FP64 operator, so with
+// prec = IBEM_FP32 the restarts are FP64 residual corrections.
+ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, int maxit, bool jacobi, int prec,
+                  int restart, int* its, int* restarts) {
+    Plan& P = h->P;
+    const int64_t N = P.N;
+    cudaStream_t st = h->stream;
+    const double* d = jacobi ? h->d_diag : nullptr;
+    const int m = restart;
+    double *V = nullptr, *w = nullptr, *z = nullptr, *hv = nullptr;
+    if (cudaMallocAsync(&V, (size_t)(m + 1) * 2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
+    if (cudaMallocAsync(&w, (size_t)2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
+    if (cudaMallocAsync(&z, (size_t)2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
+    if (cudaMallocAsync(&hv, (size_t)2 * (m + 1) * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
+    std::vector<double> H((size_t)(m + 1) * m * 2, 0.0), cs(m), snr(m), sni(m), g(2 * (m + 1)), hh(2 * (m + 1));
+    ibem_status status = IBEM_ERR_NOCONV;
+    *its = 0;
+    *restarts = 0;
+    auto done = [&](ibem_status s) {
+        cudaFreeAsync(V, st);
+        cudaFreeAsync(w, st);
+        cudaFreeAsync(z, st);
+        cudaFreeAsync(hv, st);
+        cudaStreamSynchronize(st);
+        return s;
+    };
+    cudaMemsetAsync(x, 0, 2 * N * sizeof(double), st);
+    cudaMemcpyAsync(w, b, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    auto Hr = [&](int i, int j) -> double& { return H[2 * ((size_t)i * m + j)]; };
+    auto Hi = [&](int i, int j) -> double& { return H[2 * ((size_t)i * m + j) + 1]; };
+    const unsigned nb = nblk(N, 256);
+    while (*its < maxit) {
+        double beta;
+        if (norm2(h, w, 2 * N, &beta) != cudaSuccess) return done(IBEM_ERR_CUDA);
+        if (!std::isfinite(beta)) return done(IBEM_ERR_BREAKDOWN);
+        if (beta <= tol_abs) { status = IBEM_OK; break; }
+        dscal_copy_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, 1.0 / beta, w, V);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        bool conv = false;
+        for (int j = 0; j < m && *its < maxit; ++j) {
+            zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, z);
+            if (apply_operator(h, z, w, 1, prec) != cudaSuccess) return done(IBEM_ERR_CUDA);
+            for (int i = 0; i <= j; ++i) { Hr(i, j) = 0.0; Hi(i, j) = 0.0; }
+            for (int pass = 0; pass < 2; ++pass) {
+                zdots_kernel<<<j + 1, 256, 0, st>>>(V, N, w, j + 1, hv);
+                zgemv_sub_kernel<<<nb, 256, 0, st>>>(V, N, hv, j + 1, w);
+                if (cudaMemcpyAsync(hh.data(), hv, 2 * (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st) ||
+                    cudaStreamSynchronize(st))
+                    return done(IBEM_ERR_CUDA);
+                for (int i = 0; i <= j; ++i) { Hr(i, j) += hh[2 * i]; Hi(i, j) += hh[2 * i + 1]; }
+            }
+            double hn;
+            if (norm2(h, w, 2 * N, &hn) != cudaSuccess) return done(IBEM_ERR_CUDA);
+            Hr(j + 1, j) = hn;
+            Hi(j + 1, j) = 0.0;
+            // apply the previous rotations to column j
+            for (int i = 0; i < j; ++i) {
+                double ar = Hr(i, j), ai = Hi(i, j), br = Hr(i + 1, j), bi = Hi(i + 1, j);
+                // [c  s; -conj(s)  c] with real c, complex s
+                Hr(i, j) = cs[i] * ar + (snr[i] * br - sni[i] * bi);
+                Hi(i, j) = cs[i] * ai + (snr[i] * bi + sni[i] * br);
+                Hr(i + 1, j) = -(snr[i] * ar + sni[i] * ai) + cs[i] * br;
+                Hi(i + 1, j) = -(snr[i] * ai - sni[i] * ar) + cs[i] * bi;
+            }
+            // new rotation zeroing H(j+1, j)
+            double ar = Hr(j, j), ai = Hi(j, j), bb = Hr(j + 1, j);
+            double na = std::sqrt(ar * ar + ai * ai);
+            double den = std::sqrt(na * na + bb * bb);
+            if (den == 0.0) return done(IBEM_ERR_BREAKDOWN);
+            if (na == 0.0) { cs[j] = 0.0; snr[j] = 1.0; sni[j] = 0.0; }
+            else {
+                cs[j] = na / den;
+                // s = (a / |a|) * conj(b) / den, b real
+                snr[j] = (ar / na) * bb / den;
+                sni[j] = (ai / na) * bb / den;
+            }
+            Hr(j, j) = cs[j] * ar + (snr[j] * bb);
+            Hi(j, j) = cs[j] * ai + (sni[j] * bb);
+            Hr(j + 1, j) = 0.0;
+            Hi(j + 1, j) = 0.0;
+            double gr = g[2 * j], gi = g[2 * j + 1];
+            g[2 * j] = cs[j] * gr;
+            g[2 * j + 1] = cs[j] * gi;
+            g[2 * (j + 1)] = -(snr[j] * gr + sni[j] * gi);
+            g[2 * (j + 1) + 1] = -(snr[j] * gi - sni[j] * gr);
+            k = j + 1;
+            ++*its;
+            double res = std::sqrt(g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1]);
+            if (!std::isfinite(res)) return done(IBEM_ERR_BREAKDOWN);
+            if (res <= tol_abs || hn == 0.0) { conv = true; break; }
+            dscal_copy_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, 1.0 / hn, w, V + (size_t)(j + 1) * 2 * N);
+        }
+        // back substitution R y = g (complex, upper triangular k x k)
+        std::vector<double> y(2 * k, 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+            double sr = g[2 * i], si = g[2 * i + 1];
+            for (int l = i + 1; l < k; ++l) {
+                sr -= Hr(i, l) * y[2 * l] - Hi(i, l) * y[2 * l + 1];
+                si -= Hr(i, l) * y[2 * l + 1] + Hi(i, l) * y[2 * l];
+            }
+            double dr = Hr(i, i), di = Hi(i, i), den = dr * dr + di * di;
+            y[2 * i] = (sr * dr + si * di) / den;
+            y[2 * i + 1] = (si * dr - sr * di) / den;
+        }
+        for (int i = 0; i < 2 * k; ++i) hh[i] = y[i];
+        if (cudaMemcpyAsync(hv, hh.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
+            return done(IBEM_ERR_CUDA);
+        zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, d, z);
+        add_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, z, x);
+        // restart residual with the FP64 operator
+        if (apply_operator(h, x, w, 1, IBEM_FP64) != cudaSuccess) return done(IBEM_ERR_CUDA);
+        sub_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, b, w, w);
+        ++*restarts;
+        (void)conv;
+    }
+    if (status != IBEM_OK) {
+        double beta;
+        if (norm2(h, w, 2 * N, &beta) == cudaSuccess && beta <= tol_abs) status = IBEM_OK;
+    }
+    return done(status);
+}
+
 }  // namespace
 
 ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, double rtol, int maxit,
@@ -209,7 +423,7 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
     Plan& P = h->P;
     int64_t N = P.N;
     auto t0 = std::chrono::steady_clock::now();
-    size_t need = 7 * (size_t)N;
+    size_t need = 7 * (size_t)N * (h->helm ? 2 : 1);
     if (h->solver_len < need) {
         cudaFree(h->d_solver);
         h->d_solver = nullptr;
@@ -217,26 +431,30 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
         if (cudaMalloc(&h->d_solver, need * sizeof(double)) != cudaSuccess) return IBEM_ERR_OOM;
         h->solver_len = need;
     }
-    Work w{h->d_solver, h->d_solver + N, h->d_solver + 2 * N, h->d_solver + 3 * N, h->d_solver + 4 * N,
-           h->d_solver + 5 * N, h->d_solver + 6 * N};
+    const int64_t NN = N * (h->helm ? 2 : 1);
+    Work w{h->d_solver, h->d_solver + NN, h->d_solver + 2 * NN, h->d_solver + 3 * NN, h->d_solver + 4 * NN,
+           h->d_solver + 5 * NN, h->d_solver + 6 * NN};
     bool jac = precond == IBEM_PRECOND_JACOBI;
     ibem_status worst = IBEM_OK;
     int total_it = 0, total_outer = 0;
     double worst_res = 0.0;
     cudaStream_t st = h->stream;
     for (int rhs = 0; rhs < nrhs; ++rhs) {
-        const double* bb = b + (size_t)rhs * N;
-        double* ww = wout + (size_t)rhs * N;
+        const int cw = h->helm ? 2 : 1;            // doubles per entry
+        const double* bb = b + (size_t)rhs * N * cw;
+        double* ww = wout + (size_t)rhs * N * cw;
         double nb;
-        if (norm2(h, bb, N, &nb) != cudaSuccess) return IBEM_ERR_CUDA;
+        if (norm2(h, bb, cw * N, &nb) != cudaSuccess) return IBEM_ERR_CUDA;
         if (nb == 0.0) {
-            cudaMemsetAsync(ww, 0, N * sizeof(double), st);
+            cudaMemsetAsync(ww, 0, cw * N * sizeof(double), st);
             continue;
         }
         ibem_status s = IBEM_OK;
         int its = 0, outer = 0;
         double res = 0.0;
-        if (precision == IBEM_FP64) {
+        if (h->helm) {
+            s = gmres(h, bb, ww, rtol * nb, maxit, jac, precision, 100, &its, &outer);
+        } else if (precision == IBEM_FP64) {
             s = cg(h, bb, ww, w, IBEM_FP64, rtol * nb, maxit, jac, &its);
             outer = 1;
         } else {
@@ -244,9 +462,9 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
         }
         // true residual with the FP64 operator
         if (apply_operator(h, ww, w.Ap, 1, IBEM_FP64) != cudaSuccess) return IBEM_ERR_CUDA;
-        sub_kernel<<<nblk(N, 256), 256, 0, st>>>(N, bb, w.Ap, w.rr);
+        sub_kernel<<<nblk(cw * N, 256), 256, 0, st>>>(cw * N, bb, w.Ap, w.rr);
         double rt;
-        if (norm2(h, w.rr, N, &rt) != cudaSuccess) return IBEM_ERR_CUDA;
+        if (norm2(h, w.rr, cw * N, &rt) != cudaSuccess) return IBEM_ERR_CUDA;
         res = rt / nb;
         if (s == IBEM_OK && res > rtol * 1.0001) s = IBEM_ERR_NOCONV;
         total_it += its;
