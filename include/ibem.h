@@ -77,7 +77,10 @@ enum {
                        FP32 accumulation (inputs and outputs stay FP64)        */
 };
 
-enum { IBEM_PRECOND_NONE = 0, IBEM_PRECOND_JACOBI = 1 };
+/* Preconditioners of ibem_solve: point Jacobi on the diagonal of T A_near T^T,
+ * or block Jacobi on its diagonal blocks; a block holds the dofs whose last
+ * support element lies in one cluster of level max(0, m - 2). */
+enum { IBEM_PRECOND_NONE = 0, IBEM_PRECOND_JACOBI = 1, IBEM_PRECOND_BLOCK_JACOBI = 2 };
 
 typedef struct {
     int kernel;          /* IBEM_LAPLACE or IBEM_HELMHOLTZ                          */

@@ -96,7 +96,8 @@ void free_handle(ibem_handle* h) {
                     h->d_pairs_by_cls[1], h->d_pairs_by_cls[2], h->d_pairs_by_cls[3], h->d_pairs_by_cls[4],
                     h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_Kdf, h->d_xh2, h->d_far_rows,
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
-                    h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy};
+                    h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
+                    h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -372,6 +373,10 @@ ibem_status ibem_assemble(ibem_handle* h) {
         if ((e = launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
     }
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");
+    if (!h->d_bj_inv) {
+        std::string msg;
+        if ((e = build_block_jacobi(h, &msg))) return msg.empty() ? cuda_fail(h, e, "block-Jacobi") : fail(h, IBEM_ERR_BREAKDOWN, msg);
+    }
     h->assembled = true;
     return IBEM_OK;
 }
@@ -436,7 +441,8 @@ ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int n
     if (s) return s;
     if (nrhs < 0 || (nrhs > 0 && (!b_dev || !w_dev)) || !(rtol > 0.0) || maxit < 1)
         return fail(h, IBEM_ERR_ARG, "bad solve arguments");
-    if (precond != IBEM_PRECOND_NONE && precond != IBEM_PRECOND_JACOBI) return fail(h, IBEM_ERR_ARG, "unknown preconditioner");
+    if (precond != IBEM_PRECOND_NONE && precond != IBEM_PRECOND_JACOBI && precond != IBEM_PRECOND_BLOCK_JACOBI)
+        return fail(h, IBEM_ERR_ARG, "unknown preconditioner");
     if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
     if (nrhs == 0) return IBEM_OK;
     cudaError_t e;

@@ -286,6 +286,13 @@ struct ibem_handle {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches = 0, applications = 0;
 
+    // block-Jacobi preconditioner: blocks of dofs, inverse blocks
+    int64_t* d_bj_ptr = nullptr;
+    int64_t* d_bj_off = nullptr;
+    int32_t* d_bj_dofs = nullptr;
+    double* d_bj_inv = nullptr;
+    int64_t bj_blocks = 0;
+
     // device-side waits: bound (polls) and status word (IBEM_DEVICE_* bits)
     long long wait_limit = 1LL << 26;
     int* d_status = nullptr;
@@ -329,4 +336,6 @@ cudaError_t launch_near_diagonal(ibem_handle* h, double* diag);
 ibem_status solve_impl(ibem_handle* h, const double* b, double* w, int nrhs, double rtol,
                        int maxit, int precond, int precision, ibem_solve_info* info);
 cudaError_t ensure_workspace(ibem_handle* h, int nrhs);
+cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
+void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
 }  // namespace ibem

@@ -196,14 +196,16 @@ cudaError_t norm2(ibem_handle* h, const double* v, int64_t n, double* out) {
 // CG on A (precision prec) for A x = b, x starts at 0.  Stops when
 // |r_k| <= tol_abs (recurrence residual).  Returns iterations in *its.
 ibem_status cg(ibem_handle* h, const double* b, double* x, const Work& w, int prec, double tol_abs,
-               int maxit, bool jacobi, int* its) {
+               int maxit, int precond, int* its) {
     Plan& P = h->P;
     int64_t N = P.N;
     cudaStream_t st = h->stream;
-    const double* d = jacobi ? h->d_diag : nullptr;
+    const double* d = precond == IBEM_PRECOND_JACOBI ? h->d_diag : nullptr;
+    const bool block = precond == IBEM_PRECOND_BLOCK_JACOBI;
     cudaMemsetAsync(x, 0, N * sizeof(double), st);
     cudaMemcpyAsync(w.r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     scal_div_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.r, d, w.z);
+    if (block) apply_block_jacobi(h, w.r, w.z);
     cudaMemcpyAsync(w.p, w.z, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
     double rz;
@@ -224,6 +226,11 @@ ibem_status cg(ibem_handle* h, const double* b, double* x, const Work& w, int pr
         *its = it;
         if (!std::isfinite(rr[0])) return IBEM_ERR_BREAKDOWN;
         if (std::sqrt(rr[0]) <= tol_abs) return IBEM_OK;
+        if (block) {
+            apply_block_jacobi(h, w.r, w.z);
+            dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
+            if (readback(h, h->d_red, 1, &rr[1]) != cudaSuccess) return IBEM_ERR_CUDA;
+        }
         double beta = rr[1] / rz;
         rz = rr[1];
         xpby_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.z, beta, w.p);
@@ -238,15 +245,17 @@ ibem_status cg(ibem_handle* h, const double* b, double* x, const Work& w, int pr
 // FP64 operator, and the search direction is kept.  Convergence is decided on
 // the true residual only.  *updates counts the FP64 applications.
 ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& w, double tol_abs, int maxit,
-                        bool jacobi, int* its, int* updates) {
+                        int precond, int* its, int* updates) {
     Plan& P = h->P;
     int64_t N = P.N;
     cudaStream_t st = h->stream;
-    const double* d = jacobi ? h->d_diag : nullptr;
+    const double* d = precond == IBEM_PRECOND_JACOBI ? h->d_diag : nullptr;
+    const bool block = precond == IBEM_PRECOND_BLOCK_JACOBI;
     const double drop = 1e-2;
     cudaMemsetAsync(x, 0, N * sizeof(double), st);
     cudaMemcpyAsync(w.r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     scal_div_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.r, d, w.z);
+    if (block) apply_block_jacobi(h, w.r, w.z);
     cudaMemcpyAsync(w.p, w.z, N * sizeof(double), cudaMemcpyDeviceToDevice, st);
     dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
     double rz;
@@ -279,6 +288,11 @@ ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& 
             ref = rn;
             if (rn <= tol_abs) return IBEM_OK;
             scal_div_kernel<<<nblk(N, 256), 256, 0, st>>>(N, w.r, d, w.z);
+            if (block) apply_block_jacobi(h, w.r, w.z);
+            dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
+            if (readback(h, h->d_red, 1, &rz_new) != cudaSuccess) return IBEM_ERR_CUDA;
+        } else if (block) {
+            apply_block_jacobi(h, w.r, w.z);
             dot_kernel<<<1, 1024, 0, st>>>(w.r, w.z, N, h->d_red);
             if (readback(h, h->d_red, 1, &rz_new) != cudaSuccess) return IBEM_ERR_CUDA;
         }
@@ -294,12 +308,13 @@ ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& 
 // Givens rotations on the host.  The Arnoldi operator has precision `prec`;
 // every restart recomputes the residual b - A x with the FP64 operator, so with
 // prec = IBEM_FP32 the restarts are FP64 residual corrections.
-ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, int maxit, bool jacobi, int prec,
+ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, int maxit, int precond, int prec,
                   int restart, int* its, int* restarts) {
     Plan& P = h->P;
     const int64_t N = P.N;
     cudaStream_t st = h->stream;
-    const double* d = jacobi ? h->d_diag : nullptr;
+    const double* d = precond == IBEM_PRECOND_JACOBI ? h->d_diag : nullptr;
+    const bool block = precond == IBEM_PRECOND_BLOCK_JACOBI;
     const int m = restart;
     double *V = nullptr, *w = nullptr, *z = nullptr, *hv = nullptr;
     if (cudaMallocAsync(&V, (size_t)(m + 1) * 2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
@@ -334,7 +349,8 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         int k = 0;
         bool conv = false;
         for (int j = 0; j < m && *its < maxit; ++j) {
-            zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, z);
+            if (block) apply_block_jacobi(h, V + (size_t)j * 2 * N, z);
+            else zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, z);
             if (apply_operator(h, z, w, 1, prec) != cudaSuccess) return done(IBEM_ERR_CUDA);
             for (int i = 0; i <= j; ++i) { Hr(i, j) = 0.0; Hi(i, j) = 0.0; }
             for (int pass = 0; pass < 2; ++pass) {
@@ -401,7 +417,12 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         for (int i = 0; i < 2 * k; ++i) hh[i] = y[i];
         if (cudaMemcpyAsync(hv, hh.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
             return done(IBEM_ERR_CUDA);
-        zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, d, z);
+        if (block) {
+            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, nullptr, w);
+            apply_block_jacobi(h, w, z);
+        } else {
+            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, d, z);
+        }
         add_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, z, x);
         // restart residual with the FP64 operator
         if (apply_operator(h, x, w, 1, IBEM_FP64) != cudaSuccess) return done(IBEM_ERR_CUDA);
@@ -434,7 +455,7 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
     const int64_t NN = N * (h->helm ? 2 : 1);
     Work w{h->d_solver, h->d_solver + NN, h->d_solver + 2 * NN, h->d_solver + 3 * NN, h->d_solver + 4 * NN,
            h->d_solver + 5 * NN, h->d_solver + 6 * NN};
-    bool jac = precond == IBEM_PRECOND_JACOBI;
+
     ibem_status worst = IBEM_OK;
     int total_it = 0, total_outer = 0;
     double worst_res = 0.0;
@@ -453,12 +474,12 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
         int its = 0, outer = 0;
         double res = 0.0;
         if (h->helm) {
-            s = gmres(h, bb, ww, rtol * nb, maxit, jac, precision, 100, &its, &outer);
+            s = gmres(h, bb, ww, rtol * nb, maxit, precond, precision, 100, &its, &outer);
         } else if (precision == IBEM_FP64) {
-            s = cg(h, bb, ww, w, IBEM_FP64, rtol * nb, maxit, jac, &its);
+            s = cg(h, bb, ww, w, IBEM_FP64, rtol * nb, maxit, precond, &its);
             outer = 1;
         } else {
-            s = cg_reliable(h, bb, ww, w, rtol * nb, maxit, jac, &its, &outer);
+            s = cg_reliable(h, bb, ww, w, rtol * nb, maxit, precond, &its, &outer);
         }
         // true residual with the FP64 operator
         if (apply_operator(h, ww, w.Ap, 1, IBEM_FP64) != cudaSuccess) return IBEM_ERR_CUDA;

@@ -23,7 +23,7 @@ IBEM_ERR_NOCONV = 5
 IBEM_PATCH_NURBS, IBEM_PATCH_SPHERE_FACE = 0, 1
 IBEM_LAPLACE, IBEM_HELMHOLTZ = 0, 1
 IBEM_FP64, IBEM_FP32 = 0, 1
-IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI = 0, 1
+IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI, IBEM_PRECOND_BLOCK_JACOBI = 0, 1, 2
 
 EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",

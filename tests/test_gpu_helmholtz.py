@@ -141,3 +141,23 @@ def test_gmres_fmm_fp64_and_mixed():
     s32 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precision=1)
     assert s64.rel_residual <= 1e-8 and s32.rel_residual <= 1e-8
     ibem.ibem_destroy(h)
+
+
+def test_gmres_block_jacobi():
+    import torch
+    ibem = lib()
+    h = _handle(2, 4, 6, 4.0)
+    info = ibem.ibem_get_info(h)
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    gv = -np.exp(1j * 4.0 * (qp.cpu().numpy() @ np.array([0.6, 0.0, 0.8])))
+    gq = torch.from_numpy(np.ascontiguousarray(np.stack([gv.real, gv.imag], axis=-1))).cuda()
+    b = torch.empty((info.ndof, 2), dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, gq, 1, b)
+    w = torch.empty_like(b)
+    sj = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_JACOBI)
+    sb = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI)
+    sm = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI, precision=1)
+    assert sb.rel_residual <= 1e-8 and sm.rel_residual <= 1e-8
+    assert sb.iterations <= sj.iterations
+    ibem.ibem_destroy(h)

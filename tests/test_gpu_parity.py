@@ -197,8 +197,9 @@ def test_argument_and_state_errors():
     torch.cuda.synchronize()
     assert torch.all(y == 0)                  # A 0 = 0
     ibem.ibem_destroy(h)
-    with pytest.raises(ibem.IbemError):
-        ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(2, 2, kernel=1, kappa=4.0))
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(2, 2, kernel=1, kappa=0.0))
+    assert "kappa" in str(ei.value)
 
 
 def test_bounded_wait_failure_path_and_recovery():
@@ -218,4 +219,25 @@ def test_bounded_wait_failure_path_and_recovery():
     y2 = gpu_matvec(h, x)
     assert ibem.ibem_device_status(h) == ibem.IBEM_DEVICE_OK
     assert np.array_equal(y2, y_ok)
+    ibem.ibem_destroy(h)
+
+
+def test_block_jacobi_cg_config2():
+    # block-Jacobi CG (FP64 and mixed) reaches 1e-8 in fewer iterations than point Jacobi
+    import torch
+    ibem = lib()
+    h = handle(3, 5, q=6)
+    info = ibem.ibem_get_info(h)
+    x0 = np.array([0.9, 0.9, 0.9])
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    gq = torch.from_numpy(1.0 / (4 * np.pi * np.linalg.norm(qp.cpu().numpy() - x0, axis=1))).cuda()
+    b = torch.empty(info.ndof, dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, gq, 1, b)
+    w = torch.empty_like(b)
+    sj = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_JACOBI)
+    sb = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI)
+    sm = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=3000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI, precision=1)
+    assert sb.rel_residual <= 1e-8 and sm.rel_residual <= 1e-8
+    assert sb.iterations < sj.iterations
     ibem.ibem_destroy(h)
