@@ -250,8 +250,12 @@ def ours(args, rank, world, local_rank):
     q2 = WORKLOAD["q_cheb"] ** 2
     kpt = (q2 + 3) // 4
     coup_ms = phase_ms["coupling"]
-    entries = float(q2 * q2 * info.n_far * R)
-    kbytes = info.n_far * kpt * 4 * q2 * 8 + info.n_clusters * q2 * R * (8 + 8)
+    entries = float(q2 * q2 * info.n_far * R)          # matrix entries applied (both halves)
+    # bytes: the stored upper half of K (symmetric storage), the source moments
+    # streamed with every block, column shares written and gathered, y^ written
+    n_up = info.bytes_far // (kpt * 4 * q2 * 8)
+    kbytes = info.bytes_far + n_up * ((q2 + 1) // 2 * 2) * 8 * R + n_up * q2 * 8 * R + \
+        info.n_clusters * q2 * R * 8
     hbm_gbs, sm_max, peak_src = _peaks()
     fp32_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12            # FP32 lanes x clock
     alu_frac = (12.0 * entries / (coup_ms * 1e-3) / 1e12) / fp32_peak_tops

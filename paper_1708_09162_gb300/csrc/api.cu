@@ -97,7 +97,8 @@ void free_handle(ibem_handle* h) {
                     h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_Kdf, h->d_xh2, h->d_far_rows,
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
                     h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
-                    h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv};
+                    h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv, h->d_up_ptr, h->d_up_src,
+                    h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -289,6 +290,34 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
     TRY(upload(&h->d_far_src, P.far_src, st), "upload far src");
     TRY(upload(&h->d_far_tgt, ftgt, st), "upload far tgt");
     TRY(upload(&h->d_far_rows, h->far_rows, st), "upload far rows");
+    {
+        std::vector<int64_t> uptr(P.C + 1, 0);
+        std::vector<int32_t> usrc, utgt;
+        for (int64_t c = 0; c < P.C; ++c) {
+            for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k)
+                if (P.far_src[k] > c) {
+                    usrc.push_back(P.far_src[k]);
+                    utgt.push_back((int32_t)c);
+                }
+            uptr[c + 1] = (int64_t)usrc.size();
+            int len = (int)(uptr[c + 1] - uptr[c]);
+            if (len > 0) h->up_rows.push_back((int32_t)c);
+            if (len > h->max_up_row) h->max_up_row = len;
+        }
+        h->n_up = (int64_t)usrc.size();
+        std::vector<int64_t> tptr(P.C + 1, 0);
+        for (int32_t v : usrc) tptr[v + 1]++;
+        for (int64_t c = 0; c < P.C; ++c) tptr[c + 1] += tptr[c];
+        std::vector<int32_t> tblk(usrc.size());
+        std::vector<int64_t> fill(tptr.begin(), tptr.end() - 1);
+        for (int64_t k = 0; k < (int64_t)usrc.size(); ++k) tblk[fill[usrc[k]]++] = (int32_t)k;
+        TRY(upload(&h->d_tr_ptr, tptr, st), "upload transposed ptr");
+        TRY(upload(&h->d_tr_blk, tblk, st), "upload transposed list");
+        TRY(upload(&h->d_up_ptr, uptr, st), "upload upper far ptr");
+        TRY(upload(&h->d_up_src, usrc, st), "upload upper far src");
+        TRY(upload(&h->d_up_tgt, utgt, st), "upload upper far tgt");
+        TRY(upload(&h->d_up_rows, h->up_rows, st), "upload upper far rows");
+    }
     h->kpt = (P.q2 + 3) / 4;
 
     TRY(cudaMalloc(&h->d_qgeo, (size_t)P.nq * 4 * sizeof(double)), "alloc qgeo");
@@ -333,7 +362,8 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     info->n_near_singular[2] = P.n_cls[CLS_VERTEX];
     info->n_near_singular[3] = P.n_cls[CLS_SUBDIV];
     info->bytes_near = P.n_near * (int64_t)P.nb * P.nb * (h->helm ? 16 : 8);
-    info->bytes_far = h->far_on_the_fly ? 0 : P.n_far * (int64_t)h->kpt * 4 * P.q2 * (h->helm ? 16 : 8);
+    int64_t stored = (!h->helm && P.prm.fp64_coupling == IBEM_COUPLING_DF) ? h->n_up : P.n_far;
+    info->bytes_far = h->far_on_the_fly ? 0 : stored * (int64_t)h->kpt * 4 * P.q2 * (h->helm ? 16 : 8);
     info->assembled = h->assembled ? 1 : 0;
     return IBEM_OK;
 }
@@ -361,7 +391,8 @@ ibem_status ibem_assemble(ibem_handle* h) {
             if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
                 if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
             } else {
-                if ((e = cudaMalloc(&h->d_Kdf, nk * sizeof(float2)))) return cuda_fail(h, e, "alloc coupling matrices");
+                size_t nku = (size_t)(h->n_up > 0 ? h->n_up : 1) * h->kpt * 4 * P.q2;
+                if ((e = cudaMalloc(&h->d_Kdf, nku * sizeof(float2)))) return cuda_fail(h, e, "alloc coupling matrices");
             }
         }
     }

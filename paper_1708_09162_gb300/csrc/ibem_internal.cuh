@@ -153,16 +153,27 @@ __host__ __device__ inline void bernstein(int p, double t, double* out) {
     }
 }
 
-// Morton (Z-order) interleave of (x, y), x in the even bits.
-__host__ __device__ inline uint32_t morton2(uint32_t x, uint32_t y) {
-    uint32_t r = 0;
-    for (int b = 0; b < 16; ++b) r |= ((x >> b) & 1u) << (2 * b) | ((y >> b) & 1u) << (2 * b + 1);
-    return r;
+// Morton (Z-order) interleave of (x, y), x in the even bits (16-bit inputs).
+__host__ __device__ inline uint32_t spread_bits(uint32_t v) {
+    v &= 0x0000FFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
 }
+__host__ __device__ inline uint32_t compact_bits(uint32_t v) {
+    v &= 0x55555555u;
+    v = (v | (v >> 1)) & 0x33333333u;
+    v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+    v = (v | (v >> 4)) & 0x00FF00FFu;
+    v = (v | (v >> 8)) & 0x0000FFFFu;
+    return v;
+}
+__host__ __device__ inline uint32_t morton2(uint32_t x, uint32_t y) { return spread_bits(x) | (spread_bits(y) << 1); }
 __host__ __device__ inline void morton2_inv(uint32_t z, uint32_t* x, uint32_t* y) {
-    uint32_t a = 0, b = 0;
-    for (int k = 0; k < 16; ++k) { a |= ((z >> (2 * k)) & 1u) << k; b |= ((z >> (2 * k + 1)) & 1u) << k; }
-    *x = a; *y = b;
+    *x = compact_bits(z);
+    *y = compact_bits(z >> 1);
 }
 
 // The eight symmetries rho_k(s,t) = (a0 + a1 s + a2 t, b0 + b1 s + b2 t) of the
@@ -267,6 +278,17 @@ struct ibem_handle {
     int kpt = 0;
     std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
     int max_far_row = 0;            // longest far list
+    // upper half of the far field (source id > target id), used with symmetric storage
+    std::vector<int32_t> up_rows;
+    int max_up_row = 0;
+    int64_t n_up = 0;
+    int64_t* d_up_ptr = nullptr;
+    int32_t* d_up_src = nullptr;
+    int32_t* d_up_tgt = nullptr;
+    int32_t* d_up_rows = nullptr;
+    int64_t* d_tr_ptr = nullptr;    // transposed upper list: for each source cluster, its stored blocks
+    int32_t* d_tr_blk = nullptr;
+    float2* d_colpart = nullptr;    // per stored block and right-hand side: column share K^T x^_sigma (hi, lo)
     int32_t* d_far_rows = nullptr;
 
     // work vectors (sized for ws_nrhs right-hand sides)

@@ -122,6 +122,63 @@ __global__ void m2m_kernel(int R, int64_t nL, int64_t offL, int64_t offL1, int q
     xh[(r * C + offL + pl) * q2 + a] = acc;
 }
 
+// Separable M2M: one CTA per parent; T_c[bv][au] = sum_bu S_cx[au][bu] x_c[bv][bu],
+// x^_P[av][au] = sum_c sum_bv S_cy[av][bv] T_c[bv][au].
+__global__ void m2m_sep_kernel(int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                               int64_t C, double* __restrict__ xh) {
+    __shared__ double xc[4 * IBEM_MAX_Q * IBEM_MAX_Q], Tc[4 * IBEM_MAX_Q * IBEM_MAX_Q];
+    const int q2 = q * q;
+    const int64_t pl = blockIdx.x, r = blockIdx.y;
+    const double* src = xh + (r * C + offL1 + 4 * pl) * q2;
+    for (int i = threadIdx.x; i < 4 * q2; i += blockDim.x) xc[i] = src[i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * q2; i += blockDim.x) {
+        int c = i / q2, rem = i % q2, bv = rem / q, au = rem % q;
+        const double* Su = S + (c & 1) * q2 + au * q;
+        const double* v = xc + c * q2 + bv * q;
+        double acc = 0.0;
+        for (int bu = 0; bu < q; ++bu) acc += Su[bu] * v[bu];
+        Tc[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < q2; i += blockDim.x) {
+        int av = i / q, au = i % q;
+        double acc = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            const double* Sv = S + (c >> 1) * q2 + av * q;
+            for (int bv = 0; bv < q; ++bv) acc += Sv[bv] * Tc[c * q2 + bv * q + au];
+        }
+        xh[(r * C + offL + pl) * q2 + i] = acc;
+    }
+}
+
+// Separable L2L: one CTA per parent; U_cx[av][bu] = sum_au S_cx[au][bu] y_P[av][au],
+// y_c[bv][bu] += sum_av S_cy[av][bv] U_cx[av][bu] for the 4 children.
+__global__ void l2l_sep_kernel(int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                               int64_t C, double* __restrict__ yh) {
+    __shared__ double yp[IBEM_MAX_Q * IBEM_MAX_Q], U[2 * IBEM_MAX_Q * IBEM_MAX_Q];
+    const int q2 = q * q;
+    const int64_t pl = blockIdx.x, r = blockIdx.y;
+    for (int i = threadIdx.x; i < q2; i += blockDim.x) yp[i] = yh[(r * C + offL + pl) * q2 + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * q2; i += blockDim.x) {
+        int cx = i / q2, rem = i % q2, av = rem / q, bu = rem % q;
+        const double* Su = S + cx * q2;
+        double acc = 0.0;
+        for (int au = 0; au < q; ++au) acc += Su[au * q + bu] * yp[av * q + au];
+        U[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * q2; i += blockDim.x) {
+        int c = i / q2, rem = i % q2, bv = rem / q, bu = rem % q;
+        const double* Sv = S + (c >> 1) * q2;
+        const double* u = U + (c & 1) * q2;
+        double acc = 0.0;
+        for (int av = 0; av < q; ++av) acc += Sv[av * q + bv] * u[av * q + bu];
+        yh[(r * C + offL1 + 4 * pl + c) * q2 + rem] += acc;
+    }
+}
+
 // ---- coupling, FP64, stored K ------------------------------------------------
 // One CTA per target cluster with far blocks; thread t = 4 a + s accumulates
 // row a over columns b = s + 4 kk of every block, then the 4 lanes of a row
@@ -209,11 +266,37 @@ __device__ inline bool mbar_wait(uint64_t* bar, unsigned parity, long long limit
     return false;
 }
 
+// Laplace coupling matrices are symmetric, K_{tau sigma} = K_{sigma tau}^T (the
+// kernel and the product of surface measures are symmetric and evaluated
+// identically), so only the blocks with sigma < tau are stored.  The CTA of
+// row sigma streams them once and uses each twice: rows give
+// y^_sigma = sum K x^_tau (register accumulation, stored at the end), columns
+// give the block's share K^T x^_sigma of y^_tau (reduced across the 4 lanes
+// that share a column and stored per block in `colpart`); column_gather_kernel
+// then adds the shares to every y^_tau in a fixed order, so the result is
+// deterministic.  Both passes read K from the shared-memory stage.
+__device__ inline void df_add(float& hi, float& lo, float h2, float l2) {
+    float s = hi + h2;
+    float z = s - hi;
+    float err = (hi - (s - z)) + (h2 - z);
+    hi = s;
+    lo = lo + l2 + err;
+}
+
+__device__ inline void df_fma(float kh, float kl, float xh, float xl, float& hi, float& lo) {
+    float p = kh * xh;
+    float e = fmaf(kh, xh, -p);
+    e = fmaf(kh, xl, e);
+    e = fmaf(kl, xh, e);
+    df_add(hi, lo, p, e);
+}
+
 template <int KPT, int NST>
 __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
                                    const int32_t* __restrict__ fsrc, const float2* __restrict__ K, int q2,
                                    int q2p, int maxrow, int64_t C, const float2* __restrict__ xh,
-                                   double* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
+                                   double* __restrict__ yh, float2* __restrict__ colpart, int64_t nblk_total,
+                                   long long wait_limit, int* __restrict__ status) {
     extern __shared__ __align__(128) unsigned char smem[];
     // [0, 128): mbarriers; then the row's source clusters; then NST stages of
     // (coupling block, source moments)
@@ -226,12 +309,19 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
     const unsigned kbytes = (unsigned)belems * 8u, xbytes = (unsigned)q2p * 8u;
     const int sigma = rows[blockIdx.x];
     const int64_t r = blockIdx.y;
-    const int t = threadIdx.x, s = t & 3, a = t >> 2;
+    const int t = threadIdx.x, s = t & 3, a = t >> 2;   // row pass: row a, columns s + 4 kk
+    const int bc = t >> 2, sc = t & 3;                   // column pass: column bc, rows sc + 4 j
     const bool active = t < stride;
     const int64_t b0 = fptr[sigma];
     const int n = (int)(fptr[sigma + 1] - b0);
     const float2* xr = xh + r * C * q2p;
     for (int j = t; j < n; j += blockDim.x) srcs[j] = fsrc[b0 + j];
+    float2 xs[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+        int row = sc + 4 * j;
+        xs[j] = (active && row < q2) ? xr[(int64_t)sigma * q2p + row] : make_float2(0.f, 0.f);
+    }
     if (t == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -246,34 +336,50 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
             bulk_load(dst + belems, xr + (int64_t)srcs[i] * q2p, xbytes, &full[i]);
         }
     }
+    // FP64 work is kept off the per-block path (GB300's FP64 unit is narrow):
+    // the row sum stays double-float and is folded into `acc` every 8 blocks.
     double acc = 0.0;
+    float rh = 0.0f, rl = 0.0f;
     int i = 0;
     bool failed = false;
     for (; i < n; ++i) {
         const int st = i % NST;
         const bool ok = mbar_wait(&full[st], (unsigned)((i / NST) & 1), wait_limit);
+        float ch = 0.0f, cl = 0.0f;
         if (ok && active) {
-            const float2* Kb = stage + (size_t)st * selems + t;
-            const float2* xt = stage + (size_t)st * selems + belems;
+            const float2* Kb = stage + (size_t)st * selems;
+            const float2* xt = Kb + belems;
             float hi = 0.0f, lo = 0.0f;
 #pragma unroll
             for (int kk = 0; kk < KPT; ++kk) {
                 int b = s + 4 * kk;
                 if (b < q2) {
-                    float2 kv = Kb[kk * stride];
+                    float2 kv = Kb[kk * stride + t];
                     float2 x = xt[b];
-                    float p = kv.x * x.x;
-                    float e = fmaf(kv.x, x.x, -p);
-                    e = fmaf(kv.x, x.y, e);
-                    e = fmaf(kv.y, x.x, e);
-                    float tsum = hi + p;
-                    float z = tsum - hi;
-                    float err = (hi - (tsum - z)) + (p - z);
-                    hi = tsum;
-                    lo += err + e;
+                    df_fma(kv.x, kv.y, x.x, x.y, hi, lo);
                 }
             }
-            acc += (double)hi + (double)lo;
+            df_add(rh, rl, hi, lo);
+            if ((i & 7) == 7) {
+                acc += (double)rh + (double)rl;
+                rh = 0.0f;
+                rl = 0.0f;
+            }
+            const float2* Kc = Kb + (bc >> 2) * stride + (bc & 3) + 4 * sc;
+#pragma unroll
+            for (int j = 0; j < KPT; ++j) {
+                if (sc + 4 * j < q2) {
+                    float2 kv = Kc[16 * j];
+                    df_fma(kv.x, kv.y, xs[j].x, xs[j].y, ch, cl);
+                }
+            }
+        }
+        // columns: combine the 4 lanes that share column bc (all lanes take part)
+#pragma unroll
+        for (int off = 1; off <= 2; off <<= 1) {
+            float oh = __shfl_xor_sync(0xffffffffu, ch, off);
+            float ol = __shfl_xor_sync(0xffffffffu, cl, off);
+            df_add(ch, cl, oh, ol);
         }
         if (__syncthreads_or(!ok)) {
             failed = true;
@@ -285,7 +391,9 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
             bulk_load(dst, K + (b0 + i + NST) * (int64_t)belems, kbytes, &full[st]);
             bulk_load(dst + belems, xr + (int64_t)srcs[i + NST] * q2p, xbytes, &full[st]);
         }
+        if (active && sc == 0) colpart[(r * nblk_total + b0 + i) * q2 + bc] = make_float2(ch, cl);
     }
+    acc += (double)rh + (double)rl;
     if (failed) {
         if (t == 0) {
             atomicOr(status, 1);
@@ -298,6 +406,26 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
     if (active && s == 0) yh[(r * C + sigma) * q2 + a] = acc;
+}
+
+// y^_tau += sum over the stored blocks (sigma, tau), sigma < tau, of their column
+// shares, in the order of the transposed list.
+__global__ void column_gather_kernel(int R, int64_t C, int q2, const int64_t* __restrict__ tptr,
+                                     const int32_t* __restrict__ tblk, const float2* __restrict__ colpart,
+                                     int64_t nblk_total, double* __restrict__ yh) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R * C * q2) return;
+    int64_t r = idx / (C * q2);
+    int64_t rem = idx % (C * q2);
+    int64_t tau = rem / q2;
+    int b = (int)(rem % q2);
+    if (tptr[tau + 1] == tptr[tau]) return;
+    float hi = 0.0f, lo = 0.0f;
+    for (int64_t k = tptr[tau]; k < tptr[tau + 1]; ++k) {
+        float2 v = colpart[(r * nblk_total + tblk[k]) * q2 + b];
+        df_add(hi, lo, v.x, v.y);
+    }
+    yh[(r * C + tau) * q2 + b] += (double)hi + (double)lo;
 }
 
 // ---- coupling, FP32, kernel generated on the fly ------------------------------
@@ -471,6 +599,11 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     if ((e = cudaMalloc(&h->d_xh, nh * sizeof(double)))) return e;
     if ((e = cudaMalloc(&h->d_yh, nh * sizeof(double)))) return e;
     if ((e = cudaMalloc(&h->d_xh2, (size_t)nrhs * P.C * ((P.q2 + 1) & ~1) * sizeof(float2) + 16))) return e;
+    cudaFree(h->d_colpart);
+    h->d_colpart = nullptr;
+    if ((e = cudaMalloc(&h->d_colpart, (size_t)nrhs * (h->n_up > 0 ? h->n_up : 1) * (P.q2 > 0 ? P.q2 : 1) *
+                                           sizeof(float2))))
+        return e;
     if ((e = cudaMalloc(&h->d_xs32, ns * sizeof(float)))) return e;
     if ((e = cudaMalloc(&h->d_src32, (size_t)P.C * (P.q2 > 0 ? P.q2 : 1) * sizeof(float4)))) return e;
     if (h->helm) {
@@ -538,8 +671,8 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
             h->launches++;
             for (int L = P.m - 1; L >= 0; --L) {
                 int64_t nL = P.level_off[L + 1] - P.level_off[L];
-                m2m_kernel<<<nblk(R * nL * q2, T), T, 0, st>>>(R, nL, P.level_off[L], P.level_off[L + 1], P.q,
-                                                               h->d_S, P.C, h->d_xh);
+                m2m_sep_kernel<<<dim3((unsigned)nL, R), 64, 0, st>>>(nL, P.level_off[L], P.level_off[L + 1], P.q,
+                                                                    h->d_S, P.C, h->d_xh);
                 h->launches++;
             }
             if ((e = cudaMemsetAsync(h->d_yh, 0, (size_t)R * P.C * q2 * sizeof(double), st))) return e;
@@ -568,18 +701,19 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
                 int threads = ((4 * q2 + 31) / 32) * 32;
                 const int q2p = (q2 + 1) & ~1;
                 split_kernel<<<nblk(R * P.C * q2p, T), T, 0, st>>>(R * P.C, q2, q2p, h->d_xh, h->d_xh2);
-                dim3 grid(nrows, R);
+                dim3 grid((unsigned)h->up_rows.size(), R);
                 const size_t sbytes = ((size_t)h->kpt * 4 * q2 + q2p) * sizeof(float2);
-                const size_t head = 128 + (((size_t)h->max_far_row * 4 + 15) / 16) * 16;
+                const size_t head = 128 + (((size_t)h->max_up_row * 4 + 15) / 16) * 16;
 #define IBEM_DF_LAUNCH(K_, N_)                                                                                   \
     {                                                                                                            \
         size_t sm = head + (size_t)(N_)*sbytes;                                                                  \
         if ((e = cudaFuncSetAttribute(coupling_df_kernel<K_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                       (int)sm)))                                                                 \
             return e;                                                                                            \
-        coupling_df_kernel<K_, N_><<<grid, threads, sm, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src,         \
-                                                              h->d_Kdf, q2, q2p, h->max_far_row, P.C, h->d_xh2, \
-                                                              h->d_yh, h->wait_limit, h->d_status);              \
+        coupling_df_kernel<K_, N_><<<grid, threads, sm, st>>>(h->d_up_rows, h->d_up_ptr, h->d_up_src,            \
+                                                              h->d_Kdf, q2, q2p, h->max_up_row, P.C, h->d_xh2,  \
+                                                              h->d_yh, h->d_colpart, h->n_up, h->wait_limit,    \
+                                                              h->d_status);                                      \
     }                                                                                                            \
     break;
                 switch (h->kpt) {
@@ -597,14 +731,17 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
                     default: return cudaErrorInvalidValue;
                 }
 #undef IBEM_DF_LAUNCH
+                column_gather_kernel<<<nblk((int64_t)R * P.C * q2, T), T, 0, st>>>(R, P.C, q2, h->d_tr_ptr, h->d_tr_blk,
+                                                                                   h->d_colpart, h->n_up, h->d_yh);
+                h->launches++;
                 h->launches += 2;
             }
         }
         PhaseTimer pt(h, 3);
         for (int L = 0; L < P.m; ++L) {
-            int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
-            l2l_kernel<<<nblk(R * nL1 * q2, T), T, 0, st>>>(R, nL1, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
-                                                             P.C, h->d_yh);
+            int64_t nL = P.level_off[L + 1] - P.level_off[L];
+            l2l_sep_kernel<<<dim3((unsigned)nL, R), 64, 0, st>>>(nL, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
+                                                                P.C, h->d_yh);
             h->launches++;
         }
         leaf_back_kernel<<<nblk(R * P.E * P.nb, T), T, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, h->d_yh, leaf_off, P.C,
@@ -629,7 +766,7 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
     }
     {
         PhaseTimer pt(h, 5);
-        restrict_kernel<<<nblk(R * P.N, T), T, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, h->d_ys, P.E, y);
+        restrict_kernel<<<nblk(R * P.N, 32), 32, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, h->d_ys, P.E, y);
         h->launches++;
     }
     return cudaGetLastError();

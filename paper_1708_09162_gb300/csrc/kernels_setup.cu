@@ -336,6 +336,7 @@ __global__ void to_float_kernel(const double* __restrict__ in, float* __restrict
     if (i < n) out[i] = (float)in[i];
 }
 
+
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 cudaError_t launch_geometry_tables(ibem_handle* h) {
@@ -400,8 +401,13 @@ cudaError_t launch_near_assembly(ibem_handle* h) {
 cudaError_t launch_far_assembly(ibem_handle* h) {
     Plan& P = h->P;
     if (P.n_far == 0) return cudaSuccess;
-    int64_t total = P.n_far * (int64_t)h->kpt * 4 * P.q2;
-    far_assemble_kernel<<<nblk(total, 256), 256, 0, h->stream>>>(P.n_far, h->d_far_tgt, h->d_far_src, h->d_igeo,
+    // native: every far block; double-float: the upper half (symmetric storage)
+    const bool native = h->d_K != nullptr;
+    const int64_t nblocks = native ? P.n_far : h->n_up;
+    if (nblocks == 0) return cudaSuccess;
+    int64_t total = nblocks * (int64_t)h->kpt * 4 * P.q2;
+    far_assemble_kernel<<<nblk(total, 256), 256, 0, h->stream>>>(nblocks, native ? h->d_far_tgt : h->d_up_tgt,
+                                                                 native ? h->d_far_src : h->d_up_src, h->d_igeo,
                                                                  P.q2, h->kpt, h->d_K, h->d_Kdf);
     return cudaGetLastError();
 }
