@@ -308,6 +308,10 @@ struct ibem_handle {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     int64_t launches = 0, applications = 0;
 
+    // many-right-hand-side FP32 path (tensor-core coupling): one work area
+    void* d_mr = nullptr;
+    size_t mr_bytes = 0;
+
     // block-Jacobi preconditioner: blocks of dofs, inverse blocks
     int64_t* d_bj_ptr = nullptr;
     int64_t* d_bj_off = nullptr;
@@ -359,5 +363,7 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* w, int nrhs, dou
                        int maxit, int precond, int precision, ibem_solve_info* info);
 cudaError_t ensure_workspace(ibem_handle* h, int nrhs);
 cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
+bool mr_supported(const ibem_handle* h, int nrhs);
+cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs);
 void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
 }  // namespace ibem

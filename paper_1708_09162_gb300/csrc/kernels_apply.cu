@@ -647,6 +647,7 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
     Plan& P = h->P;
     cudaStream_t st = h->stream;
     cudaError_t e;
+    if (precision == IBEM_FP32 && mr_supported(h, nrhs)) return apply_operator_mrhs(h, x, y, nrhs);
     if (h->helm) {
         if ((e = ensure_workspace(h, 2 * nrhs))) return e;
         h->applications++;

@@ -1,0 +1,537 @@
+// Many right-hand sides at once (FP32 operator): y = T A T^T x for R right-hand
+// sides with the far-field coupling contracted on the 5th-generation tensor
+// cores (Sec. 4.2: with R columns the coupling y^_s += K_st x^_t is a dense
+// GEMM).
+//
+// Layouts put the right-hand side innermost: x* [E][nb][R], x^ [C][q2][R],
+// y* [E][nb][R]; values are float (Laplace) or float2 (Helmholtz).
+//
+// Coupling on tcgen05: one CTA per target cluster sigma.  For every far block
+// the CTA evaluates K_{sigma tau} in FP32 (rsqrt, phase reduced to [-pi, pi],
+// sine and cosine) and writes it as BF16 into a shared-memory A tile, in the
+// real form [[Kr, -Ki], [Ki, Kr]] for Helmholtz, padded to MAP = 128 rows and
+// KAP (multiple of 16) columns.  The B tile - the moments x^_tau as BF16 in the
+// same form, RP (multiple of 16) right-hand sides - is prepared once per
+// application in global memory and fetched with one cp.async.bulk per block.
+// Both tiles are double-buffered; one thread issues tcgen05.mma (kind::f16,
+// BF16 inputs, FP32 accumulation) into a TMEM accumulator [MAP lanes][RP
+// columns] that persists over the whole far row, and tcgen05.commit signals an
+// mbarrier when a buffer may be reused.  Tiles use the no-swizzle K-major
+// layout: 8 x 8 core matrices of 128 contiguous bytes, LBO = 128 bytes along
+// K, SBO = (KAP / 8) * 128 bytes along M or N.  All waits are bounded.
+#include <cuda_bf16.h>
+
+#include "ibem_internal.cuh"
+
+namespace ibem {
+
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <bool CPLX> struct MrType { typedef float T; };
+template <> struct MrType<true> { typedef float2 T; };
+
+__device__ inline float mr_zero(float) { return 0.0f; }
+__device__ inline float2 mr_zero(float2) { return make_float2(0.0f, 0.0f); }
+__device__ inline float mr_axpy(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ inline float2 mr_axpy(float a, float2 x, float2 y) { return make_float2(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y)); }
+
+// ---- layout conversion ---------------------------------------------------------------
+// x [R][N] doubles (interleaved complex) -> xt [N][R]
+template <bool CPLX>
+__global__ void mr_in_kernel(int R, int64_t N, const double* __restrict__ x, typename MrType<CPLX>::T* __restrict__ xt) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)R * N) return;
+    int64_t n = idx / R;
+    int r = (int)(idx % R);
+    if constexpr (CPLX) xt[idx] = make_float2((float)x[2 * (r * N + n)], (float)x[2 * (r * N + n) + 1]);
+    else xt[idx] = (float)x[r * N + n];
+}
+
+// ---- T^T, moments, M2M ----------------------------------------------------------------
+template <bool CPLX>
+__global__ void mr_lift_kernel(int R, int64_t E, int p, int ne1, const double* __restrict__ ext,
+                               const typename MrType<CPLX>::T* __restrict__ xt, typename MrType<CPLX>::T* __restrict__ xs) {
+    typedef typename MrType<CPLX>::T T;
+    const int pp = p + 1, nb = pp * pp, n1 = ne1 + p;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * nb * R) return;
+    int r = (int)(idx % R);
+    int64_t rem = idx / R;
+    int i = (int)(rem % nb);
+    int64_t e = rem / nb;
+    int64_t per = (int64_t)ne1 * ne1;
+    int patch = (int)(e / per);
+    uint32_t ix, iy;
+    morton2_inv((uint32_t)(e % per), &ix, &iy);
+    const int iu = i % pp, iv = i / pp;
+    T acc = mr_zero(T());
+    for (int r2 = 0; r2 < pp; ++r2) {
+        float cv = (float)ext[((int64_t)iy * pp + r2) * pp + iv];
+        for (int r1 = 0; r1 < pp; ++r1) {
+            float c = cv * (float)ext[((int64_t)ix * pp + r1) * pp + iu];
+            int64_t dof = (int64_t)patch * n1 * n1 + (int64_t)(iy + r2) * n1 + (ix + r1);
+            acc = mr_axpy(c, xt[dof * R + r], acc);
+        }
+    }
+    xs[idx] = acc;
+}
+
+template <bool CPLX>
+__global__ void mr_leaf_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                               const typename MrType<CPLX>::T* __restrict__ xs, int64_t leaf_off,
+                               typename MrType<CPLX>::T* __restrict__ xh) {
+    typedef typename MrType<CPLX>::T T;
+    const int q2 = q * q, nb = pp * pp;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * q2 * R) return;
+    int r = (int)(idx % R);
+    int64_t rem = idx / R;
+    int a = (int)(rem % q2);
+    int64_t e = rem / q2;
+    const int au = a % q, av = a / q;
+    T acc = mr_zero(T());
+    for (int iv = 0; iv < pp; ++iv)
+        for (int iu = 0; iu < pp; ++iu)
+            acc = mr_axpy((float)(M[au * pp + iu] * M[av * pp + iv]), xs[(e * nb + iv * pp + iu) * R + r], acc);
+    xh[((leaf_off + e) * q2 + a) * R + r] = acc;
+}
+
+template <bool CPLX>
+__global__ void mr_m2m_kernel(int R, int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                              typename MrType<CPLX>::T* __restrict__ xh) {
+    typedef typename MrType<CPLX>::T T;
+    const int q2 = q * q;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nL * q2 * R) return;
+    int r = (int)(idx % R);
+    int64_t rem = idx / R;
+    int a = (int)(rem % q2);
+    int64_t pl = rem / q2;
+    const int au = a % q, av = a / q;
+    T acc = mr_zero(T());
+    for (int c = 0; c < 4; ++c) {
+        const double* Su = S + (c & 1) * q2;
+        const double* Sv = S + (c >> 1) * q2;
+        const T* v = xh + ((offL1 + 4 * pl + c) * q2) * R;
+        for (int bv = 0; bv < q; ++bv)
+            for (int bu = 0; bu < q; ++bu)
+                acc = mr_axpy((float)(Su[au * q + bu] * Sv[av * q + bv]), v[(bv * q + bu) * R + r], acc);
+    }
+    xh[((offL + pl) * q2 + a) * R + r] = acc;
+}
+
+// B tiles: per cluster [RP][KAP] BF16 in the canonical no-swizzle K-major layout;
+// column k < q2 is Re x^[k] (x^[k] for Laplace), q2 <= k < 2 q2 is Im x^[k - q2].
+template <bool CPLX>
+__global__ void mr_bpack_kernel(int R, int RP, int KAP, int64_t C, int q2, const typename MrType<CPLX>::T* __restrict__ xh,
+                                __nv_bfloat16* __restrict__ xb) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= C * RP * KAP) return;
+    int k = (int)(idx % KAP);
+    int64_t rem = idx / KAP;
+    int r = (int)(rem % RP);
+    int64_t c = rem / RP;
+    float v = 0.0f;
+    if (r < R) {
+        if constexpr (CPLX) {
+            if (k < q2) v = xh[(c * q2 + k) * R + r].x;
+            else if (k < 2 * q2) v = xh[(c * q2 + k - q2) * R + r].y;
+        } else {
+            if (k < q2) v = xh[(c * q2 + k) * R + r];
+        }
+    }
+    int64_t off = c * (int64_t)RP * KAP + ((int64_t)((r >> 3) * (KAP >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7));
+    xb[off] = __float2bfloat16(v);
+}
+
+// ---- tensor-core coupling ---------------------------------------------------------------
+__device__ inline unsigned tsm(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ inline bool tc_wait(uint64_t* bar, unsigned parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(tsm(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
+    const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
+    const float4* __restrict__ geo, int q, int R, int RP, int KAP, int tcols, float kappa,
+    const __nv_bfloat16* __restrict__ xb, typename MrType<CPLX>::T* __restrict__ yh, long long wait_limit,
+    int* __restrict__ status) {
+    constexpr int MAP = 128;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bfull = reinterpret_cast<uint64_t*>(smem);        // [2]
+    uint64_t* mdone = bfull + 2;                                 // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 64);
+    int* flag = reinterpret_cast<int*>(smem + 72);
+    float4* Xs = reinterpret_cast<float4*>(smem + 128);
+    const int q2 = q * q;
+    const size_t abytes = (size_t)MAP * KAP * 2, bbytes = (size_t)RP * KAP * 2;
+    unsigned char* tiles = smem + 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024);
+    // buffer b: A tile at tiles + b * abytes, B tile at tiles + 2 * abytes + b * bbytes
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int sigma = rows[blockIdx.x];
+    const int64_t b0 = fptr[sigma];
+    const int n = (int)(fptr[sigma + 1] - b0);
+    const int K8 = KAP >> 3;
+    if (t == 0) {
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&bfull[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&mdone[i])) : "memory");
+        }
+        *flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tsm(tslot)), "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = t; i < q2; i += blockDim.x) Xs[i] = geo[(int64_t)sigma * q2 + i];
+    // padding rows / columns of both A buffers stay zero
+    for (size_t i = t; i < 2 * abytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(tiles)[i] = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(MAP >> 4) << 24);
+    const float inv4pi = 0.07957747154594767f, inv2pi = 0.15915494309189535f, twopi = 6.283185307179586f;
+    int issued = 0;          // blocks whose MMAs were committed
+    bool failed = false;
+    for (int i = 0; i < n; ++i) {
+        const int buf = i & 1;
+        bool ok = true;
+        if (i >= 2) ok = tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+        const int tau = fsrc[b0 + i];
+        if (t == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tsm(&bfull[buf])),
+                         "r"((unsigned)bbytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tsm(tiles + 2 * abytes + buf * bbytes)),
+                         "l"(xb + (int64_t)tau * RP * KAP), "r"((unsigned)bbytes), "r"(tsm(&bfull[buf]))
+                         : "memory");
+        }
+        // A tile: the coupling block in FP32, stored as BF16
+        __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tiles + buf * abytes);
+        const float4* Y = geo + (int64_t)tau * q2;
+        for (int idx = t; idx < q2 * q2; idx += blockDim.x) {
+            const int a = idx / q2, b = idx % q2;
+            const float4 X = Xs[a];
+            const float4 Yb = Y[b];
+            const float d0 = X.x - Yb.x, d1 = X.y - Yb.y, d2 = X.z - Yb.z;
+            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const float rinv = rsqrtf(r2);
+            const float w = X.w * Yb.w * rinv * inv4pi;
+            if constexpr (CPLX) {
+                float ph = kappa * (r2 * rinv);
+                ph = fmaf(-twopi, rintf(ph * inv2pi), ph);
+                float sn, cs;
+                __sincosf(ph, &sn, &cs);
+                const __nv_bfloat16 kr = __float2bfloat16(w * cs), ki = __float2bfloat16(w * sn),
+                                    mki = __float2bfloat16(-w * sn);
+                const int a2 = a + q2, bb2 = b + q2;
+                A[((a >> 3) * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7)] = kr;
+                A[((a >> 3) * K8 + (bb2 >> 3)) * 64 + (a & 7) * 8 + (bb2 & 7)] = mki;
+                A[((a2 >> 3) * K8 + (b >> 3)) * 64 + (a2 & 7) * 8 + (b & 7)] = ki;
+                A[((a2 >> 3) * K8 + (bb2 >> 3)) * 64 + (a2 & 7) * 8 + (bb2 & 7)] = kr;
+            } else {
+                A[((a >> 3) * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7)] = __float2bfloat16(w);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bool bok = true;
+        if (t == 0) bok = tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), wait_limit);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (__syncthreads_or(!bok)) {
+            failed = true;
+            // the copy for this block may still land: wait for it before leaving
+            if (t == 0) tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), 1LL << 24);
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t == 0) {
+            for (int kk = 0; kk < KAP / 16; ++kk) {
+                const uint64_t ad = umma_desc(tsm(A) + kk * 256, 128, K8 * 128);
+                const uint64_t bd = umma_desc(tsm(tiles + 2 * abytes + buf * bbytes) + kk * 256, 128, K8 * 128);
+                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tsm(&mdone[buf]))
+                         : "memory");
+        }
+        issued = i + 1;
+    }
+    // wait for the last committed MMAs (bounded), then read the accumulator
+    bool ok = true;
+    if (issued > 0) {
+        const int last = issued - 1;
+        ok = tc_wait(&mdone[last & 1], (unsigned)((last >> 1) & 1), failed ? (1LL << 24) : wait_limit);
+        if (issued > 1) {
+            const int prev = issued - 2;
+            tc_wait(&mdone[prev & 1], (unsigned)((prev >> 1) & 1), 1LL << 24);
+        }
+    }
+    if (__syncthreads_or(!ok || failed)) {
+        if (t == 0) atomicOr(status, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int row = 32 * warp + lane;
+        const int mvalid = CPLX ? 2 * q2 : q2;
+        for (int c0 = 0; c0 < RP; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < mvalid) {
+                for (int j = 0; j < 16; ++j) {
+                    const int r = c0 + j;
+                    if (r >= R) break;
+                    const float val = __uint_as_float(v[j]);
+                    if constexpr (CPLX) {
+                        float* dst = reinterpret_cast<float*>(yh + ((int64_t)sigma * q2 + (row % q2)) * R + r);
+                        dst[row < q2 ? 0 : 1] = val;
+                    } else {
+                        yh[((int64_t)sigma * q2 + row) * R + r] = val;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// ---- L2L, back-projection, near field, restriction ---------------------------------------
+template <bool CPLX>
+__global__ void mr_l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                              typename MrType<CPLX>::T* __restrict__ yh) {
+    typedef typename MrType<CPLX>::T T;
+    const int q2 = q * q;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nL1 * q2 * R) return;
+    int r = (int)(idx % R);
+    int64_t rem = idx / R;
+    int b = (int)(rem % q2);
+    int64_t cl = rem / q2;
+    const int bu = b % q, bv = b / q, c = (int)(cl & 3);
+    const double* Su = S + (c & 1) * q2;
+    const double* Sv = S + (c >> 1) * q2;
+    const T* v = yh + ((offL + cl / 4) * q2) * R;
+    T acc = mr_zero(T());
+    for (int av = 0; av < q; ++av)
+        for (int au = 0; au < q; ++au)
+            acc = mr_axpy((float)(Su[au * q + bu] * Sv[av * q + bv]), v[(av * q + au) * R + r], acc);
+    T* o = yh + ((offL1 + cl) * q2 + b) * R + r;
+    if constexpr (CPLX) *o = make_float2(o->x + acc.x, o->y + acc.y);
+    else *o += acc;
+}
+
+template <bool CPLX>
+__global__ void mr_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+                               const typename MrType<CPLX>::T* __restrict__ yh, int64_t leaf_off,
+                               typename MrType<CPLX>::T* __restrict__ ys) {
+    typedef typename MrType<CPLX>::T T;
+    const int q2 = q * q, nb = pp * pp;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * nb * R) return;
+    int r = (int)(idx % R);
+    int64_t rem = idx / R;
+    int i = (int)(rem % nb);
+    int64_t e = rem / nb;
+    const int iu = i % pp, iv = i / pp;
+    T acc = mr_zero(T());
+    for (int av = 0; av < q; ++av)
+        for (int au = 0; au < q; ++au)
+            acc = mr_axpy((float)(M[au * pp + iu] * M[av * pp + iv]), yh[((leaf_off + e) * q2 + av * q + au) * R + r],
+                          acc);
+    ys[idx] = acc;
+}
+
+// one CTA per target element; thread (i, r) over the row's near blocks
+template <bool CPLX>
+__global__ void mr_near_kernel(int R, int nb, const int64_t* __restrict__ nptr, const int32_t* __restrict__ nsrc,
+                               const float* __restrict__ blocks, const typename MrType<CPLX>::T* __restrict__ xs,
+                               typename MrType<CPLX>::T* __restrict__ ys) {
+    typedef typename MrType<CPLX>::T T;
+    const int64_t e = blockIdx.x;
+    const int nbb = nb * nb;
+    for (int o = threadIdx.x; o < nb * R; o += blockDim.x) {
+        const int i = o / R, r = o % R;
+        float ar = 0.0f, ai = 0.0f;
+        for (int64_t k = nptr[e]; k < nptr[e + 1]; ++k) {
+            const int64_t s = nsrc[k];
+            for (int j = 0; j < nb; ++j) {
+                const T x = xs[(s * nb + j) * R + r];
+                if constexpr (CPLX) {
+                    const float br = blocks[2 * (k * nbb + i * nb + j)], bi = blocks[2 * (k * nbb + i * nb + j) + 1];
+                    ar = fmaf(br, x.x, fmaf(-bi, x.y, ar));
+                    ai = fmaf(br, x.y, fmaf(bi, x.x, ai));
+                } else {
+                    ar = fmaf(blocks[k * nbb + i * nb + j], x, ar);
+                }
+            }
+        }
+        T* out = ys + (e * nb + i) * R + r;
+        if constexpr (CPLX) *out = make_float2(out->x + ar, out->y + ai);
+        else *out += ar;
+    }
+}
+
+// y [R][N] (doubles, interleaved complex) = T y*
+template <bool CPLX>
+__global__ void mr_restrict_kernel(int R, int64_t N, int p, int ne1, const double* __restrict__ ext,
+                                   const typename MrType<CPLX>::T* __restrict__ ys, double* __restrict__ y) {
+    typedef typename MrType<CPLX>::T T;
+    const int pp = p + 1, nb = pp * pp, n1 = ne1 + p;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * N) return;
+    int r = (int)(idx % R);
+    int64_t dof = idx / R;
+    int patch = (int)(dof / ((int64_t)n1 * n1));
+    int rem = (int)(dof % ((int64_t)n1 * n1));
+    int jv = rem / n1, ju = rem % n1;
+    int64_t per = (int64_t)ne1 * ne1;
+    double ar = 0.0, ai = 0.0;
+    for (int iy = jv - p; iy <= jv; ++iy) {
+        if (iy < 0 || iy >= ne1) continue;
+        for (int ix = ju - p; ix <= ju; ++ix) {
+            if (ix < 0 || ix >= ne1) continue;
+            const int64_t e = patch * per + morton2(ix, iy);
+            const double* cu = ext + ((int64_t)ix * pp + (ju - ix)) * pp;
+            const double* cv = ext + ((int64_t)iy * pp + (jv - iy)) * pp;
+            for (int iv = 0; iv < pp; ++iv)
+                for (int iu = 0; iu < pp; ++iu) {
+                    const double c = cu[iu] * cv[iv];
+                    const T v = ys[(e * nb + iv * pp + iu) * R + r];
+                    if constexpr (CPLX) {
+                        ar += c * v.x;
+                        ai += c * v.y;
+                    } else {
+                        ar += c * v;
+                    }
+                }
+        }
+    }
+    if constexpr (CPLX) {
+        y[2 * (r * N + dof)] = ar;
+        y[2 * (r * N + dof) + 1] = ai;
+    } else {
+        y[r * N + dof] = ar;
+    }
+}
+
+template <bool CPLX>
+static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
+    typedef typename MrType<CPLX>::T T;
+    Plan& P = h->P;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    const int T_ = 256;
+    const int q2 = P.q2;
+    const int RP = (R + 15) & ~15;
+    const int KAP = ((CPLX ? 2 * q2 : q2) + 15) & ~15;
+    // work space (grown on demand)
+    const size_t need_t = (size_t)R * P.N, need_s = (size_t)R * P.Nstar, need_h = (size_t)R * P.C * (q2 > 0 ? q2 : 1);
+    const size_t need_b = (size_t)P.C * RP * (KAP > 0 ? KAP : 16);
+    const size_t bytes = sizeof(T) * (need_t + 2 * need_s + 2 * need_h) + 2 * need_b + 1024;
+    if (bytes > h->mr_bytes) {
+        cudaFree(h->d_mr);
+        h->d_mr = nullptr;
+        h->mr_bytes = 0;
+        if ((e = cudaMalloc(&h->d_mr, bytes))) return e;
+        h->mr_bytes = bytes;
+    }
+    T* xt = reinterpret_cast<T*>(h->d_mr);
+    T* xs = xt + need_t;
+    T* ys = xs + need_s;
+    T* xh = ys + need_s;
+    T* yh = xh + need_h;
+    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(
+        reinterpret_cast<unsigned char*>(h->d_mr) + (((sizeof(T) * (need_t + 2 * need_s + 2 * need_h)) + 255) / 256) * 256);
+    mr_in_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, x, xt);
+    mr_lift_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.p, P.ne1, h->d_ext, xt, xs);
+    h->launches += 2;
+    if ((e = cudaMemsetAsync(ys, 0, need_s * sizeof(T), st))) return e;
+    if (P.q > 0) {
+        const int64_t leaf_off = P.level_off[P.m];
+        mr_leaf_kernel<CPLX><<<nblk(P.E * q2 * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, xs, leaf_off, xh);
+        h->launches++;
+        for (int L = P.m - 1; L >= 0; --L) {
+            int64_t nL = P.level_off[L + 1] - P.level_off[L];
+            mr_m2m_kernel<CPLX><<<nblk(nL * q2 * R, T_), T_, 0, st>>>(R, nL, P.level_off[L], P.level_off[L + 1], P.q,
+                                                                      h->d_S, xh);
+            h->launches++;
+        }
+        if ((e = cudaMemsetAsync(yh, 0, need_h * sizeof(T), st))) return e;
+        const unsigned nrows = (unsigned)h->far_rows.size();
+        if (nrows > 0) {
+            mr_bpack_kernel<CPLX><<<nblk((int64_t)P.C * RP * KAP, T_), T_, 0, st>>>(R, RP, KAP, P.C, q2, xh, xb);
+            int tcols = 32;
+            while (tcols < RP) tcols <<= 1;
+            const size_t sm = 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024) + 2 * (size_t)128 * KAP * 2 +
+                              2 * (size_t)RP * KAP * 2;
+            if ((e = cudaFuncSetAttribute(mr_coupling_tc_kernel<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)))
+                return e;
+            mr_coupling_tc_kernel<CPLX><<<nrows, 128, sm, st>>>(
+                h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const float4*>(h->d_igeo32), P.q, R, RP,
+                KAP, tcols, (float)P.prm.kappa, xb, yh, h->wait_limit, h->d_status);
+            h->launches += 2;
+        }
+        for (int L = 0; L < P.m; ++L) {
+            int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
+            mr_l2l_kernel<CPLX><<<nblk(nL1 * q2 * R, T_), T_, 0, st>>>(R, nL1, P.level_off[L], P.level_off[L + 1], P.q,
+                                                                       h->d_S, yh);
+            h->launches++;
+        }
+        mr_back_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, yh, leaf_off, ys);
+        h->launches++;
+    }
+    int nthreads = P.nb * R < 512 ? ((P.nb * R + 31) / 32) * 32 : 512;
+    mr_near_kernel<CPLX><<<(unsigned)P.E, nthreads, 0, st>>>(R, P.nb, h->d_near_ptr, h->d_near_src, h->d_near32, xs, ys);
+    mr_restrict_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, ys, y);
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+bool mr_supported(const ibem_handle* h, int nrhs) {
+    const Plan& P = h->P;
+    if (nrhs < 16 || nrhs > 256) return false;
+    if (P.q == 0) return true;
+    return (h->helm ? 2 * P.q2 : P.q2) <= 128;
+}
+
+cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs) {
+    h->applications++;
+    return h->helm ? mr_apply<true>(h, x, y, nrhs) : mr_apply<false>(h, x, y, nrhs);
+}
+
+}  // namespace ibem

@@ -11,8 +11,6 @@
 
 namespace ibem {
 
-static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
-
 // One CTA per block: entries (i, j) of T A_near T^T on the block's dofs.
 // CW = 1 (real) or 2 (complex, blocks of double2).
 template <int CW>

@@ -347,7 +347,6 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int k = 0;
-        bool conv = false;
         for (int j = 0; j < m && *its < maxit; ++j) {
             if (block) apply_block_jacobi(h, V + (size_t)j * 2 * N, z);
             else zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, z);
@@ -399,7 +398,7 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
             ++*its;
             double res = std::sqrt(g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1]);
             if (!std::isfinite(res)) return done(IBEM_ERR_BREAKDOWN);
-            if (res <= tol_abs || hn == 0.0) { conv = true; break; }
+            if (res <= tol_abs || hn == 0.0) break;
             dscal_copy_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, 1.0 / hn, w, V + (size_t)(j + 1) * 2 * N);
         }
         // back substitution R y = g (complex, upper triangular k x k)
@@ -428,7 +427,6 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         if (apply_operator(h, x, w, 1, IBEM_FP64) != cudaSuccess) return done(IBEM_ERR_CUDA);
         sub_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, b, w, w);
         ++*restarts;
-        (void)conv;
     }
     if (status != IBEM_OK) {
         double beta;
