@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64-coupling comparison")
+    ap.add_argument("--no-config3", action="store_true", help="skip the many-right-hand-side Helmholtz section")
+    ap.add_argument("--config3-only", action="store_true", help="run only the many-right-hand-side section")
+    ap.add_argument("--config3-m", type=int, default=6, help="refinement level of that section (profiling)")
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -182,6 +185,81 @@ def _peaks():
         return 6800.0, 2070.0, "fallback"
 
 
+def helmholtz_many_rhs(ibem, stream, world, barrier, args):
+    """Exterior Helmholtz, kappa = 4, p = 2, m = 6, q = 8, 64 incident plane waves
+    (seeded uniform directions): the FP32 operator with the coupling on the
+    tensor cores, its error against the FP64 operator on one right-hand side,
+    and the roofline of the tensor-core coupling kernel."""
+    import numpy as np
+    import torch
+    p, m, q, kappa, R = 2, args.config3_m, 8, 4.0, 64
+    t0 = time.perf_counter()
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=ibem.IBEM_HELMHOLTZ,
+                                                                 kappa=kappa), stream)
+    ibem.ibem_assemble(h)
+    setup_s = time.perf_counter() - t0
+    info = ibem.ibem_get_info(h)
+    N = info.ndof
+    rng = np.random.default_rng(SEED + 3)
+    d = rng.normal(size=(R, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    torch.cuda.synchronize()
+    ph = qp.cpu().numpy() @ d.T                                    # [nq, R]
+    g = -np.exp(1j * kappa * ph).T                                 # sound-soft data, [R, nq]
+    gq = torch.from_numpy(np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))).cuda()
+    b = torch.empty((R, N, 2), dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, gq, R, b)
+    y = torch.empty_like(b)
+    steps = max(3, args.steps // 20)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ibem.ibem_matvec(h, b, y, R, ibem.IBEM_FP32)
+    barrier()
+    ibem.ibem_profile_enable(h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            ibem.ibem_matvec(h, b, y, R, ibem.IBEM_FP32)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / steps
+    prof = ibem.ibem_profile_read(h)
+    ibem.ibem_profile_enable(h, False)
+    coup_ms = prof["ms"]["coupling"] / steps
+    phases = {k: v / steps for k, v in prof["ms"].items()}
+    # FP64 operator on the first right-hand side (coupling generated on the fly in FP64)
+    y64 = torch.empty((1, N, 2), dtype=torch.float64, device="cuda")
+    t1 = time.perf_counter()
+    ibem.ibem_matvec(h, b[:1].contiguous(), y64, 1, ibem.IBEM_FP64)
+    torch.cuda.synchronize()
+    fp64_s = time.perf_counter() - t1
+    err = float((y[0] - y64[0]).abs().max() / y64[0].abs().max())
+    q2 = q * q
+    flops = 2.0 * 128 * 128 * 64 * info.n_far                      # real-form GEMM per far block
+    peak = 1912.6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = json.load(f).get("bf16_tflops", peak)
+    except OSError:
+        pass
+    sfu = 3.0 * q2 * q2 * info.n_far                               # rsqrt, sine, cosine per complex entry
+    sfu_peak = 152 * 16 * 2070e6
+    ibem.ibem_destroy(h)
+    return {"workload": "helmholtz-sphere-p2-m%d-q8-k4-R64" % m, "ndof": N, "ndof_super": info.ndof_super,
+            "n_near": info.n_near, "n_far": info.n_far, "nrhs": R, "setup_s": setup_s,
+            "value": world * N * R / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "coupling_ms": coup_ms,
+            "phase_ms": phases,
+            "rel_err_vs_fp64_rhs0": err, "fp64_one_rhs_s": fp64_s,
+            "tensor": {"kernel": "mr_coupling_tc_kernel", "achieved_tflops": flops / (coup_ms * 1e-3) / 1e12,
+                       "peak_tflops": peak, "frac": flops / (coup_ms * 1e-3) / 1e12 / peak,
+                       "sfu_frac": sfu / (coup_ms * 1e-3) / sfu_peak,
+                       "note": "K is generated per block on the SFU (rsqrt, sine, cosine); the tensor pipe waits "
+                               "for it"}}
+
+
 # ---------------------------------------------------------------- our arm
 def ours(args, rank, world, local_rank):
     import numpy as np
@@ -201,6 +279,11 @@ def ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     stream = torch.cuda.Stream()
+    if args.config3_only:
+        out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
+        if rank == 0:
+            print(json.dumps({"helmholtz_64rhs": out}), flush=True)
+        return
     prm = ibem.make_params(WORKLOAD["p"], WORKLOAD["m"], q_cheb=WORKLOAD["q_cheb"], eta=WORKLOAD["eta"])
     t0 = time.perf_counter()
     h = ibem.ibem_create(ibem.sphere_patches(), prm, stream)
@@ -346,6 +429,9 @@ def ours(args, rank, world, local_rank):
                                      "fp64_updates": s32.outer, "rel_residual": s32.rel_residual},
                            "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}
 
+    # ---- Helmholtz, 64 plane waves: tensor-core coupling ----
+    config3 = None if args.no_config3 else helmholtz_many_rhs(ibem, stream, world, barrier, args)
+
     # ---- oracle on the host cores (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -369,6 +455,7 @@ def ours(args, rank, world, local_rank):
             "solve": solve,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "helmholtz_64rhs": config3,
             "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
                     "d2h_bytes_per_step": N * R * 8},
             "gpu_launches": prof["launches"],

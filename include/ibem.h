@@ -75,8 +75,8 @@ enum {
     IBEM_FP64 = 0,  /* FP64-accurate near field and coupling                   */
     IBEM_FP32 = 1   /* FP32 near blocks, coupling generated on the fly in FP32,
                        FP32 accumulation (inputs and outputs stay FP64).  With
-                       16..256 right-hand sides (and 2 q^2 <= 128 for Helmholtz,
-                       q^2 <= 128 for Laplace) the coupling is contracted on the
+                       16..256 right-hand sides (and q even, 2 q^2 <= 128 for
+                       Helmholtz, q^2 <= 128 for Laplace) the coupling is contracted on the
                        tensor cores: K and the moments in BF16, FP32 accumulation */
 };
 

@@ -98,7 +98,7 @@ void free_handle(ibem_handle* h) {
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
                     h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
                     h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv, h->d_up_ptr, h->d_up_src,
-                    h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr};
+                    h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr, h->d_Mf, h->d_Sf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -264,6 +264,9 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
             }
         TRY(upload(&h->d_M, M, st), "upload M");
         TRY(upload(&h->d_S, S, st), "upload S");
+        std::vector<float> Mf(M.begin(), M.end()), Sf(S.begin(), S.end());
+        TRY(upload(&h->d_Mf, Mf, st), "upload Mf");
+        TRY(upload(&h->d_Sf, Sf, st), "upload Sf");
     }
 
     // near and far lists

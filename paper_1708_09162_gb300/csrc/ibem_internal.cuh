@@ -252,6 +252,8 @@ struct ibem_handle {
     int rule_n[3] = {0, 0, 0};
     double* d_M = nullptr;          // [q][pp] 1D leaf moments int L_a B_i (times h)
     double* d_S = nullptr;          // [2][q][q] 1D M2M: S_c[a][b] = L_a((c + z_b) / 2)
+    float* d_Mf = nullptr;          // FP32 copies of M and S for the FP32 many-right-hand-side path
+    float* d_Sf = nullptr;
 
     // near field
     int64_t* d_near_ptr = nullptr;
@@ -325,6 +327,30 @@ struct ibem_handle {
 };
 
 namespace ibem {
+// Phase timer: records an event pair on the stream while profiling is on.
+struct PhaseTimer {
+    ibem_handle* h;
+    int phase;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t take() {
+        cudaEvent_t ev = nullptr;
+        if (!h->ev_free.empty()) { ev = h->ev_free.back(); h->ev_free.pop_back(); }
+        else cudaEventCreate(&ev);
+        return ev;
+    }
+    PhaseTimer(ibem_handle* hh, int ph) : h(hh), phase(ph) {
+        if (!h->prof) return;
+        a = take();
+        b = take();
+        cudaEventRecord(a, h->stream);
+    }
+    ~PhaseTimer() {
+        if (!a) return;
+        cudaEventRecord(b, h->stream);
+        h->ev_used.push_back({phase, {a, b}});
+    }
+};
+
 // real kernels of kernels_apply.cu reused by the complex (Helmholtz) path
 __global__ void lift_kernel(int R, int64_t E, int p, int ne1, const double* __restrict__ ext,
                             const double* __restrict__ x, int64_t N, double* __restrict__ xs);

@@ -617,31 +617,7 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     return cudaSuccess;
 }
 
-namespace {
-// Phase timer: records an event pair on the stream while profiling is on.
-struct PhaseTimer {
-    ibem_handle* h;
-    int phase;
-    cudaEvent_t a = nullptr, b = nullptr;
-    cudaEvent_t take() {
-        cudaEvent_t ev = nullptr;
-        if (!h->ev_free.empty()) { ev = h->ev_free.back(); h->ev_free.pop_back(); }
-        else cudaEventCreate(&ev);
-        return ev;
-    }
-    PhaseTimer(ibem_handle* hh, int ph) : h(hh), phase(ph) {
-        if (!h->prof) return;
-        a = take();
-        b = take();
-        cudaEventRecord(a, h->stream);
-    }
-    ~PhaseTimer() {
-        if (!a) return;
-        cudaEventRecord(b, h->stream);
-        h->ev_used.push_back({phase, {a, b}});
-    }
-};
-}  // namespace
+
 
 cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs, int precision) {
     Plan& P = h->P;

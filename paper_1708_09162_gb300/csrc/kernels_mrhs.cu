@@ -77,7 +77,7 @@ __global__ void mr_lift_kernel(int R, int64_t E, int p, int ne1, const double* _
 }
 
 template <bool CPLX>
-__global__ void mr_leaf_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+__global__ void mr_leaf_kernel(int R, int64_t E, int pp, int q, const float* __restrict__ M,
                                const typename MrType<CPLX>::T* __restrict__ xs, int64_t leaf_off,
                                typename MrType<CPLX>::T* __restrict__ xh) {
     typedef typename MrType<CPLX>::T T;
@@ -92,32 +92,96 @@ __global__ void mr_leaf_kernel(int R, int64_t E, int pp, int q, const double* __
     T acc = mr_zero(T());
     for (int iv = 0; iv < pp; ++iv)
         for (int iu = 0; iu < pp; ++iu)
-            acc = mr_axpy((float)(M[au * pp + iu] * M[av * pp + iv]), xs[(e * nb + iv * pp + iu) * R + r], acc);
+            acc = mr_axpy(M[au * pp + iu] * M[av * pp + iv], xs[(e * nb + iv * pp + iu) * R + r], acc);
     xh[((leaf_off + e) * q2 + a) * R + r] = acc;
 }
 
+// Separable M2M, one CTA per (parent, chunk of RC right-hand sides):
+// T_c[bv][au] = sum_bu S_cx[au][bu] x_c[bv][bu], x_P[av][au] = sum_c sum_bv S_cy[av][bv] T_c[bv][au].
+constexpr int MR_RC = 8;
 template <bool CPLX>
-__global__ void mr_m2m_kernel(int R, int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
-                              typename MrType<CPLX>::T* __restrict__ xh) {
+__global__ void mr_m2m_sep_kernel(int R, int64_t offL, int64_t offL1, int q, const float* __restrict__ S,
+                                  typename MrType<CPLX>::T* __restrict__ xh) {
     typedef typename MrType<CPLX>::T T;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
     const int q2 = q * q;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nL * q2 * R) return;
-    int r = (int)(idx % R);
-    int64_t rem = idx / R;
-    int a = (int)(rem % q2);
-    int64_t pl = rem / q2;
-    const int au = a % q, av = a / q;
-    T acc = mr_zero(T());
-    for (int c = 0; c < 4; ++c) {
-        const double* Su = S + (c & 1) * q2;
-        const double* Sv = S + (c >> 1) * q2;
-        const T* v = xh + ((offL1 + 4 * pl + c) * q2) * R;
-        for (int bv = 0; bv < q; ++bv)
-            for (int bu = 0; bu < q; ++bu)
-                acc = mr_axpy((float)(Su[au * q + bu] * Sv[av * q + bv]), v[(bv * q + bu) * R + r], acc);
+    T* xc = reinterpret_cast<T*>(sm_raw);               // [4][q2][RC]
+    T* Tc = xc + 4 * q2 * MR_RC;                        // [4][q][q][RC]
+    float* Ss = reinterpret_cast<float*>(Tc + 4 * q2 * MR_RC);   // [2][q][q]
+    const int64_t pl = blockIdx.x;
+    const int r0 = blockIdx.y * MR_RC;
+    const int rc = R - r0 < MR_RC ? R - r0 : MR_RC;
+    for (int i = threadIdx.x; i < 2 * q2; i += blockDim.x) Ss[i] = S[i];
+    for (int i = threadIdx.x; i < 4 * q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, cb = i / MR_RC;        // cb = c * q2 + b
+        xc[i] = r < rc ? xh[((offL1 + 4 * pl) * q2 + cb) * R + r0 + r] : mr_zero(T());
     }
-    xh[((offL + pl) * q2 + a) * R + r] = acc;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, rest = i / MR_RC;
+        const int c = rest / q2, bv = (rest % q2) / q, au = rest % q;
+        const float* Su = Ss + (c & 1) * q2 + au * q;
+        const T* v = xc + (c * q2 + bv * q) * MR_RC + r;
+        T acc = mr_zero(T());
+        for (int bu = 0; bu < q; ++bu) acc = mr_axpy(Su[bu], v[bu * MR_RC], acc);
+        Tc[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, a = i / MR_RC, av = a / q, au = a % q;
+        if (r >= rc) continue;
+        T acc = mr_zero(T());
+        for (int c = 0; c < 4; ++c) {
+            const float* Sv = Ss + (c >> 1) * q2 + av * q;
+            const T* tv = Tc + (c * q2 + au) * MR_RC + r;
+            for (int bv = 0; bv < q; ++bv) acc = mr_axpy(Sv[bv], tv[bv * q * MR_RC], acc);
+        }
+        xh[((offL + pl) * q2 + a) * R + r0 + r] = acc;
+    }
+}
+
+// Separable L2L, one CTA per (parent, chunk): U_cx[av][bu] = sum_au S_cx[au][bu] y_P[av][au],
+// y_c[bv][bu] += sum_av S_cy[av][bv] U_cx[av][bu].
+template <bool CPLX>
+__global__ void mr_l2l_sep_kernel(int R, int64_t offL, int64_t offL1, int q, const float* __restrict__ S,
+                                  typename MrType<CPLX>::T* __restrict__ yh) {
+    typedef typename MrType<CPLX>::T T;
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    const int q2 = q * q;
+    T* yp = reinterpret_cast<T*>(sm_raw);               // [q2][RC]
+    T* U = yp + q2 * MR_RC;                             // [2][q][q][RC]
+    float* Ss = reinterpret_cast<float*>(U + 2 * q2 * MR_RC);
+    const int64_t pl = blockIdx.x;
+    const int r0 = blockIdx.y * MR_RC;
+    const int rc = R - r0 < MR_RC ? R - r0 : MR_RC;
+    for (int i = threadIdx.x; i < 2 * q2; i += blockDim.x) Ss[i] = S[i];
+    for (int i = threadIdx.x; i < q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, a = i / MR_RC;
+        yp[i] = r < rc ? yh[((offL + pl) * q2 + a) * R + r0 + r] : mr_zero(T());
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, rest = i / MR_RC;
+        const int cx = rest / q2, av = (rest % q2) / q, bu = rest % q;
+        const float* Su = Ss + cx * q2;
+        const T* v = yp + (av * q) * MR_RC + r;
+        T acc = mr_zero(T());
+        for (int au = 0; au < q; ++au) acc = mr_axpy(Su[au * q + bu], v[au * MR_RC], acc);
+        U[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * q2 * MR_RC; i += blockDim.x) {
+        const int r = i % MR_RC, rest = i / MR_RC;
+        const int c = rest / q2, bv = (rest % q2) / q, bu = rest % q;
+        if (r >= rc) continue;
+        const float* Sv = Ss + (c >> 1) * q2;
+        const T* u = U + ((c & 1) * q2 + bu) * MR_RC + r;
+        T acc = mr_zero(T());
+        for (int av = 0; av < q; ++av) acc = mr_axpy(Sv[av * q + bv], u[av * q * MR_RC], acc);
+        T* o = yh + ((offL1 + 4 * pl + c) * q2 + bv * q + bu) * R + r0 + r;
+        if constexpr (CPLX) *o = make_float2(o->x + acc.x, o->y + acc.y);
+        else *o += acc;
+    }
 }
 
 // B tiles: per cluster [RP][KAP] BF16 in the canonical no-swizzle K-major layout;
@@ -166,7 +230,7 @@ __device__ inline bool tc_wait(uint64_t* bar, unsigned parity, long long limit) 
 }
 
 template <bool CPLX>
-__global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
+__global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
     const float4* __restrict__ geo, int q, int R, int RP, int KAP, int tcols, float kappa,
     const __nv_bfloat16* __restrict__ xb, typename MrType<CPLX>::T* __restrict__ yh, long long wait_limit,
@@ -182,7 +246,7 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
     const size_t abytes = (size_t)MAP * KAP * 2, bbytes = (size_t)RP * KAP * 2;
     unsigned char* tiles = smem + 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024);
     // buffer b: A tile at tiles + b * abytes, B tile at tiles + 2 * abytes + b * bbytes
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nwarps = blockDim.x >> 5;
     const int sigma = rows[blockIdx.x];
     const int64_t b0 = fptr[sigma];
     const int n = (int)(fptr[sigma + 1] - b0);
@@ -200,7 +264,11 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = t; i < q2; i += blockDim.x) Xs[i] = geo[(int64_t)sigma * q2 + i];
+    for (int i = t; i < q2; i += blockDim.x) {
+        float4 g = geo[(int64_t)sigma * q2 + i];
+        g.w *= 0.07957747154594767f;   // k / (4 pi)
+        Xs[i] = g;
+    }
     // padding rows / columns of both A buffers stay zero
     for (size_t i = t; i < 2 * abytes / 16; i += blockDim.x) reinterpret_cast<uint4*>(tiles)[i] = make_uint4(0, 0, 0, 0);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -209,7 +277,6 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(MAP >> 4) << 24);
-    const float inv4pi = 0.07957747154594767f, inv2pi = 0.15915494309189535f, twopi = 6.283185307179586f;
     int issued = 0;          // blocks whose MMAs were committed
     bool failed = false;
     for (int i = 0; i < n; ++i) {
@@ -227,31 +294,59 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
                          "l"(xb + (int64_t)tau * RP * KAP), "r"((unsigned)bbytes), "r"(tsm(&bfull[buf]))
                          : "memory");
         }
-        // A tile: the coupling block in FP32, stored as BF16
+        // A tile: the coupling block in FP32, stored as BF16.  A warp fills one
+        // 8 x 8 core matrix per step (lane -> row lane / 4, columns 2 (lane % 4)
+        // and +1) with packed 4-byte stores: 128 contiguous bytes, no bank conflicts.
         __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tiles + buf * abytes);
         const float4* Y = geo + (int64_t)tau * q2;
-        for (int idx = t; idx < q2 * q2; idx += blockDim.x) {
-            const int a = idx / q2, b = idx % q2;
+        const int q8 = (q2 + 7) >> 3;
+        // quadrant offsets of the real form when q2 is a multiple of 8
+        const int offR = (q2 >> 3) * 64, offD = (q2 >> 3) * K8 * 64;
+        const bool aligned8 = (q2 & 7) == 0;
+        for (int cm = warp; cm < q8 * q8; cm += nwarps) {
+            const int ca = cm / q8, cb = cm - ca * q8;
+            const int a = 8 * ca + (lane >> 2), b = 8 * cb + 2 * (lane & 3);
+            if (a >= q2 || b >= q2) continue;   // q2 is even, so b + 1 < q2 as well
             const float4 X = Xs[a];
-            const float4 Yb = Y[b];
-            const float d0 = X.x - Yb.x, d1 = X.y - Yb.y, d2 = X.z - Yb.z;
-            const float r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            const float rinv = rsqrtf(r2);
-            const float w = X.w * Yb.w * rinv * inv4pi;
+            float wr[2], wi[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float4 Yb = Y[b + u];
+                const float d0 = X.x - Yb.x, d1 = X.y - Yb.y, d2 = X.z - Yb.z;
+                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+                const float rinv = rsqrtf(r2);
+                const float w = X.w * Yb.w * rinv;          // X.w holds k / (4 pi)
+                if constexpr (CPLX) {
+                    // |kappa r| stays within a few periods here; the hardware sine
+                    // and cosine are accurate far below the BF16 rounding of K
+                    float sn, cs;
+                    __sincosf(kappa * (r2 * rinv), &sn, &cs);
+                    wr[u] = w * cs;
+                    wi[u] = w * sn;
+                } else {
+                    wr[u] = w;
+                    wi[u] = 0.0f;
+                }
+            }
+            const int base = (ca * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7);
+            const __nv_bfloat162 kr = __floats2bfloat162_rn(wr[0], wr[1]);
+            reinterpret_cast<__nv_bfloat162*>(A + base)[0] = kr;
             if constexpr (CPLX) {
-                float ph = kappa * (r2 * rinv);
-                ph = fmaf(-twopi, rintf(ph * inv2pi), ph);
-                float sn, cs;
-                __sincosf(ph, &sn, &cs);
-                const __nv_bfloat16 kr = __float2bfloat16(w * cs), ki = __float2bfloat16(w * sn),
-                                    mki = __float2bfloat16(-w * sn);
-                const int a2 = a + q2, bb2 = b + q2;
-                A[((a >> 3) * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7)] = kr;
-                A[((a >> 3) * K8 + (bb2 >> 3)) * 64 + (a & 7) * 8 + (bb2 & 7)] = mki;
-                A[((a2 >> 3) * K8 + (b >> 3)) * 64 + (a2 & 7) * 8 + (b & 7)] = ki;
-                A[((a2 >> 3) * K8 + (bb2 >> 3)) * 64 + (a2 & 7) * 8 + (bb2 & 7)] = kr;
-            } else {
-                A[((a >> 3) * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7)] = __float2bfloat16(w);
+                const __nv_bfloat162 mki = __floats2bfloat162_rn(-wi[0], -wi[1]);
+                const __nv_bfloat162 ki = __floats2bfloat162_rn(wi[0], wi[1]);
+                if (aligned8) {
+                    reinterpret_cast<__nv_bfloat162*>(A + base + offR)[0] = mki;
+                    reinterpret_cast<__nv_bfloat162*>(A + base + offD)[0] = ki;
+                    reinterpret_cast<__nv_bfloat162*>(A + base + offD + offR)[0] = kr;
+                } else {
+                    auto at = [&](int m, int k) -> __nv_bfloat162* {
+                        return reinterpret_cast<__nv_bfloat162*>(A + ((m >> 3) * K8 + (k >> 3)) * 64 + (m & 7) * 8 +
+                                                                 (k & 7));
+                    };
+                    *at(a, b + q2) = mki;
+                    *at(a + q2, b) = ki;
+                    *at(a + q2, b + q2) = kr;
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -294,7 +389,8 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
     }
     if (__syncthreads_or(!ok || failed)) {
         if (t == 0) atomicOr(status, 1);
-    } else {
+    } else if (warp < 4) {
+        // warps 0..3 own TMEM lane quarters 0..3
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = 32 * warp + lane;
         const int mvalid = CPLX ? 2 * q2 : q2;
@@ -331,31 +427,7 @@ __global__ void __launch_bounds__(128) mr_coupling_tc_kernel(
 
 // ---- L2L, back-projection, near field, restriction ---------------------------------------
 template <bool CPLX>
-__global__ void mr_l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
-                              typename MrType<CPLX>::T* __restrict__ yh) {
-    typedef typename MrType<CPLX>::T T;
-    const int q2 = q * q;
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nL1 * q2 * R) return;
-    int r = (int)(idx % R);
-    int64_t rem = idx / R;
-    int b = (int)(rem % q2);
-    int64_t cl = rem / q2;
-    const int bu = b % q, bv = b / q, c = (int)(cl & 3);
-    const double* Su = S + (c & 1) * q2;
-    const double* Sv = S + (c >> 1) * q2;
-    const T* v = yh + ((offL + cl / 4) * q2) * R;
-    T acc = mr_zero(T());
-    for (int av = 0; av < q; ++av)
-        for (int au = 0; au < q; ++au)
-            acc = mr_axpy((float)(Su[au * q + bu] * Sv[av * q + bv]), v[(av * q + au) * R + r], acc);
-    T* o = yh + ((offL1 + cl) * q2 + b) * R + r;
-    if constexpr (CPLX) *o = make_float2(o->x + acc.x, o->y + acc.y);
-    else *o += acc;
-}
-
-template <bool CPLX>
-__global__ void mr_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
+__global__ void mr_back_kernel(int R, int64_t E, int pp, int q, const float* __restrict__ M,
                                const typename MrType<CPLX>::T* __restrict__ yh, int64_t leaf_off,
                                typename MrType<CPLX>::T* __restrict__ ys) {
     typedef typename MrType<CPLX>::T T;
@@ -370,8 +442,7 @@ __global__ void mr_back_kernel(int R, int64_t E, int pp, int q, const double* __
     T acc = mr_zero(T());
     for (int av = 0; av < q; ++av)
         for (int au = 0; au < q; ++au)
-            acc = mr_axpy((float)(M[au * pp + iu] * M[av * pp + iv]), yh[((leaf_off + e) * q2 + av * q + au) * R + r],
-                          acc);
+            acc = mr_axpy(M[au * pp + iu] * M[av * pp + iv], yh[((leaf_off + e) * q2 + av * q + au) * R + r], acc);
     ys[idx] = acc;
 }
 
@@ -419,7 +490,7 @@ __global__ void mr_restrict_kernel(int R, int64_t N, int p, int ne1, const doubl
     int rem = (int)(dof % ((int64_t)n1 * n1));
     int jv = rem / n1, ju = rem % n1;
     int64_t per = (int64_t)ne1 * ne1;
-    double ar = 0.0, ai = 0.0;
+    float ar = 0.0f, ai = 0.0f;
     for (int iy = jv - p; iy <= jv; ++iy) {
         if (iy < 0 || iy >= ne1) continue;
         for (int ix = ju - p; ix <= ju; ++ix) {
@@ -429,7 +500,7 @@ __global__ void mr_restrict_kernel(int R, int64_t N, int p, int ne1, const doubl
             const double* cv = ext + ((int64_t)iy * pp + (jv - iy)) * pp;
             for (int iv = 0; iv < pp; ++iv)
                 for (int iu = 0; iu < pp; ++iu) {
-                    const double c = cu[iu] * cv[iv];
+                    const float c = (float)cu[iu] * (float)cv[iv];
                     const T v = ys[(e * nb + iv * pp + iu) * R + r];
                     if constexpr (CPLX) {
                         ar += c * v.x;
@@ -476,23 +547,31 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
     T* yh = xh + need_h;
     __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(
         reinterpret_cast<unsigned char*>(h->d_mr) + (((sizeof(T) * (need_t + 2 * need_s + 2 * need_h)) + 255) / 256) * 256);
-    mr_in_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, x, xt);
-    mr_lift_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.p, P.ne1, h->d_ext, xt, xs);
-    h->launches += 2;
+    {
+        PhaseTimer pt(h, 0);
+        mr_in_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, x, xt);
+        mr_lift_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.p, P.ne1, h->d_ext, xt, xs);
+        h->launches += 2;
+    }
     if ((e = cudaMemsetAsync(ys, 0, need_s * sizeof(T), st))) return e;
     if (P.q > 0) {
         const int64_t leaf_off = P.level_off[P.m];
-        mr_leaf_kernel<CPLX><<<nblk(P.E * q2 * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, xs, leaf_off, xh);
-        h->launches++;
-        for (int L = P.m - 1; L >= 0; --L) {
-            int64_t nL = P.level_off[L + 1] - P.level_off[L];
-            mr_m2m_kernel<CPLX><<<nblk(nL * q2 * R, T_), T_, 0, st>>>(R, nL, P.level_off[L], P.level_off[L + 1], P.q,
-                                                                      h->d_S, xh);
+        {
+            PhaseTimer pt(h, 1);
+            mr_leaf_kernel<CPLX><<<nblk(P.E * q2 * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_Mf, xs, leaf_off, xh);
             h->launches++;
+            const size_t smm = (size_t)8 * q2 * MR_RC * sizeof(T) + 2 * q2 * sizeof(float);
+            for (int L = P.m - 1; L >= 0; --L) {
+                int64_t nL = P.level_off[L + 1] - P.level_off[L];
+                mr_m2m_sep_kernel<CPLX><<<dim3((unsigned)nL, (R + MR_RC - 1) / MR_RC), 256, smm, st>>>(
+                    R, P.level_off[L], P.level_off[L + 1], P.q, h->d_Sf, xh);
+                h->launches++;
+            }
         }
         if ((e = cudaMemsetAsync(yh, 0, need_h * sizeof(T), st))) return e;
         const unsigned nrows = (unsigned)h->far_rows.size();
         if (nrows > 0) {
+            PhaseTimer pt(h, 2);
             mr_bpack_kernel<CPLX><<<nblk((int64_t)P.C * RP * KAP, T_), T_, 0, st>>>(R, RP, KAP, P.C, q2, xh, xb);
             int tcols = 32;
             while (tcols < RP) tcols <<= 1;
@@ -501,23 +580,32 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
             if ((e = cudaFuncSetAttribute(mr_coupling_tc_kernel<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm)))
                 return e;
-            mr_coupling_tc_kernel<CPLX><<<nrows, 128, sm, st>>>(
+            mr_coupling_tc_kernel<CPLX><<<nrows, 512, sm, st>>>(
                 h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const float4*>(h->d_igeo32), P.q, R, RP,
                 KAP, tcols, (float)P.prm.kappa, xb, yh, h->wait_limit, h->d_status);
             h->launches += 2;
         }
+        PhaseTimer pt(h, 3);
+        const size_t sml = (size_t)3 * q2 * MR_RC * sizeof(T) + 2 * q2 * sizeof(float);
         for (int L = 0; L < P.m; ++L) {
-            int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
-            mr_l2l_kernel<CPLX><<<nblk(nL1 * q2 * R, T_), T_, 0, st>>>(R, nL1, P.level_off[L], P.level_off[L + 1], P.q,
-                                                                       h->d_S, yh);
+            int64_t nL = P.level_off[L + 1] - P.level_off[L];
+            mr_l2l_sep_kernel<CPLX><<<dim3((unsigned)nL, (R + MR_RC - 1) / MR_RC), 256, sml, st>>>(
+                R, P.level_off[L], P.level_off[L + 1], P.q, h->d_Sf, yh);
             h->launches++;
         }
-        mr_back_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_M, yh, leaf_off, ys);
+        mr_back_kernel<CPLX><<<nblk(P.E * P.nb * R, T_), T_, 0, st>>>(R, P.E, P.pp, P.q, h->d_Mf, yh, leaf_off, ys);
         h->launches++;
     }
     int nthreads = P.nb * R < 512 ? ((P.nb * R + 31) / 32) * 32 : 512;
-    mr_near_kernel<CPLX><<<(unsigned)P.E, nthreads, 0, st>>>(R, P.nb, h->d_near_ptr, h->d_near_src, h->d_near32, xs, ys);
-    mr_restrict_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, ys, y);
+    {
+        PhaseTimer pt(h, 4);
+        mr_near_kernel<CPLX><<<(unsigned)P.E, nthreads, 0, st>>>(R, P.nb, h->d_near_ptr, h->d_near_src, h->d_near32, xs,
+                                                                 ys);
+    }
+    {
+        PhaseTimer pt(h, 5);
+        mr_restrict_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, ys, y);
+    }
     h->launches += 2;
     return cudaGetLastError();
 }
@@ -526,7 +614,8 @@ bool mr_supported(const ibem_handle* h, int nrhs) {
     const Plan& P = h->P;
     if (nrhs < 16 || nrhs > 256) return false;
     if (P.q == 0) return true;
-    return (h->helm ? 2 * P.q2 : P.q2) <= 128;
+    // even q: the A tile is written in aligned pairs of columns
+    return (P.q % 2 == 0) && (h->helm ? 2 * P.q2 : P.q2) <= 128;
 }
 
 cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs) {
