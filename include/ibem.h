@@ -107,7 +107,10 @@ typedef struct {
  * generates the coupling on the fly in FP64 (also chosen automatically when the
  * stored complex matrices would exceed half of the free device memory).  All
  * variants reproduce the FP64 oracle to 1e-12. */
-enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1 };
+enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2 };
+/* IBEM_COUPLING_NONE stores no FP64 coupling matrices (memory for large
+ * batches): the FP32 operator is available; the FP64 operator of a Laplace
+ * handle then returns IBEM_ERR_STATE, Helmholtz generates it on the fly. */
 
 typedef struct {
     int64_t ndof;          /* dim S_{p,m} = n (2^m + p)^2                          */
@@ -238,6 +241,30 @@ ibem_status ibem_device_status(ibem_handle* h, int* status);
 #define IBEM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_dev, int nrhs,
                                    const double* pts_dev, int64_t npts, double* u_dev);
+
+/* ---- Batches of uneven instances (spec batching; no counterpart in the
+ * paper) ----
+ * A batch applies the FP32 operator of many assembled handles (different
+ * geometry, level, degree, kernel and number of right-hand sides) together:
+ * every stage runs as one launch over all instances, the far-field coupling as
+ * one persistent kernel balancing (instance, right-hand side, target cluster)
+ * items through an atomic counter, and the application is captured once into a
+ * CUDA graph and replayed.  The coupling kernel's CTA size is autotuned at
+ * creation.  Handles must be assembled, with q_cheb in 2..8, on the current
+ * device; they must outlive the batch.  nrhs[i] in 1..256.  `cuda_stream`
+ * (NULL: the batch creates its own non-default stream). */
+typedef struct ibem_batch ibem_batch;
+ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrhs, void* cuda_stream,
+                              ibem_batch** out);
+/* offsets[0..n]: instance i's input and output occupy doubles offsets[i] ..
+ * offsets[i+1] of the concatenated arrays ([nrhs_i][ndof_i], complex interleaved). */
+ibem_status ibem_batch_offsets(const ibem_batch* b, int64_t* offsets);
+/* y = A x for every instance (FP32 operator, FP64 in and out), enqueued on the
+ * batch stream as one graph launch (captured on first use for this (x, y) pair). */
+ibem_status ibem_batch_matvec(ibem_batch* b, const double* x_dev, double* y_dev);
+/* kernel launches in one application, and the autotuned coupling CTA size. */
+ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads);
+ibem_status ibem_batch_destroy(ibem_batch* b);
 
 /* Host-only: build the block cluster tree without a GPU and return its lists.
  * Call once with null arrays to get the counts.  near: [n_near][8] int32 =

@@ -116,6 +116,12 @@ ibem_status check_ready(ibem_handle* h) {
 
 cudaError_t set_device(ibem_handle* h) { return cudaSetDevice(h->device); }
 
+// the FP64 operator needs stored coupling matrices for Laplace (Helmholtz can
+// generate them on the fly)
+bool fp64_available(const ibem_handle* h) {
+    return h->helm || h->P.n_far == 0 || h->d_K || h->d_Kdf;
+}
+
 }  // namespace
 
 extern "C" {
@@ -385,11 +391,10 @@ ibem_status ibem_assemble(ibem_handle* h) {
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             size_t free_b = 0, total_b = 0;
             cudaMemGetInfo(&free_b, &total_b);
-            h->far_on_the_fly =
-                P.prm.fp64_coupling == IBEM_COUPLING_NATIVE || nk * sizeof(float4) > free_b / 2;
+            h->far_on_the_fly = P.prm.fp64_coupling != IBEM_COUPLING_DF || nk * sizeof(float4) > free_b / 2;
             if (!h->far_on_the_fly)
                 if ((e = cudaMalloc(&h->d_Kc, nk * sizeof(float4)))) return cuda_fail(h, e, "alloc coupling matrices");
-        } else if (P.n_far > 0) {
+        } else if (P.n_far > 0 && P.prm.fp64_coupling != IBEM_COUPLING_NONE) {
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
                 if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
@@ -441,6 +446,8 @@ ibem_status ibem_matvec(ibem_handle* h, const double* x_dev, double* y_dev, int 
     if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
     if (x_dev == y_dev) return fail(h, IBEM_ERR_ARG, "x and y must not overlap");
     if (nrhs == 0) return IBEM_OK;
+    if (precision == IBEM_FP64 && !fp64_available(h))
+        return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
     cudaError_t e;
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
     if ((e = apply_operator(h, x_dev, y_dev, nrhs, precision))) return cuda_fail(h, e, "matvec");
@@ -450,6 +457,8 @@ ibem_status ibem_matvec(ibem_handle* h, const double* x_dev, double* y_dev, int 
 ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrhs, int precision) {
     ibem_status s = check_ready(h);
     if (s) return s;
+    if (precision == IBEM_FP64 && !fp64_available(h))
+        return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
     if (nrhs < 0 || (nrhs > 0 && (!x || !y))) return fail(h, IBEM_ERR_ARG, "bad matvec arguments");
     if (nrhs == 0) return IBEM_OK;
     cudaError_t e;
@@ -479,6 +488,7 @@ ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int n
         return fail(h, IBEM_ERR_ARG, "unknown preconditioner");
     if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
     if (nrhs == 0) return IBEM_OK;
+    if (!fp64_available(h)) return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
     cudaError_t e;
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
     s = solve_impl(h, b_dev, w_dev, nrhs, rtol, maxit, precond, precision, info);

@@ -624,6 +624,9 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
     cudaStream_t st = h->stream;
     cudaError_t e;
     if (precision == IBEM_FP32 && mr_supported(h, nrhs)) return apply_operator_mrhs(h, x, y, nrhs);
+    // the FP64 Laplace coupling needs stored matrices (absent with IBEM_COUPLING_NONE)
+    if (!h->helm && precision == IBEM_FP64 && P.q > 0 && !h->far_rows.empty() && !h->d_K && !h->d_Kdf)
+        return cudaErrorInvalidValue;
     if (h->helm) {
         if ((e = ensure_workspace(h, 2 * nrhs))) return e;
         h->applications++;

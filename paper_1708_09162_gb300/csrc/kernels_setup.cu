@@ -400,7 +400,8 @@ cudaError_t launch_near_assembly(ibem_handle* h) {
 
 cudaError_t launch_far_assembly(ibem_handle* h) {
     Plan& P = h->P;
-    if (P.n_far == 0) return cudaSuccess;
+    // nothing stored (IBEM_COUPLING_NONE) or no far field: nothing to assemble
+    if (P.n_far == 0 || (!h->d_K && !h->d_Kdf)) return cudaSuccess;
     // native: every far block; double-float: the upper half (symmetric storage)
     const bool native = h->d_K != nullptr;
     const int64_t nblocks = native ? P.n_far : h->n_up;

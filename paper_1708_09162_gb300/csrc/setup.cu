@@ -223,8 +223,9 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.q_cheb != 0 && !(q.eta > 0.0)) return "eta must be > 0";
     if (q.gauss_regular < 1 || q.gauss_regular > 16) return "gauss_regular must be in 1..16";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
-    if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE)
-        return "fp64_coupling must be IBEM_COUPLING_DF or IBEM_COUPLING_NATIVE";
+    if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
+        q.fp64_coupling != IBEM_COUPLING_NONE)
+        return "fp64_coupling must be IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE or IBEM_COUPLING_NONE";
     P.prm = q;
     P.npatch = npatch;
     P.p = q.p;

@@ -28,7 +28,8 @@ IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI, IBEM_PRECOND_BLOCK_JACOBI = 0, 1, 2
 EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
             "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
-            "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc")
+            "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc",
+            "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy")
 
 
 class IbemError(RuntimeError):
@@ -92,6 +93,11 @@ def _load():
         "ibem_profile_enable": (I32, [P, I32]),
         "ibem_profile_read": (I32, [P, ctypes.POINTER(ibem_profile_data)]),
         "ibem_set_wait_limit": (I32, [P, ctypes.c_longlong]),
+        "ibem_batch_create": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), P, ctypes.POINTER(P)]),
+        "ibem_batch_offsets": (I32, [P, ctypes.POINTER(I64)]),
+        "ibem_batch_matvec": (I32, [P, P, P]),
+        "ibem_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "ibem_batch_destroy": (I32, [P]),
         "ibem_device_status": (I32, [P, ctypes.POINTER(I32)]),
         "ibem_last_error": (ctypes.c_char_p, [P]),
         "ibem_status_string": (ctypes.c_char_p, [I32]),
@@ -163,7 +169,7 @@ def nurbs_patches(specs):
     return arr
 
 
-IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE = 0, 1
+IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE = 0, 1, 2
 
 
 def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8,
@@ -264,6 +270,36 @@ def ibem_device_status(h):
     st = ctypes.c_int()
     _check(_lib.ibem_device_status(h, ctypes.byref(st)), h)
     return st.value
+
+
+def ibem_batch_create(handles, nrhs, stream=None):
+    n = len(handles)
+    arr = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    rr = (ctypes.c_int * n)(*nrhs)
+    b = ctypes.c_void_p()
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.ibem_batch_create(arr, n, rr, sp, ctypes.byref(b)))
+    return b
+
+
+def ibem_batch_offsets(b, n):
+    off = (ctypes.c_int64 * (n + 1))()
+    _check(_lib.ibem_batch_offsets(b, off))
+    return list(off)
+
+
+def ibem_batch_matvec(b, x, y):
+    _check(_lib.ibem_batch_matvec(b, _dptr(x), _dptr(y)))
+
+
+def ibem_batch_info(b):
+    l, t = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.ibem_batch_info(b, ctypes.byref(l), ctypes.byref(t)))
+    return {"launches_per_apply": l.value, "coupling_threads": t.value}
+
+
+def ibem_batch_destroy(b):
+    _check(_lib.ibem_batch_destroy(b))
 
 
 def ibem_last_error(h=None):

@@ -1,0 +1,69 @@
+"""Batched application of uneven instances (one launch per stage over all
+instances, persistent coupling kernel, CUDA graph): every instance must match
+its own FP64 operator to FP32 accuracy, and replays must be identical."""
+import numpy as np
+import pytest
+
+from gpu_common import lib, rel_err
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [  # (kernel, kappa, p, m, q, R, radius, center)
+    (0, 0.0, 1, 3, 6, 3, 1.0, (0.0, 0.0, 0.0)),
+    (1, 2.0, 2, 2, 6, 2, 1.0, (0.0, 0.0, 0.0)),
+    (0, 0.0, 3, 2, 6, 1, 1.0, (0.0, 0.0, 0.0)),
+    (1, 5.0, 1, 3, 8, 4, 0.7, (0.2, 0.0, -0.1)),
+    (0, 0.0, 2, 4, 6, 5, 1.0, (0.0, 0.0, 0.0)),
+    (0, 0.0, 2, 3, 8, 2, 1.8, (1.0, -2.0, 0.5)),
+]
+
+
+def test_batched_uneven_instances():
+    import torch
+    ibem = lib()
+    handles = []
+    for kern, kappa, p, m, q, R, rad, cen in SPECS:
+        h = ibem.ibem_create(ibem.sphere_patches(rad, cen), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=kern,
+                                                                             kappa=kappa))
+        ibem.ibem_assemble(h)
+        handles.append(h)
+    nrhs = [s[5] for s in SPECS]
+    b = ibem.ibem_batch_create(handles, nrhs)
+    off = ibem.ibem_batch_offsets(b, len(handles))
+    rng = np.random.default_rng(42)
+    x = torch.from_numpy(rng.normal(size=off[-1])).cuda()
+    y1 = torch.zeros_like(x)
+    y2 = torch.zeros_like(x)
+    ibem.ibem_batch_matvec(b, x, y1)
+    ibem.ibem_batch_matvec(b, x, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    info = ibem.ibem_batch_info(b)
+    assert info["launches_per_apply"] <= 2 * max(s[3] for s in SPECS) + 8
+    assert info["coupling_threads"] in (128, 256, 512)
+    for i, (h, spec) in enumerate(zip(handles, SPECS)):
+        R = spec[5]
+        xi = x[off[i]:off[i + 1]].contiguous()
+        y64 = torch.empty_like(xi)
+        ibem.ibem_matvec(h, xi, y64, R, 0)
+        torch.cuda.synchronize()
+        yb = y1[off[i]:off[i + 1]].cpu().numpy()
+        assert rel_err(yb, y64.cpu().numpy()) < 2e-5, (i, rel_err(yb, y64.cpu().numpy()))
+    ibem.ibem_batch_destroy(b)
+    for h in handles:
+        ibem.ibem_destroy(h)
+
+
+def test_coupling_none_refuses_fp64():
+    import torch
+    ibem = lib()
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(1, 3, q_cheb=6, fp64_coupling=2))
+    ibem.ibem_assemble(h)
+    N = ibem.ibem_get_info(h).ndof
+    x = torch.ones(N, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_matvec(h, x, y, 1, 0)
+    assert ei.value.status == "IBEM_ERR_STATE"
+    ibem.ibem_matvec(h, x, y, 1, 1)        # FP32 operator still available
+    ibem.ibem_destroy(h)
