@@ -93,3 +93,52 @@ def potential(disc, w, points):
         U = fundamental_solution(disc.kernel, points[:, None, :], F[None, :, :])
         u += U @ ((wq * k)[:, None] * dens)
     return u
+
+
+def fgmres(apply_A, b, precond, rtol=1e-8, restart=100, maxit=1000, record=None):
+    """Flexible GMRES (Saad, SIAM J. Sci. Comput. 14, 1993): right
+    preconditioning where the preconditioner may change from step to step, so
+    the preconditioned vectors z_k = precond(v_k) are kept and the iterate is
+    x = x0 + Z y.  Arnoldi with two passes of classical Gram-Schmidt; the
+    small least-squares problem is solved by numpy.linalg.lstsq.
+
+    With ``record`` a list, the iterate x_k after every step of the first cycle
+    is appended to it (used to form residual/error training pairs)."""
+    n = b.shape[0]
+    dt = np.result_type(b, np.complex128)
+    x = np.zeros(n, dtype=dt)
+    nb = np.linalg.norm(b)
+    total = 0
+    cycle = 0
+    while total < maxit:
+        r = b - apply_A(x)
+        beta = np.linalg.norm(r)
+        if beta <= rtol * nb:
+            return x, total
+        V = np.zeros((n, restart + 1), dtype=dt)
+        Z = np.zeros((n, restart), dtype=dt)
+        H = np.zeros((restart + 1, restart), dtype=dt)
+        V[:, 0] = r / beta
+        k_done = 0
+        for k in range(restart):
+            Z[:, k] = precond(V[:, k])
+            w = apply_A(Z[:, k])
+            for _ in range(2):
+                h = V[:, :k + 1].conj().T @ w
+                w = w - V[:, :k + 1] @ h
+                H[:k + 1, k] += h
+            H[k + 1, k] = np.linalg.norm(w)
+            k_done = k + 1
+            total += 1
+            e1 = np.zeros(k + 2, dtype=dt)
+            e1[0] = beta
+            y, *_ = np.linalg.lstsq(H[:k + 2, :k + 1], e1, rcond=None)
+            if record is not None and cycle == 0:
+                record.append(x + Z[:, :k + 1] @ y)
+            res = np.linalg.norm(H[:k + 2, :k + 1] @ y - e1)
+            if H[k + 1, k].real == 0.0 or res <= rtol * nb or total >= maxit:
+                break
+            V[:, k + 1] = w / H[k + 1, k]
+        x = x + Z[:, :k_done] @ y
+        cycle += 1
+    return x, total
