@@ -73,17 +73,22 @@ enum { IBEM_LAPLACE = 0, IBEM_HELMHOLTZ = 1 };   /* Eqs. fundament1 / fundament2
 /* Arithmetic of the operator application. */
 enum {
     IBEM_FP64 = 0,  /* FP64-accurate near field and coupling                   */
-    IBEM_FP32 = 1   /* FP32 near blocks, coupling generated on the fly in FP32,
+    IBEM_FP32 = 1,  /* FP32 near blocks, coupling generated on the fly in FP32,
                        FP32 accumulation (inputs and outputs stay FP64).  With
                        16..256 right-hand sides (and q even, 2 q^2 <= 128 for
                        Helmholtz, q^2 <= 128 for Laplace) the coupling is contracted on the
                        tensor cores: K and the moments in BF16, FP32 accumulation */
+    IBEM_BF16 = 2   /* network entries only (ibem_cnn_*): BF16 activations and
+                       weights, FP32 accumulation                              */
 };
 
 /* Preconditioners of ibem_solve: point Jacobi on the diagonal of T A_near T^T,
  * or block Jacobi on its diagonal blocks; a block holds the dofs whose last
  * support element lies in one cluster of level max(0, m - 2). */
-enum { IBEM_PRECOND_NONE = 0, IBEM_PRECOND_JACOBI = 1, IBEM_PRECOND_BLOCK_JACOBI = 2 };
+enum { IBEM_PRECOND_NONE = 0, IBEM_PRECOND_JACOBI = 1, IBEM_PRECOND_BLOCK_JACOBI = 2,
+       IBEM_PRECOND_LEARNED = 3   /* block-Jacobi plus the correction of an attached
+                                     network, flexible GMRES (Helmholtz only); see
+                                     ibem_set_learned_preconditioner */ };
 
 typedef struct {
     int kernel;          /* IBEM_LAPLACE or IBEM_HELMHOLTZ                          */
@@ -275,6 +280,95 @@ ibem_status ibem_batch_destroy(ibem_batch* b);
  * of the target cluster then of the source cluster.  Lists are sorted. */
 ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_params* params,
                             int64_t* n_near, int32_t* near, int64_t* n_far, int32_t* far);
+
+/* ---------------------------------------------------------------------------
+ * Learned right preconditioner.  The paper has no counterpart (it preconditions
+ * with Jacobi, Sec. 4 item 3); this is an addition of the library.
+ *
+ * Images: a complex vector of S_{p,m} is, patch by patch, an image of two
+ * channels (real, imaginary part) and n1 x n1 pixels, pixel (j_v, j_u) of patch
+ * k holding dof k * n1^2 + j_v * n1 + j_u.  Image arrays are FP32 device
+ * memory [B][2][H][W].
+ *
+ * Network: four 3 x 3 convolutions with zero padding, channels
+ * 2 -> C -> C -> C -> 2, ReLU after the first three.  Parameters are FP32,
+ * flat, layer by layer: W[cout][cin][3][3] then bias[cout].  Loss of a batch of
+ * B images: (1 / 2B) sum (net(in) - target)^2.  Optimiser: Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected).
+ *
+ * Preconditioner: with s = B^-1 v the block-Jacobi vector and
+ * sigma = |s| / sqrt(2 ndof), z = s + sigma * net(s / sigma) (network in BF16).
+ * ibem_solve with IBEM_PRECOND_LEARNED runs flexible GMRES(100) with it.
+ *
+ * A network object is tied to the device current at creation and to the
+ * stream given there (the preconditioner runs on the handle's stream).  It may
+ * be attached to several handles; it must outlive them or be detached first.
+ * --------------------------------------------------------------------------- */
+typedef struct ibem_cnn ibem_cnn;
+
+/* augmentation flags of ibem_cnn_train */
+enum { IBEM_AUGMENT_PHASE = 1,      /* multiply input and target by e^{i theta}  */
+       IBEM_AUGMENT_DIHEDRAL = 2 }; /* same symmetry of the square on both (H == W) */
+
+/* New network with `channels` hidden channels (1..32), He-initialised from
+ * `seed` (last layer scaled by 1/4, zero biases).  Synchronises. */
+ibem_status ibem_cnn_create(int channels, unsigned long long seed, void* cuda_stream, ibem_cnn** out);
+ibem_status ibem_cnn_destroy(ibem_cnn* cnn);
+
+/* Parameter count into *count (if not null); copies the parameters to
+ * get_host (if not null) after loading set_host (if not null; this also
+ * resets the Adam state).  Synchronises. */
+ibem_status ibem_cnn_params(ibem_cnn* cnn, float* get_host, const float* set_host, size_t* count);
+
+/* out_dev = net(in_dev) for B images of H x W; precision IBEM_FP32 or
+ * IBEM_BF16.  Enqueues only. */
+ibem_status ibem_cnn_forward(ibem_cnn* cnn, const float* in_dev, int B, int H, int W, float* out_dev,
+                             int precision);
+
+/* Loss and its gradient with respect to the parameters (grad_host, FP32, the
+ * parameter layout; loss in *loss), forward and backward in `precision`.
+ * Either output may be null.  Synchronises. */
+ibem_status ibem_cnn_gradients(ibem_cnn* cnn, const float* in_dev, const float* target_dev, int B, int H,
+                               int W, int precision, float* grad_host, double* loss);
+
+/* One Adam step with learning rate lr on one batch; the loss before the step in
+ * *loss (synchronises if loss is not null). */
+ibem_status ibem_cnn_train_step(ibem_cnn* cnn, const float* in_dev, const float* target_dev, int B, int H,
+                                int W, float lr, int precision, double* loss);
+
+/* Minibatch training in BF16: `epochs` passes over n_images (input, target)
+ * images in a seeded random order, `batch` images per Adam step, with the
+ * augmentations of `augment`.  *last_epoch_loss = mean over the images of the
+ * last epoch of (1/2) |net(in) - target|^2.  Synchronises. */
+ibem_status ibem_cnn_train(ibem_cnn* cnn, const float* in_dev, const float* target_dev, int n_images, int H,
+                           int W, int batch, int epochs, float lr, unsigned long long seed, int augment,
+                           double* last_epoch_loss);
+
+/* Kernel launches of the network since the last call (then reset). */
+ibem_status ibem_cnn_launches(ibem_cnn* cnn, int64_t* launches);
+
+/* Attach (or with NULL detach) a network as the learned preconditioner of a
+ * Helmholtz handle.  The handle does not own it. */
+ibem_status ibem_set_learned_preconditioner(ibem_handle* h, ibem_cnn* cnn);
+
+/* z_dev = the learned preconditioner applied to v_dev (complex [ndof]; must
+ * not overlap).  Requires ibem_assemble and an attached network. */
+ibem_status ibem_learned_apply(ibem_handle* h, const double* v_dev, double* z_dev);
+
+/* Residual/error training pairs from the plain solver: for every right-hand
+ * side (b_dev, complex [nrhs][ndof]) block-Jacobi GMRES on the FP64 operator
+ * runs to rtol; after every `stride`-th step of its first cycle (at most
+ * max_pairs per right-hand side) the iterate x_k and its residual
+ * r_k = b - A x_k (from the Arnoldi relation) are kept, and with x* the final
+ * solution, e_k = x* - x_k, s_k = B^-1 r_k, sigma = |s_k| / sqrt(2 ndof) the
+ * pair is written as images: in = s_k / sigma, target = (e_k - s_k) / sigma.
+ * in_img_dev and tgt_img_dev hold nrhs * max_pairs * npatch images of
+ * n1 x n1; pair n occupies images n * npatch ... (n + 1) * npatch - 1.
+ * *n_pairs = pairs written.  Synchronises.  Returns IBEM_ERR_NOCONV (pairs
+ * kept) if a solve did not reach rtol. */
+ibem_status ibem_solver_pairs(ibem_handle* h, const double* b_dev, int nrhs, double rtol, int maxit,
+                              int stride, int max_pairs, float* in_img_dev, float* tgt_img_dev,
+                              int* n_pairs, ibem_solve_info* info);
 
 /* Text of the last error recorded on the handle ("" if none).  NULL handle:
  * the last error of ibem_create / ibem_block_tree in this thread. */

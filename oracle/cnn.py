@@ -69,13 +69,10 @@ def forward(params, x, C, keep=False):
     return (h, acts, pres) if keep else h
 
 
-def loss_and_grad(params, x, target, C):
-    """L = 1/(2B) sum (net(x) - target)^2 and dL/dparams (flat, same layout)."""
-    B = x.shape[0]
-    out, acts, pres = forward(params, x, C, keep=True)
-    d = out - target
-    loss = 0.5 * np.sum(d * d) / B
-    g = d / B                                    # dL/d out
+def backward(params, acts, pres, gout, C):
+    """dL/dparams (flat) given dL/d(network output) = gout and the layer inputs
+    and pre-activations of ``forward(..., keep=True)``."""
+    g = gout
     layers = unpack(params, C)
     grads = [None] * len(layers)
     for l in range(len(layers) - 1, -1, -1):
@@ -100,8 +97,16 @@ def loss_and_grad(params, x, target, C):
                     gin += np.einsum("oc,bohw->bchw", W[:, :, dy, dx],
                                      gp[:, :, 2 - dy:2 - dy + H, 2 - dx:2 - dx + Wd])
             g = gin
-    flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
-    return loss, flat
+    return np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
+
+
+def loss_and_grad(params, x, target, C):
+    """L = 1/(2B) sum (net(x) - target)^2 and dL/dparams (flat, same layout)."""
+    B = x.shape[0]
+    out, acts, pres = forward(params, x, C, keep=True)
+    d = out - target
+    loss = 0.5 * np.sum(d * d) / B
+    return loss, backward(params, acts, pres, d / B, C)
 
 
 class Adam:

@@ -16,6 +16,14 @@ A training pair is built from a residual r and the error e with A e = r:
 input s / sigma, target (e - s) / sigma, with s = B^-1 r.  The network thus
 learns what block-Jacobi misses, in units that do not depend on the level, the
 wavenumber or the size of r.
+
+Operator-aware objective: the error of the preconditioned pair measured in the
+residual norm, |A (z - e)| = |A z - r| with z = M(r), so that
+    L = 1 / (2 nb) * sum_j |A M(r_j) - r_j|^2
+over nb residuals of unit norm (e is not needed).  With z_j = s_j + sigma_j
+net(x_j) and the complex linear A, dL / d(real, imag of z_j) is
+A^H (A z_j - r_j) / nb, and dL / d(net output of x_j) is sigma_j times that,
+in the real / imaginary channels.
 """
 import numpy as np
 
@@ -78,3 +86,23 @@ def training_pair(r, e, bj, n1):
     s = bj(r)
     sigma = rms(s)
     return cnn.vector_to_images(s / sigma, n1), cnn.vector_to_images((e - s) / sigma, n1)
+
+
+def operator_loss_and_grad(params, rs, apply_A, apply_AH, bj, C, n1):
+    """L = 1/(2 nb) sum_j |A (s_j + sigma_j net(s_j / sigma_j)) - r_j|^2 and
+    dL/dparams for residuals rs [nb, N] (complex)."""
+    nb = rs.shape[0]
+    ss = [bj(r) for r in rs]
+    sig = [rms(s) for s in ss]
+    X = np.concatenate([cnn.vector_to_images(s / g, n1) for s, g in zip(ss, sig)])
+    out, acts, pres = cnn.forward(params, X, C, keep=True)
+    npatch = X.shape[0] // nb
+    loss = 0.0
+    gout = np.zeros_like(out)
+    for j in range(nb):
+        sl = slice(j * npatch, (j + 1) * npatch)
+        z = ss[j] + sig[j] * cnn.images_to_vector(out[sl])
+        res = apply_A(z) - rs[j]
+        loss += 0.5 * np.vdot(res, res).real / nb
+        gout[sl] = sig[j] * cnn.vector_to_images(apply_AH(res) / nb, n1)
+    return loss, cnn.backward(params, acts, pres, gout, C)

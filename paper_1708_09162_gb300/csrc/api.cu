@@ -484,8 +484,11 @@ ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int n
     if (s) return s;
     if (nrhs < 0 || (nrhs > 0 && (!b_dev || !w_dev)) || !(rtol > 0.0) || maxit < 1)
         return fail(h, IBEM_ERR_ARG, "bad solve arguments");
-    if (precond != IBEM_PRECOND_NONE && precond != IBEM_PRECOND_JACOBI && precond != IBEM_PRECOND_BLOCK_JACOBI)
+    if (precond != IBEM_PRECOND_NONE && precond != IBEM_PRECOND_JACOBI && precond != IBEM_PRECOND_BLOCK_JACOBI &&
+        precond != IBEM_PRECOND_LEARNED)
         return fail(h, IBEM_ERR_ARG, "unknown preconditioner");
+    if (precond == IBEM_PRECOND_LEARNED && (!h->helm || !h->cnn))
+        return fail(h, IBEM_ERR_STATE, "learned preconditioner: Helmholtz handle with an attached network required");
     if (precision != IBEM_FP64 && precision != IBEM_FP32) return fail(h, IBEM_ERR_ARG, "unknown precision");
     if (nrhs == 0) return IBEM_OK;
     if (!fp64_available(h)) return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
@@ -495,6 +498,43 @@ ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int n
     if (s == IBEM_ERR_NOCONV) h->err = "solver did not reach rtol within maxit";
     else if (s == IBEM_ERR_BREAKDOWN) h->err = "solver breakdown";
     else if (s != IBEM_OK) h->err = "solver failed (CUDA error)";
+    return s;
+}
+
+ibem_status ibem_set_learned_preconditioner(ibem_handle* h, ibem_cnn* cnn) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (cnn && !h->helm) return fail(h, IBEM_ERR_ARG, "the learned preconditioner is for Helmholtz handles");
+    h->cnn = cnn;
+    return IBEM_OK;
+}
+
+ibem_status ibem_learned_apply(ibem_handle* h, const double* v_dev, double* z_dev) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (!v_dev || !z_dev || v_dev == z_dev) return fail(h, IBEM_ERR_ARG, "bad learned_apply arguments");
+    if (!h->helm || !h->cnn) return fail(h, IBEM_ERR_STATE, "no learned preconditioner attached");
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cnn_precondition(h, h->cnn, v_dev, z_dev))) return cuda_fail(h, e, "learned preconditioner");
+    return IBEM_OK;
+}
+
+ibem_status ibem_solver_pairs(ibem_handle* h, const double* b_dev, int nrhs, double rtol, int maxit, int stride,
+                              int max_pairs, float* in_img_dev, float* tgt_img_dev, int* n_pairs,
+                              ibem_solve_info* info) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (!h->helm) return fail(h, IBEM_ERR_ARG, "solver pairs are generated for Helmholtz handles");
+    if (nrhs < 1 || !b_dev || !in_img_dev || !tgt_img_dev || !n_pairs || !(rtol > 0.0) || maxit < 1 || stride < 1 ||
+        max_pairs < 1)
+        return fail(h, IBEM_ERR_ARG, "bad solver_pairs arguments");
+    if (!fp64_available(h)) return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    *n_pairs = 0;
+    s = solver_pairs_impl(h, b_dev, nrhs, rtol, maxit, stride, max_pairs, in_img_dev, tgt_img_dev, n_pairs, info);
+    if (s == IBEM_ERR_NOCONV) h->err = "a solve of the pair generation did not reach rtol (pairs kept)";
+    else if (s != IBEM_OK) h->err = "pair generation failed";
     return s;
 }
 

@@ -1,0 +1,713 @@
+// Learned right preconditioner (no counterpart in the paper, which uses Jacobi
+// preconditioning, Sec. 4 item 3): a small convolutional network on the
+// B-spline coefficient grid of each patch, used as a correction of block-Jacobi
+// inside flexible GMRES.
+//
+// A complex vector of S_{p,m} is, patch by patch, an image with 2 channels
+// (real, imaginary part) of n1 x n1 pixels (pixel (jv, ju) = dof (patch, ju, jv)).
+// Network: four 3 x 3 convolutions (2 -> C -> C -> C -> 2 channels, zero
+// padding), ReLU after the first three; parameters flat, layer by layer,
+// W[cout][cin][3][3] then bias[cout], kept in FP32 with the Adam moments.
+// BF16 mode stores activations in BF16 and rounds the weights to BF16 where they
+// are used, with FP32 accumulation; FP32 mode keeps everything in FP32.
+//
+// Preconditioner: s = B^-1 v (block-Jacobi), sigma = |s| / sqrt(2N),
+// z = s + sigma * net(s / sigma), the network in BF16.
+//
+// Kernels: one tiled direct convolution (16 x 16 output pixels of one image and
+// 16 output channels per CTA, input halo tile and weights staged in shared
+// memory, FP32 FMA) serves the forward pass and, with flipped transposed
+// weights and the ReLU mask fused, the input gradient; the weight gradient is
+// a tiled reduction over pixels into per-CTA partial sums that a second kernel
+// adds in a fixed order, so training is deterministic.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <random>
+
+#include "ibem_internal.cuh"
+
+struct ibem_cnn {
+    int C = 32;                  // hidden channels
+    int L = 4;                   // layers
+    std::vector<int> cin, cout;  // per layer
+    std::vector<size_t> woff, boff;
+    size_t nparam = 0;
+    int device = 0;
+    float* d_param = nullptr;    // weights and biases, FP32
+    float* d_grad = nullptr;
+    float* d_m = nullptr;        // Adam moments
+    float* d_v = nullptr;
+    float* d_wt = nullptr;       // flipped transposed weights of one layer (backward)
+    int64_t step = 0;
+    void* d_act = nullptr;       // activations of the last forward pass: L + 1 slots
+    size_t act_slot = 0;         // elements per slot
+    size_t act_bytes = 0;
+    float* d_gbuf = nullptr;     // two gradient buffers, act_slot floats each
+    size_t gbuf_floats = 0;
+    float* d_part = nullptr;     // weight-gradient partial sums
+    size_t part_floats = 0;
+    float* d_img = nullptr;      // preconditioner / training batch images
+    size_t img_floats = 0;
+    void* d_items = nullptr;     // training minibatch items of one epoch
+    size_t items_bytes = 0;
+    double* d_red = nullptr;     // [0] loss, [1] |s|^2, [2] loss sum of an epoch
+    cudaStream_t stream = nullptr;
+    int64_t launches = 0;
+};
+
+namespace ibem {
+
+namespace {
+
+constexpr int TS = 16;        // output tile side
+constexpr int CIB = 8;        // input channels per shared-memory stage
+constexpr int WG_ITEMS = 256; // CTAs along the pixel axis of the weight gradient
+
+inline unsigned cblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+__device__ inline float ld_act(const float* p, int64_t i) { return p[i]; }
+__device__ inline float ld_act(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
+__device__ inline void st_act(float* p, int64_t i, float v) { p[i] = v; }
+__device__ inline void st_act(__nv_bfloat16* p, int64_t i, float v) { p[i] = __float2bfloat16(v); }
+__device__ inline float wq(float w, int bf) { return bf ? __bfloat162float(__float2bfloat16(w)) : w; }
+
+// out[b][co][y][x] = bias[co] + sum_ci sum_k w[co][ci][k] in[b][ci][y + dy - 1][x + dx - 1]
+// (k = 3 dy + dx), then ReLU if relu, then zeroed where mask[b][co][y][x] <= 0
+// if mask is given.  Grid: (tiles of the image, ceil(Cout / COB), B).
+template <typename TI, typename TO, typename TM, int COB>
+__global__ void __launch_bounds__(256) conv_tile_kernel(const TI* __restrict__ in, int Cin, int H, int W,
+                                                        const float* __restrict__ w,
+                                                        const float* __restrict__ bias, int Cout, int relu, int bf,
+                                                        const TM* __restrict__ mask, TO* __restrict__ out) {
+    __shared__ float s_in[CIB][TS + 2][TS + 2];
+    __shared__ __align__(16) float s_w[CIB][9][COB];
+    const int tiles_x = (W + TS - 1) / TS;
+    const int ty0 = (blockIdx.x / tiles_x) * TS, tx0 = (blockIdx.x % tiles_x) * TS;
+    const int co0 = blockIdx.y * COB;
+    const int64_t b = blockIdx.z;
+    const int t = threadIdx.x, py = t / TS, px = t % TS;
+    const int y = ty0 + py, x = tx0 + px;
+    const int64_t HW = (int64_t)H * W;
+    float acc[COB];
+#pragma unroll
+    for (int c = 0; c < COB; ++c) acc[c] = (bias && co0 + c < Cout) ? bias[co0 + c] : 0.0f;
+    for (int ci0 = 0; ci0 < Cin; ci0 += CIB) {
+        for (int i = t; i < CIB * (TS + 2) * (TS + 2); i += 256) {
+            const int c = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
+            const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+            float v = 0.0f;
+            if (ci0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = ld_act(in, (b * Cin + ci0 + c) * HW + (int64_t)yy * W + xx);
+            s_in[c][r / (TS + 2)][r % (TS + 2)] = v;
+        }
+        for (int i = t; i < CIB * 9 * COB; i += 256) {
+            const int co = i % COB, k = (i / COB) % 9, c = i / (9 * COB);
+            float v = 0.0f;
+            if (ci0 + c < Cin && co0 + co < Cout) v = wq(w[((int64_t)(co0 + co) * Cin + ci0 + c) * 9 + k], bf);
+            s_w[c][k][co] = v;
+        }
+        __syncthreads();
+        const int cmax = min(CIB, Cin - ci0);
+        for (int c = 0; c < cmax; ++c) {
+            float v[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = s_in[c][py + k / 3][px + k % 3];
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+#pragma unroll
+                for (int co = 0; co < COB; ++co) acc[co] = fmaf(s_w[c][k][co], v[k], acc[co]);
+        }
+        __syncthreads();
+    }
+    if (y >= H || x >= W) return;
+#pragma unroll
+    for (int co = 0; co < COB; ++co) {
+        if (co0 + co >= Cout) break;
+        float r = acc[co];
+        if (relu && r < 0.0f) r = 0.0f;
+        const int64_t o = (b * Cout + co0 + co) * HW + (int64_t)y * W + x;
+        if (mask && !(ld_act(mask, o) > 0.0f)) r = 0.0f;
+        st_act(out, o, r);
+    }
+}
+
+// wt[ci][co][k] = w[co][ci][8 - k] (rounded to BF16 in BF16 mode): the kernel of
+// the input gradient, which is a convolution of the output gradient with the
+// flipped, channel-transposed weights.
+__global__ void flip_weights_kernel(const float* __restrict__ w, int Cin, int Cout, int bf, float* __restrict__ wt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Cin * Cout * 9) return;
+    const int k = i % 9, co = (i / 9) % Cout, ci = i / (9 * Cout);
+    wt[i] = wq(w[((int64_t)co * Cin + ci) * 9 + (8 - k)], bf);
+}
+
+// Partial weight gradients: CTA (x, y) sums, over its range of (image, tile)
+// items, g[b][co][pix] * in[b][ci][pix + tap] for co < Cout (<= 32), the 8
+// input channels of chunk y and the 9 taps; thread = (ci within chunk, co).
+template <typename T>
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict__ g, const T* __restrict__ in, int B,
+                                                         int Cin, int H, int W, int Cout, int items_per_cta,
+                                                         float* __restrict__ part) {
+    __shared__ float s_g[32][TS * TS + 1];
+    __shared__ float s_in[CIB][TS + 2][TS + 2];
+    const int tiles_x = (W + TS - 1) / TS, tiles = tiles_x * ((H + TS - 1) / TS);
+    const int64_t HW = (int64_t)H * W;
+    const int t = threadIdx.x, co = t % 32, c = t / 32;
+    const int ci0 = blockIdx.y * CIB;
+    const int64_t it0 = (int64_t)blockIdx.x * items_per_cta;
+    const int64_t it1 = min((int64_t)B * tiles, it0 + items_per_cta);
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+    for (int64_t item = it0; item < it1; ++item) {
+        const int64_t b = item / tiles;
+        const int tile = (int)(item % tiles);
+        const int ty0 = (tile / tiles_x) * TS, tx0 = (tile % tiles_x) * TS;
+        for (int i = t; i < Cout * TS * TS; i += 256) {
+            const int o = i / (TS * TS), pix = i % (TS * TS);
+            const int yy = ty0 + pix / TS, xx = tx0 + pix % TS;
+            s_g[o][pix] = (yy < H && xx < W) ? g[(b * Cout + o) * HW + (int64_t)yy * W + xx] : 0.0f;
+        }
+        for (int i = t; i < CIB * (TS + 2) * (TS + 2); i += 256) {
+            const int cc = i / ((TS + 2) * (TS + 2)), r = i % ((TS + 2) * (TS + 2));
+            const int yy = ty0 - 1 + r / (TS + 2), xx = tx0 - 1 + r % (TS + 2);
+            float v = 0.0f;
+            if (ci0 + cc < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = ld_act(in, (b * Cin + ci0 + cc) * HW + (int64_t)yy * W + xx);
+            s_in[cc][r / (TS + 2)][r % (TS + 2)] = v;
+        }
+        __syncthreads();
+        if (co < Cout && ci0 + c < Cin) {
+            for (int py = 0; py < TS; ++py) {
+                // 3 x 3 window slid along the row: three new values per pixel
+                float w0[3], w1[3];
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    w0[dy] = s_in[c][py + dy][0];
+                    w1[dy] = s_in[c][py + dy][1];
+                }
+                for (int px = 0; px < TS; ++px) {
+                    float w2[3];
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) w2[dy] = s_in[c][py + dy][px + 2];
+                    const float gv = s_g[co][py * TS + px];
+#pragma unroll
+                    for (int dy = 0; dy < 3; ++dy) {
+                        acc[dy * 3 + 0] = fmaf(gv, w0[dy], acc[dy * 3 + 0]);
+                        acc[dy * 3 + 1] = fmaf(gv, w1[dy], acc[dy * 3 + 1]);
+                        acc[dy * 3 + 2] = fmaf(gv, w2[dy], acc[dy * 3 + 2]);
+                        w0[dy] = w1[dy];
+                        w1[dy] = w2[dy];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (co < Cout && ci0 + c < Cin) {
+        float* dst = part + (int64_t)blockIdx.x * Cout * Cin * 9 + ((int64_t)co * Cin + ci0 + c) * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dst[k] = acc[k];
+    }
+}
+
+// gw[i] = sum over rows r (in order) of part[r][i]
+__global__ void sum_rows_kernel(const float* __restrict__ part, int rows, int n, float* __restrict__ gw) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int r = 0; r < rows; ++r) s += part[(int64_t)r * n + i];
+    gw[i] = s;
+}
+
+// gb[co] = sum over b and pixels of g[b][co][.]; one CTA per channel
+__global__ void bias_grad_kernel(const float* __restrict__ g, int B, int Cout, int64_t HW, float* __restrict__ gb) {
+    __shared__ float red[256];
+    const int co = blockIdx.x;
+    float s = 0.0f;
+    for (int64_t i = threadIdx.x; i < (int64_t)B * HW; i += blockDim.x) s += g[((i / HW) * Cout + co) * HW + i % HW];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) gb[co] = red[0];
+}
+
+// g = (out - target) / B; loss[0] = 1/(2B) sum (out - target)^2; loss[2] += B * loss[0]
+template <typename T>
+__global__ void loss_kernel(int64_t n, int B, const T* __restrict__ out, const float* __restrict__ target,
+                            float* __restrict__ g, double* __restrict__ loss) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const float d = ld_act(out, i) - target[i];
+        g[i] = d / B;
+        acc += (double)d * d;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        loss[0] = red[0] / (2.0 * B);
+        loss[2] += red[0] / 2.0;
+    }
+}
+
+__global__ void adam_kernel(size_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, float lr, float b1, float b2, float c1, float c2, float eps) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+template <typename T>
+__global__ void f32_to_act_kernel(int64_t n, const float* __restrict__ in, T* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) st_act(out, i, in[i]);
+}
+
+template <typename T>
+__global__ void act_to_f32_kernel(int64_t n, const T* __restrict__ in, float* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ld_act(in, i);
+}
+
+// One training image of a minibatch: source index, symmetry of the square and
+// phase rotation (cos, sin) applied to input and target alike.
+struct TrainItem {
+    int src;
+    int dihedral;
+    float c, s;
+};
+
+// dihedral d: optionally transpose (bit 2), then mirror rows (bit 0) and
+// columns (bit 1); out[j][ch][y][x] = rotate(in[src][.][sy][sx])
+__global__ void gather_kernel(int nb, int H, int W, const TrainItem* __restrict__ items, const float* __restrict__ in,
+                              const float* __restrict__ tgt, float* __restrict__ bin, float* __restrict__ btgt) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t HW = (int64_t)H * W;
+    if (idx >= (int64_t)nb * HW) return;
+    const int j = (int)(idx / HW);
+    const int y = (int)((idx % HW) / W), x = (int)(idx % W);
+    const TrainItem it = items[j];
+    int a = y, bcol = x;
+    if (it.dihedral & 4) { a = x; bcol = y; }
+    if (it.dihedral & 1) a = H - 1 - a;
+    if (it.dihedral & 2) bcol = W - 1 - bcol;
+    const int64_t s0 = ((int64_t)it.src * 2) * HW + (int64_t)a * W + bcol;
+    const int64_t d0 = ((int64_t)j * 2) * HW + (int64_t)y * W + x;
+    float re = in[s0], im = in[s0 + HW];
+    bin[d0] = it.c * re - it.s * im;
+    bin[d0 + HW] = it.s * re + it.c * im;
+    re = tgt[s0];
+    im = tgt[s0 + HW];
+    btgt[d0] = it.c * re - it.s * im;
+    btgt[d0 + HW] = it.s * re + it.c * im;
+}
+
+// Preconditioner glue.  img[patch][2][n1][n1] = s / sigma with
+// sigma^2 = |s|^2 / (2N) (zero image if s = 0).
+__global__ void pack_images_kernel(int64_t N, int n1, const double* __restrict__ s, const double* __restrict__ ss,
+                                   float* __restrict__ img) {
+    int64_t dof = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (dof >= N) return;
+    const int64_t per = (int64_t)n1 * n1;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double inv = ss[0] > 0.0 ? 1.0 / sqrt(ss[0] / (2.0 * N)) : 0.0;
+    img[(patch * 2) * per + pix] = (float)(s[2 * dof] * inv);
+    img[(patch * 2 + 1) * per + pix] = (float)(s[2 * dof + 1] * inv);
+}
+
+// z += sigma * out
+template <typename T>
+__global__ void unpack_add_kernel(int64_t N, int n1, const T* __restrict__ img, const double* __restrict__ ss,
+                                  double* __restrict__ z) {
+    int64_t dof = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (dof >= N) return;
+    const int64_t per = (int64_t)n1 * n1;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double sig = sqrt(ss[0] / (2.0 * N));
+    z[2 * dof] += sig * (double)ld_act(img, (patch * 2) * per + pix);
+    z[2 * dof + 1] += sig * (double)ld_act(img, (patch * 2 + 1) * per + pix);
+}
+
+__global__ void sumsq_kernel(int64_t n, const double* __restrict__ v, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * v[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+namespace {
+
+cudaError_t grow(void** p, size_t* have, size_t need_bytes) {
+    if (need_bytes <= *have) return cudaSuccess;
+    cudaFree(*p);
+    *p = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc(p, need_bytes);
+    if (!e) *have = need_bytes;
+    return e;
+}
+
+cudaError_t ensure_buffers(ibem_cnn* c, int B, int H, int W) {
+    int mc = 2;
+    for (int l = 0; l < c->L; ++l) mc = std::max(mc, std::max(c->cin[l], c->cout[l]));
+    const size_t slot = (size_t)B * mc * H * W;
+    cudaError_t e;
+    size_t ab = c->act_bytes;
+    if ((e = grow(&c->d_act, &ab, slot * (c->L + 1) * sizeof(float)))) return e;
+    c->act_bytes = ab;
+    c->act_slot = slot;
+    size_t gb = c->gbuf_floats * sizeof(float);
+    if ((e = grow(reinterpret_cast<void**>(&c->d_gbuf), &gb, 2 * slot * sizeof(float)))) return e;
+    c->gbuf_floats = gb / sizeof(float);
+    return cudaSuccess;
+}
+
+template <typename TI, typename TO, typename TM>
+void launch_conv(ibem_cnn* c, const TI* in, int B, int Cin, int H, int W, const float* w, const float* bias, int Cout,
+                 int relu, int bf, const TM* mask, TO* out) {
+    const int tiles = ((H + TS - 1) / TS) * ((W + TS - 1) / TS);
+    if (Cout <= 4) {
+        dim3 grid(tiles, 1, B);
+        conv_tile_kernel<TI, TO, TM, 4><<<grid, 256, 0, c->stream>>>(in, Cin, H, W, w, bias, Cout, relu, bf, mask, out);
+    } else {
+        dim3 grid(tiles, (Cout + 15) / 16, B);
+        conv_tile_kernel<TI, TO, TM, 16><<<grid, 256, 0, c->stream>>>(in, Cin, H, W, w, bias, Cout, relu, bf, mask, out);
+    }
+    ++c->launches;
+}
+
+// forward: slot 0 = input (converted), slot l + 1 = output of layer l
+template <typename T>
+cudaError_t forward(ibem_cnn* c, const float* in, int B, int H, int W, int bf) {
+    cudaError_t e;
+    if ((e = ensure_buffers(c, B, H, W))) return e;
+    const size_t per = c->act_slot;
+    T* act = reinterpret_cast<T*>(c->d_act);
+    const int64_t n0 = (int64_t)B * 2 * H * W;
+    f32_to_act_kernel<T><<<cblk(n0, 256), 256, 0, c->stream>>>(n0, in, act);
+    ++c->launches;
+    for (int l = 0; l < c->L; ++l)
+        launch_conv<T, T, T>(c, act + l * per, B, c->cin[l], H, W, c->d_param + c->woff[l], c->d_param + c->boff[l],
+                             c->cout[l], l + 1 < c->L ? 1 : 0, bf, nullptr, act + (l + 1) * per);
+    return cudaGetLastError();
+}
+
+// backward from the loss against target (forward must have run on the same
+// batch); gradients into d_grad, loss into d_red[0]
+template <typename T>
+cudaError_t backward(ibem_cnn* c, const float* target, int B, int H, int W, int bf) {
+    const size_t per = c->act_slot;
+    T* act = reinterpret_cast<T*>(c->d_act);
+    float* g0 = c->d_gbuf;
+    float* g1 = c->d_gbuf + per;
+    const int64_t HW = (int64_t)H * W;
+    const int tiles = ((H + TS - 1) / TS) * ((W + TS - 1) / TS);
+    const int64_t items = (int64_t)B * tiles;
+    const int nx = (int)std::min<int64_t>(items, WG_ITEMS);
+    const int ipc = (int)((items + nx - 1) / nx);
+    cudaError_t e;
+    size_t maxw = 0;
+    for (int l = 0; l < c->L; ++l) maxw = std::max(maxw, (size_t)c->cout[l] * c->cin[l] * 9);
+    size_t pb = c->part_floats * sizeof(float);
+    if ((e = grow(reinterpret_cast<void**>(&c->d_part), &pb, (size_t)nx * maxw * sizeof(float)))) return e;
+    c->part_floats = pb / sizeof(float);
+    loss_kernel<T><<<1, 1024, 0, c->stream>>>((int64_t)B * 2 * HW, B, act + c->L * per, target, g0, c->d_red);
+    ++c->launches;
+    for (int l = c->L - 1; l >= 0; --l) {
+        const int Cin = c->cin[l], Cout = c->cout[l];
+        // g0 = dL / d(pre-activation of layer l)
+        dim3 wg(nx, (Cin + CIB - 1) / CIB);
+        conv_wgrad_kernel<T><<<wg, 256, 0, c->stream>>>(g0, act + l * per, B, Cin, H, W, Cout, ipc, c->d_part);
+        const int nw = Cout * Cin * 9;
+        sum_rows_kernel<<<cblk(nw, 256), 256, 0, c->stream>>>(c->d_part, nx, nw, c->d_grad + c->woff[l]);
+        bias_grad_kernel<<<Cout, 256, 0, c->stream>>>(g0, B, Cout, HW, c->d_grad + c->boff[l]);
+        c->launches += 3;
+        if (l > 0) {
+            flip_weights_kernel<<<cblk(nw, 256), 256, 0, c->stream>>>(c->d_param + c->woff[l], Cin, Cout, bf, c->d_wt);
+            // dL/d(pre-activation of layer l-1): through the flipped convolution, masked by ReLU'
+            launch_conv<float, float, T>(c, g0, B, Cout, H, W, c->d_wt, nullptr, Cin, 0, 0, act + l * per, g1);
+            c->launches += 1;
+            std::swap(g0, g1);
+        }
+    }
+    return cudaGetLastError();
+}
+
+void adam(ibem_cnn* c, float lr) {
+    c->step++;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - (float)std::pow(0.9, (double)c->step);
+    const float c2 = 1.0f - (float)std::pow(0.999, (double)c->step);
+    adam_kernel<<<cblk((int64_t)c->nparam, 256), 256, 0, c->stream>>>(c->nparam, c->d_param, c->d_grad, c->d_m, c->d_v,
+                                                                       lr, b1, b2, c1, c2, 1e-8f);
+    ++c->launches;
+}
+
+bool dims_ok(int B, int H, int W) {
+    return B >= 1 && H >= 1 && W >= 1 && B <= 65535 && (int64_t)H * W <= (1ll << 24);
+}
+
+}  // namespace
+
+// Learned preconditioner application z = s + sigma * net(s / sigma), s = B^-1 v
+// (complex v, z of length N).  Runs on the handle's stream; no host sync.
+cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, double* z) {
+    Plan& P = h->P;
+    cudaStream_t keep = c->stream;
+    c->stream = h->stream;
+    const int B = P.npatch, n1 = P.n1;
+    cudaError_t e = cudaSuccess;
+    size_t ib = c->img_floats * sizeof(float);
+    if ((e = grow(reinterpret_cast<void**>(&c->d_img), &ib, (size_t)B * 2 * n1 * n1 * sizeof(float)))) {
+        c->stream = keep;
+        return e;
+    }
+    c->img_floats = ib / sizeof(float);
+    apply_block_jacobi(h, v, z);
+    sumsq_kernel<<<1, 1024, 0, h->stream>>>(2 * P.N, z, c->d_red + 1);
+    pack_images_kernel<<<cblk(P.N, 256), 256, 0, h->stream>>>(P.N, n1, z, c->d_red + 1, c->d_img);
+    e = forward<__nv_bfloat16>(c, c->d_img, B, n1, n1, 1);
+    if (!e) {
+        unpack_add_kernel<__nv_bfloat16><<<cblk(P.N, 256), 256, 0, h->stream>>>(
+            P.N, n1, reinterpret_cast<const __nv_bfloat16*>(c->d_act) + c->L * c->act_slot, c->d_red + 1, z);
+        e = cudaGetLastError();
+    }
+    h->launches += 4 + 1 + c->L;
+    c->stream = keep;
+    return e;
+}
+
+}  // namespace ibem
+
+using namespace ibem;
+
+extern "C" {
+
+ibem_status ibem_cnn_create(int channels, unsigned long long seed, void* cuda_stream, ibem_cnn** out) {
+    if (!out || channels < 1 || channels > 32) return IBEM_ERR_ARG;
+    *out = nullptr;
+    ibem_cnn* c = new ibem_cnn();
+    c->C = channels;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaGetDevice(&c->device);
+    c->cin = {2, channels, channels, channels};
+    c->cout = {channels, channels, channels, 2};
+    size_t off = 0, maxw = 0;
+    for (int l = 0; l < c->L; ++l) {
+        c->woff.push_back(off);
+        off += (size_t)c->cout[l] * c->cin[l] * 9;
+        maxw = std::max(maxw, (size_t)c->cout[l] * c->cin[l] * 9);
+        c->boff.push_back(off);
+        off += c->cout[l];
+    }
+    c->nparam = off;
+    // He initialisation N(0, 2 / (9 cin)), the last layer scaled by 1/4 so that
+    // the untrained correction is small; zero biases
+    std::vector<float> p(off, 0.0f);
+    std::mt19937_64 rng(seed);
+    for (int l = 0; l < c->L; ++l) {
+        std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / (9.0 * c->cin[l])) * (l + 1 == c->L ? 0.25 : 1.0));
+        for (size_t i = 0; i < (size_t)c->cout[l] * c->cin[l] * 9; ++i) p[c->woff[l] + i] = (float)nd(rng);
+    }
+    if (cudaMalloc(&c->d_param, off * sizeof(float)) || cudaMalloc(&c->d_grad, off * sizeof(float)) ||
+        cudaMalloc(&c->d_m, off * sizeof(float)) || cudaMalloc(&c->d_v, off * sizeof(float)) ||
+        cudaMalloc(&c->d_wt, maxw * sizeof(float)) || cudaMalloc(&c->d_red, 8 * sizeof(double))) {
+        ibem_cnn_destroy(c);
+        return IBEM_ERR_OOM;
+    }
+    if (cudaMemcpyAsync(c->d_param, p.data(), off * sizeof(float), cudaMemcpyHostToDevice, c->stream) ||
+        cudaMemsetAsync(c->d_grad, 0, off * sizeof(float), c->stream) ||
+        cudaMemsetAsync(c->d_m, 0, off * sizeof(float), c->stream) ||
+        cudaMemsetAsync(c->d_v, 0, off * sizeof(float), c->stream) ||
+        cudaMemsetAsync(c->d_red, 0, 8 * sizeof(double), c->stream) || cudaStreamSynchronize(c->stream)) {
+        ibem_cnn_destroy(c);
+        return IBEM_ERR_CUDA;
+    }
+    *out = c;
+    return IBEM_OK;
+}
+
+ibem_status ibem_cnn_destroy(ibem_cnn* c) {
+    if (!c) return IBEM_OK;
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_param);
+    cudaFree(c->d_grad);
+    cudaFree(c->d_m);
+    cudaFree(c->d_v);
+    cudaFree(c->d_wt);
+    cudaFree(c->d_act);
+    cudaFree(c->d_gbuf);
+    cudaFree(c->d_part);
+    cudaFree(c->d_img);
+    cudaFree(c->d_items);
+    cudaFree(c->d_red);
+    delete c;
+    return IBEM_OK;
+}
+
+ibem_status ibem_cnn_params(ibem_cnn* c, float* get_host, const float* set_host, size_t* count) {
+    if (!c) return IBEM_ERR_ARG;
+    if (count) *count = c->nparam;
+    cudaError_t e = cudaSuccess;
+    if (set_host) {
+        e = cudaMemcpyAsync(c->d_param, set_host, c->nparam * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+        // new parameters start a new optimisation
+        if (!e) e = cudaMemsetAsync(c->d_m, 0, c->nparam * sizeof(float), c->stream);
+        if (!e) e = cudaMemsetAsync(c->d_v, 0, c->nparam * sizeof(float), c->stream);
+        c->step = 0;
+    }
+    if (!e && get_host)
+        e = cudaMemcpyAsync(get_host, c->d_param, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    return e ? IBEM_ERR_CUDA : IBEM_OK;
+}
+
+ibem_status ibem_cnn_forward(ibem_cnn* c, const float* in_dev, int B, int H, int W, float* out_dev, int precision) {
+    if (!c || !in_dev || !out_dev || !dims_ok(B, H, W)) return IBEM_ERR_ARG;
+    if (precision != IBEM_FP32 && precision != IBEM_BF16) return IBEM_ERR_ARG;
+    const int bf = precision == IBEM_BF16;
+    cudaError_t e = bf ? forward<__nv_bfloat16>(c, in_dev, B, H, W, 1) : forward<float>(c, in_dev, B, H, W, 0);
+    if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
+    const int64_t n = (int64_t)B * 2 * H * W;
+    if (bf)
+        act_to_f32_kernel<__nv_bfloat16><<<cblk(n, 256), 256, 0, c->stream>>>(
+            n, reinterpret_cast<const __nv_bfloat16*>(c->d_act) + c->L * c->act_slot, out_dev);
+    else
+        act_to_f32_kernel<float><<<cblk(n, 256), 256, 0, c->stream>>>(
+            n, reinterpret_cast<const float*>(c->d_act) + c->L * c->act_slot, out_dev);
+    ++c->launches;
+    return cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK;
+}
+
+ibem_status ibem_cnn_gradients(ibem_cnn* c, const float* in_dev, const float* target_dev, int B, int H, int W,
+                               int precision, float* grad_host, double* loss) {
+    if (!c || !in_dev || !target_dev || !dims_ok(B, H, W)) return IBEM_ERR_ARG;
+    if (precision != IBEM_FP32 && precision != IBEM_BF16) return IBEM_ERR_ARG;
+    const int bf = precision == IBEM_BF16;
+    cudaError_t e;
+    if (bf) {
+        e = forward<__nv_bfloat16>(c, in_dev, B, H, W, 1);
+        if (!e) e = backward<__nv_bfloat16>(c, target_dev, B, H, W, 1);
+    } else {
+        e = forward<float>(c, in_dev, B, H, W, 0);
+        if (!e) e = backward<float>(c, target_dev, B, H, W, 0);
+    }
+    if (!e && grad_host)
+        e = cudaMemcpyAsync(grad_host, c->d_grad, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (!e && loss) e = cudaMemcpyAsync(loss, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
+    return IBEM_OK;
+}
+
+ibem_status ibem_cnn_train_step(ibem_cnn* c, const float* in_dev, const float* target_dev, int B, int H, int W,
+                                float lr, int precision, double* loss) {
+    if (!c || !in_dev || !target_dev || !dims_ok(B, H, W) || !(lr > 0.0f)) return IBEM_ERR_ARG;
+    if (precision != IBEM_FP32 && precision != IBEM_BF16) return IBEM_ERR_ARG;
+    const int bf = precision == IBEM_BF16;
+    cudaError_t e;
+    if (bf) {
+        e = forward<__nv_bfloat16>(c, in_dev, B, H, W, 1);
+        if (!e) e = backward<__nv_bfloat16>(c, target_dev, B, H, W, 1);
+    } else {
+        e = forward<float>(c, in_dev, B, H, W, 0);
+        if (!e) e = backward<float>(c, target_dev, B, H, W, 0);
+    }
+    if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
+    adam(c, lr);
+    if (loss) {
+        if (cudaMemcpyAsync(loss, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream) ||
+            cudaStreamSynchronize(c->stream))
+            return IBEM_ERR_CUDA;
+    }
+    return cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK;
+}
+
+ibem_status ibem_cnn_train(ibem_cnn* c, const float* in_dev, const float* target_dev, int n_images, int H, int W,
+                           int batch, int epochs, float lr, unsigned long long seed, int augment,
+                           double* last_epoch_loss) {
+    if (!c || !in_dev || !target_dev || n_images < 1 || batch < 1 || epochs < 1 || !(lr > 0.0f) ||
+        !dims_ok(batch, H, W) || (augment & ~3))
+        return IBEM_ERR_ARG;
+    if ((augment & IBEM_AUGMENT_DIHEDRAL) && H != W) return IBEM_ERR_ARG;
+    const int nb_max = std::min(batch, n_images);
+    cudaError_t e;
+    size_t ib = c->img_floats * sizeof(float);
+    if ((e = grow(reinterpret_cast<void**>(&c->d_img), &ib, (size_t)2 * nb_max * 2 * H * W * sizeof(float))))
+        return IBEM_ERR_OOM;
+    c->img_floats = ib / sizeof(float);
+    if ((e = grow(&c->d_items, &c->items_bytes, (size_t)n_images * sizeof(TrainItem)))) return IBEM_ERR_OOM;
+    float* bin = c->d_img;
+    float* btgt = c->d_img + (size_t)nb_max * 2 * H * W;
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> phase(0.0, 2.0 * M_PI);
+    std::vector<TrainItem> items(n_images);
+    std::vector<int> perm(n_images);
+    TrainItem* d_items = reinterpret_cast<TrainItem*>(c->d_items);
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::iota(perm.begin(), perm.end(), 0);
+        std::shuffle(perm.begin(), perm.end(), rng);
+        for (int i = 0; i < n_images; ++i) {
+            const double th = (augment & IBEM_AUGMENT_PHASE) ? phase(rng) : 0.0;
+            items[i].src = perm[i];
+            items[i].dihedral = (augment & IBEM_AUGMENT_DIHEDRAL) ? (int)(rng() & 7) : 0;
+            items[i].c = (float)std::cos(th);
+            items[i].s = (float)std::sin(th);
+        }
+        // pageable copy: staged before return, ordered after the previous epoch
+        if (cudaMemcpyAsync(d_items, items.data(), n_images * sizeof(TrainItem), cudaMemcpyHostToDevice, c->stream) ||
+            cudaMemsetAsync(c->d_red + 2, 0, sizeof(double), c->stream))
+            return IBEM_ERR_CUDA;
+        for (int i0 = 0; i0 < n_images; i0 += nb_max) {
+            const int nb = std::min(nb_max, n_images - i0);
+            gather_kernel<<<cblk((int64_t)nb * H * W, 256), 256, 0, c->stream>>>(nb, H, W, d_items + i0, in_dev,
+                                                                                 target_dev, bin, btgt);
+            ++c->launches;
+            e = forward<__nv_bfloat16>(c, bin, nb, H, W, 1);
+            if (!e) e = backward<__nv_bfloat16>(c, btgt, nb, H, W, 1);
+            if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
+            adam(c, lr);
+        }
+    }
+    double s = 0.0;
+    if (cudaMemcpyAsync(&s, c->d_red + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream) ||
+        cudaStreamSynchronize(c->stream))
+        return IBEM_ERR_CUDA;
+    // d_red[2] sums (1/2) |out - target|^2 over the images of the last epoch
+    if (last_epoch_loss) *last_epoch_loss = s / n_images;
+    return cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK;
+}
+
+ibem_status ibem_cnn_launches(ibem_cnn* c, int64_t* launches) {
+    if (!c || !launches) return IBEM_ERR_ARG;
+    *launches = c->launches;
+    c->launches = 0;
+    return IBEM_OK;
+}
+
+}  // extern "C"

@@ -230,6 +230,8 @@ void singular_rule(int cls, int n, std::vector<double>& soa);
 // ---------------------------------------------------------------------------
 // The handle
 // ---------------------------------------------------------------------------
+struct ibem_cnn;
+
 struct ibem_handle {
     ibem::Plan P;
     cudaStream_t stream = nullptr;
@@ -321,6 +323,9 @@ struct ibem_handle {
     double* d_bj_inv = nullptr;
     int64_t bj_blocks = 0;
 
+    // learned preconditioner (not owned; IBEM_PRECOND_LEARNED)
+    ibem_cnn* cnn = nullptr;
+
     // device-side waits: bound (polls) and status word (IBEM_DEVICE_* bits)
     long long wait_limit = 1LL << 26;
     int* d_status = nullptr;
@@ -392,4 +397,10 @@ cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
 bool mr_supported(const ibem_handle* h, int nrhs);
 cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs);
 void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
+
+// Learned preconditioner (cnn.cu): z = s + sigma net(s / sigma), s = B^-1 v.
+cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, double* z);
+// Residual/error training pairs from block-Jacobi GMRES solves (solve.cu).
+ibem_status solver_pairs_impl(ibem_handle* h, const double* b, int nrhs, double rtol, int maxit, int stride,
+                              int max_pairs, float* in_img, float* tgt_img, int* n_pairs, ibem_solve_info* info);
 }  // namespace ibem

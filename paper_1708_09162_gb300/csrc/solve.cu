@@ -308,20 +308,35 @@ ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& 
 // Givens rotations on the host.  The Arnoldi operator has precision `prec`;
 // every restart recomputes the residual b - A x with the FP64 operator, so with
 // prec = IBEM_FP32 the restarts are FP64 residual corrections.
+// Iterates of the first GMRES cycle kept for residual/error training pairs:
+// after step j with (j + 1) % stride == 0 the iterate x_j goes to X[n] and its
+// residual r_j = b - A x_j to R[n], the latter from the Arnoldi relation
+// r_j = V_{j+1} (beta e_1 - Hbar_j y_j) without an operator application.
+struct Recorder {
+    int stride = 1, max = 0, n = 0;
+    double* X = nullptr;  // [max][2N]
+    double* R = nullptr;  // [max][2N]
+};
+
 ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, int maxit, int precond, int prec,
-                  int restart, int* its, int* restarts) {
+                  int restart, int* its, int* restarts, Recorder* rec = nullptr) {
     Plan& P = h->P;
     const int64_t N = P.N;
     cudaStream_t st = h->stream;
     const double* d = precond == IBEM_PRECOND_JACOBI ? h->d_diag : nullptr;
     const bool block = precond == IBEM_PRECOND_BLOCK_JACOBI;
+    // flexible GMRES (Saad 1993) for the learned preconditioner, which is not a
+    // fixed linear map: the preconditioned vectors Z are kept and x += Z y
+    const bool flex = precond == IBEM_PRECOND_LEARNED;
     const int m = restart;
-    double *V = nullptr, *w = nullptr, *z = nullptr, *hv = nullptr;
+    double *V = nullptr, *w = nullptr, *z = nullptr, *hv = nullptr, *Z = nullptr;
+    if (flex && cudaMallocAsync(&Z, (size_t)m * 2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
     if (cudaMallocAsync(&V, (size_t)(m + 1) * 2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
     if (cudaMallocAsync(&w, (size_t)2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
     if (cudaMallocAsync(&z, (size_t)2 * N * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
     if (cudaMallocAsync(&hv, (size_t)2 * (m + 1) * sizeof(double), st) != cudaSuccess) return IBEM_ERR_OOM;
     std::vector<double> H((size_t)(m + 1) * m * 2, 0.0), cs(m), snr(m), sni(m), g(2 * (m + 1)), hh(2 * (m + 1));
+    std::vector<double> Hu(rec ? (size_t)(m + 1) * m * 2 : 0, 0.0);   // unrotated Hessenberg (recording)
     ibem_status status = IBEM_ERR_NOCONV;
     *its = 0;
     *restarts = 0;
@@ -330,6 +345,7 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         cudaFreeAsync(w, st);
         cudaFreeAsync(z, st);
         cudaFreeAsync(hv, st);
+        if (Z) cudaFreeAsync(Z, st);
         cudaStreamSynchronize(st);
         return s;
     };
@@ -338,6 +354,31 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
     auto Hr = [&](int i, int j) -> double& { return H[2 * ((size_t)i * m + j)]; };
     auto Hi = [&](int i, int j) -> double& { return H[2 * ((size_t)i * m + j) + 1]; };
     const unsigned nb = nblk(N, 256);
+    // back substitution R y = g (complex, upper triangular k x k)
+    auto backsolve = [&](int k, std::vector<double>& y) {
+        y.assign(2 * k, 0.0);
+        for (int i = k - 1; i >= 0; --i) {
+            double sr = g[2 * i], si = g[2 * i + 1];
+            for (int l = i + 1; l < k; ++l) {
+                sr -= Hr(i, l) * y[2 * l] - Hi(i, l) * y[2 * l + 1];
+                si -= Hr(i, l) * y[2 * l + 1] + Hi(i, l) * y[2 * l];
+            }
+            double dr = Hr(i, i), di = Hi(i, i), den = dr * dr + di * di;
+            y[2 * i] = (sr * dr + si * di) / den;
+            y[2 * i + 1] = (si * dr - sr * di) / den;
+        }
+    };
+    // M^-1 (V y) into out (tmp is scratch), for the fixed preconditioners
+    auto precond_combine = [&](int k, double* tmp, double* out) {
+        if (flex) {
+            zcombine_kernel<<<nb, 256, 0, st>>>(Z, N, hv, k, nullptr, out);
+        } else if (block) {
+            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, nullptr, tmp);
+            apply_block_jacobi(h, tmp, out);
+        } else {
+            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, d, out);
+        }
+    };
     while (*its < maxit) {
         double beta;
         if (norm2(h, w, 2 * N, &beta) != cudaSuccess) return done(IBEM_ERR_CUDA);
@@ -348,9 +389,15 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
         g[0] = beta;
         int k = 0;
         for (int j = 0; j < m && *its < maxit; ++j) {
-            if (block) apply_block_jacobi(h, V + (size_t)j * 2 * N, z);
-            else zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, z);
-            if (apply_operator(h, z, w, 1, prec) != cudaSuccess) return done(IBEM_ERR_CUDA);
+            double* zj = flex ? Z + (size_t)j * 2 * N : z;
+            if (flex) {
+                if (cnn_precondition(h, h->cnn, V + (size_t)j * 2 * N, zj) != cudaSuccess) return done(IBEM_ERR_CUDA);
+            } else if (block) {
+                apply_block_jacobi(h, V + (size_t)j * 2 * N, zj);
+            } else {
+                zdiv_kernel<<<nb, 256, 0, st>>>(N, V + (size_t)j * 2 * N, d, zj);
+            }
+            if (apply_operator(h, zj, w, 1, prec) != cudaSuccess) return done(IBEM_ERR_CUDA);
             for (int i = 0; i <= j; ++i) { Hr(i, j) = 0.0; Hi(i, j) = 0.0; }
             for (int pass = 0; pass < 2; ++pass) {
                 zdots_kernel<<<j + 1, 256, 0, st>>>(V, N, w, j + 1, hv);
@@ -364,6 +411,13 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
             if (norm2(h, w, 2 * N, &hn) != cudaSuccess) return done(IBEM_ERR_CUDA);
             Hr(j + 1, j) = hn;
             Hi(j + 1, j) = 0.0;
+            if (rec)
+                for (int i = 0; i <= j + 1; ++i) {
+                    Hu[2 * ((size_t)i * m + j)] = Hr(i, j);
+                    Hu[2 * ((size_t)i * m + j) + 1] = Hi(i, j);
+                }
+            if (hn != 0.0)
+                dscal_copy_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, 1.0 / hn, w, V + (size_t)(j + 1) * 2 * N);
             // apply the previous rotations to column j
             for (int i = 0; i < j; ++i) {
                 double ar = Hr(i, j), ai = Hi(i, j), br = Hr(i + 1, j), bi = Hi(i + 1, j);
@@ -398,30 +452,35 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
             ++*its;
             double res = std::sqrt(g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1]);
             if (!std::isfinite(res)) return done(IBEM_ERR_BREAKDOWN);
-            if (res <= tol_abs || hn == 0.0) break;
-            dscal_copy_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, 1.0 / hn, w, V + (size_t)(j + 1) * 2 * N);
-        }
-        // back substitution R y = g (complex, upper triangular k x k)
-        std::vector<double> y(2 * k, 0.0);
-        for (int i = k - 1; i >= 0; --i) {
-            double sr = g[2 * i], si = g[2 * i + 1];
-            for (int l = i + 1; l < k; ++l) {
-                sr -= Hr(i, l) * y[2 * l] - Hi(i, l) * y[2 * l + 1];
-                si -= Hr(i, l) * y[2 * l + 1] + Hi(i, l) * y[2 * l];
+            if (rec && *restarts == 0 && rec->n < rec->max && k % rec->stride == 0) {
+                // x_k = M^-1 V_k y_k (x0 = 0 in the first cycle)
+                std::vector<double> y, c(2 * (k + 1), 0.0);
+                backsolve(k, y);
+                if (cudaMemcpyAsync(hv, y.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
+                    return done(IBEM_ERR_CUDA);
+                precond_combine(k, w, rec->X + (size_t)rec->n * 2 * N);
+                // r_k = V_{k+1} (beta e_1 - Hbar_k y_k)
+                c[0] = beta;
+                for (int i = 0; i <= k; ++i)
+                    for (int l = 0; l < k; ++l) {
+                        if (i > l + 1) continue;
+                        const double hr = Hu[2 * ((size_t)i * m + l)], hi = Hu[2 * ((size_t)i * m + l) + 1];
+                        c[2 * i] -= hr * y[2 * l] - hi * y[2 * l + 1];
+                        c[2 * i + 1] -= hr * y[2 * l + 1] + hi * y[2 * l];
+                    }
+                if (cudaMemcpyAsync(hv, c.data(), 2 * (k + 1) * sizeof(double), cudaMemcpyHostToDevice, st))
+                    return done(IBEM_ERR_CUDA);
+                zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, hn != 0.0 ? k + 1 : k, nullptr,
+                                                    rec->R + (size_t)rec->n * 2 * N);
+                ++rec->n;
             }
-            double dr = Hr(i, i), di = Hi(i, i), den = dr * dr + di * di;
-            y[2 * i] = (sr * dr + si * di) / den;
-            y[2 * i + 1] = (si * dr - sr * di) / den;
+            if (res <= tol_abs || hn == 0.0) break;
         }
-        for (int i = 0; i < 2 * k; ++i) hh[i] = y[i];
-        if (cudaMemcpyAsync(hv, hh.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
+        std::vector<double> y;
+        backsolve(k, y);
+        if (cudaMemcpyAsync(hv, y.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
             return done(IBEM_ERR_CUDA);
-        if (block) {
-            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, nullptr, w);
-            apply_block_jacobi(h, w, z);
-        } else {
-            zcombine_kernel<<<nb, 256, 0, st>>>(V, N, hv, k, d, z);
-        }
+        precond_combine(k, w, z);
         add_kernel<<<nblk(2 * N, 256), 256, 0, st>>>(2 * N, z, x);
         // restart residual with the FP64 operator
         if (apply_operator(h, x, w, 1, IBEM_FP64) != cudaSuccess) return done(IBEM_ERR_CUDA);
@@ -435,7 +494,91 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
     return done(status);
 }
 
+// Training images of one pair: in = s / sigma, target = (x* - x - s) / sigma,
+// sigma^2 = |s|^2 / (2N) (ss[0] = |s|^2), patch images [npatch][2][n1][n1].
+__global__ void pair_images_kernel(int64_t N, int n1, const double* __restrict__ xstar, const double* __restrict__ x,
+                                   const double* __restrict__ s, const double* __restrict__ ss,
+                                   float* __restrict__ in_img, float* __restrict__ tgt_img) {
+    int64_t dof = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (dof >= N) return;
+    const int64_t per = (int64_t)n1 * n1;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double inv = ss[0] > 0.0 ? 1.0 / sqrt(ss[0] / (2.0 * N)) : 0.0;
+    for (int c = 0; c < 2; ++c) {
+        const double sv = s[2 * dof + c], ev = xstar[2 * dof + c] - x[2 * dof + c];
+        in_img[(patch * 2 + c) * per + pix] = (float)(sv * inv);
+        tgt_img[(patch * 2 + c) * per + pix] = (float)((ev - sv) * inv);
+    }
+}
+
 }  // namespace
+
+ibem_status solver_pairs_impl(ibem_handle* h, const double* b, int nrhs, double rtol, int maxit, int stride,
+                              int max_pairs, float* in_img, float* tgt_img, int* n_pairs, ibem_solve_info* info) {
+    Plan& P = h->P;
+    const int64_t N = P.N;
+    cudaStream_t st = h->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t vec = (size_t)2 * N;
+    double *X = nullptr, *R = nullptr, *xs = nullptr, *s = nullptr;
+    auto release = [&](ibem_status r) {
+        if (X) cudaFreeAsync(X, st);
+        if (R) cudaFreeAsync(R, st);
+        if (xs) cudaFreeAsync(xs, st);
+        if (s) cudaFreeAsync(s, st);
+        cudaStreamSynchronize(st);
+        return r;
+    };
+    if (cudaMallocAsync(&X, (size_t)max_pairs * vec * sizeof(double), st) ||
+        cudaMallocAsync(&R, (size_t)max_pairs * vec * sizeof(double), st) ||
+        cudaMallocAsync(&xs, vec * sizeof(double), st) || cudaMallocAsync(&s, vec * sizeof(double), st))
+        return release(IBEM_ERR_OOM);
+    const size_t img = (size_t)P.npatch * 2 * P.n1 * P.n1;
+    int total = 0, total_it = 0, total_outer = 0;
+    double worst = 0.0;
+    ibem_status worst_s = IBEM_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        const double* bb = b + (size_t)r * vec;
+        double nb;
+        if (norm2(h, bb, vec, &nb) != cudaSuccess) return release(IBEM_ERR_CUDA);
+        if (nb == 0.0) continue;
+        Recorder rec;
+        rec.stride = stride;
+        rec.max = max_pairs;
+        rec.X = X;
+        rec.R = R;
+        int its = 0, outer = 0;
+        ibem_status sres = gmres(h, bb, xs, rtol * nb, maxit, IBEM_PRECOND_BLOCK_JACOBI, IBEM_FP64,
+                                 std::max(100, std::min(maxit, 400)), &its, &outer, &rec);
+        if (sres != IBEM_OK && sres != IBEM_ERR_NOCONV) return release(sres);
+        if (sres != IBEM_OK && worst_s == IBEM_OK) worst_s = sres;
+        // true residual of x*
+        if (apply_operator(h, xs, s, 1, IBEM_FP64) != cudaSuccess) return release(IBEM_ERR_CUDA);
+        sub_kernel<<<nblk(vec, 256), 256, 0, st>>>(vec, bb, s, s);
+        double rt;
+        if (norm2(h, s, vec, &rt) != cudaSuccess) return release(IBEM_ERR_CUDA);
+        worst = std::max(worst, rt / nb);
+        total_it += its;
+        total_outer += outer;
+        for (int n = 0; n < rec.n; ++n) {
+            apply_block_jacobi(h, R + (size_t)n * vec, s);
+            dot_kernel<<<1, 1024, 0, st>>>(s, s, vec, h->d_red);
+            pair_images_kernel<<<nblk(N, 256), 256, 0, st>>>(N, P.n1, xs, X + (size_t)n * vec, s, h->d_red,
+                                                             in_img + (size_t)(total + n) * img,
+                                                             tgt_img + (size_t)(total + n) * img);
+        }
+        total += rec.n;
+    }
+    if (cudaGetLastError() != cudaSuccess) return release(IBEM_ERR_CUDA);
+    *n_pairs = total;
+    if (info) {
+        info->iterations = total_it;
+        info->outer = total_outer;
+        info->rel_residual = worst;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return release(worst_s);
+}
 
 ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, double rtol, int maxit,
                        int precond, int precision, ibem_solve_info* info) {

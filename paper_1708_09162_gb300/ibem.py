@@ -22,14 +22,18 @@ IBEM_OK = 0
 IBEM_ERR_NOCONV = 5
 IBEM_PATCH_NURBS, IBEM_PATCH_SPHERE_FACE = 0, 1
 IBEM_LAPLACE, IBEM_HELMHOLTZ = 0, 1
-IBEM_FP64, IBEM_FP32 = 0, 1
-IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI, IBEM_PRECOND_BLOCK_JACOBI = 0, 1, 2
+IBEM_FP64, IBEM_FP32, IBEM_BF16 = 0, 1, 2
+IBEM_PRECOND_NONE, IBEM_PRECOND_JACOBI, IBEM_PRECOND_BLOCK_JACOBI, IBEM_PRECOND_LEARNED = 0, 1, 2, 3
+IBEM_AUGMENT_PHASE, IBEM_AUGMENT_DIHEDRAL = 1, 2
 
 EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ibem_quad_points",
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
             "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
             "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc",
-            "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy")
+            "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy",
+            "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
+            "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
+            "ibem_learned_apply", "ibem_solver_pairs")
 
 
 class IbemError(RuntimeError):
@@ -99,6 +103,19 @@ def _load():
         "ibem_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "ibem_batch_destroy": (I32, [P]),
         "ibem_device_status": (I32, [P, ctypes.POINTER(I32)]),
+        "ibem_cnn_create": (I32, [I32, ctypes.c_ulonglong, P, ctypes.POINTER(P)]),
+        "ibem_cnn_destroy": (I32, [P]),
+        "ibem_cnn_params": (I32, [P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "ibem_cnn_forward": (I32, [P, P, I32, I32, I32, P, I32]),
+        "ibem_cnn_gradients": (I32, [P, P, P, I32, I32, I32, I32, P, ctypes.POINTER(ctypes.c_double)]),
+        "ibem_cnn_train_step": (I32, [P, P, P, I32, I32, I32, ctypes.c_float, I32, ctypes.POINTER(ctypes.c_double)]),
+        "ibem_cnn_train": (I32, [P, P, P, I32, I32, I32, I32, I32, ctypes.c_float, ctypes.c_ulonglong, I32,
+                                 ctypes.POINTER(ctypes.c_double)]),
+        "ibem_cnn_launches": (I32, [P, ctypes.POINTER(I64)]),
+        "ibem_set_learned_preconditioner": (I32, [P, P]),
+        "ibem_learned_apply": (I32, [P, P, P]),
+        "ibem_solver_pairs": (I32, [P, P, I32, ctypes.c_double, I32, I32, I32, P, P, ctypes.POINTER(I32),
+                                    ctypes.POINTER(ibem_solve_info)]),
         "ibem_last_error": (ctypes.c_char_p, [P]),
         "ibem_status_string": (ctypes.c_char_p, [I32]),
     }
@@ -123,6 +140,13 @@ def _dptr(t):
         return None
     if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float64":
         raise ValueError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _fptr(t):
+    """Device pointer of a contiguous float32 CUDA tensor (network images)."""
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != "torch.float32":
+        raise ValueError("expected a contiguous float32 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -308,3 +332,89 @@ def ibem_last_error(h=None):
 
 def ibem_status_string(s):
     return _lib.ibem_status_string(s).decode()
+
+
+# ---- learned preconditioner --------------------------------------------------------
+def ibem_cnn_create(channels=32, seed=0, stream=None):
+    c = ctypes.c_void_p()
+    sp = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(_lib.ibem_cnn_create(channels, seed, sp, ctypes.byref(c)))
+    return c
+
+
+def ibem_cnn_destroy(c):
+    _check(_lib.ibem_cnn_destroy(c))
+
+
+def ibem_cnn_params(c, set_params=None):
+    """Current parameters (float32 numpy array) after loading set_params if given."""
+    n = ctypes.c_size_t()
+    _check(_lib.ibem_cnn_params(c, None, None, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.float32)
+    src = None
+    if set_params is not None:
+        src = np.ascontiguousarray(set_params, dtype=np.float32)
+        if src.shape != (n.value,):
+            raise ValueError("expected %d parameters" % n.value)
+    _check(_lib.ibem_cnn_params(c, out.ctypes.data_as(ctypes.c_void_p),
+                                src.ctypes.data_as(ctypes.c_void_p) if src is not None else None, None))
+    return out
+
+
+def ibem_cnn_forward(c, x, out, precision=IBEM_BF16):
+    B, _, H, W = x.shape
+    _check(_lib.ibem_cnn_forward(c, _fptr(x), B, H, W, _fptr(out), precision))
+
+
+def ibem_cnn_gradients(c, x, target, precision=IBEM_FP32):
+    """(loss, gradient as float32 numpy array)."""
+    B, _, H, W = x.shape
+    n = ctypes.c_size_t()
+    _check(_lib.ibem_cnn_params(c, None, None, ctypes.byref(n)))
+    g = np.zeros(n.value, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.ibem_cnn_gradients(c, _fptr(x), _fptr(target), B, H, W, precision,
+                                   g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)))
+    return loss.value, g
+
+
+def ibem_cnn_train_step(c, x, target, lr, precision=IBEM_BF16):
+    B, _, H, W = x.shape
+    loss = ctypes.c_double()
+    _check(_lib.ibem_cnn_train_step(c, _fptr(x), _fptr(target), B, H, W, lr, precision, ctypes.byref(loss)))
+    return loss.value
+
+
+def ibem_cnn_train(c, x, target, batch, epochs, lr, seed=0, augment=IBEM_AUGMENT_PHASE | IBEM_AUGMENT_DIHEDRAL):
+    n, _, H, W = x.shape
+    loss = ctypes.c_double()
+    _check(_lib.ibem_cnn_train(c, _fptr(x), _fptr(target), n, H, W, batch, epochs, lr, seed, augment,
+                               ctypes.byref(loss)))
+    return loss.value
+
+
+def ibem_cnn_launches(c):
+    n = ctypes.c_int64()
+    _check(_lib.ibem_cnn_launches(c, ctypes.byref(n)))
+    return n.value
+
+
+def ibem_set_learned_preconditioner(h, c):
+    _check(_lib.ibem_set_learned_preconditioner(h, c), h)
+
+
+def ibem_learned_apply(h, v, z):
+    _check(_lib.ibem_learned_apply(h, _dptr(v), _dptr(z)), h)
+
+
+def ibem_solver_pairs(h, b, nrhs, in_img, tgt_img, rtol=1e-10, maxit=400, stride=1, max_pairs=32, check=True):
+    """Writes pairs into the float32 image tensors; returns (n_pairs, info) or
+    (status, n_pairs, info) with check=False."""
+    n = ctypes.c_int()
+    info = ibem_solve_info()
+    s = _lib.ibem_solver_pairs(h, _dptr(b), nrhs, rtol, maxit, stride, max_pairs, _fptr(in_img), _fptr(tgt_img),
+                               ctypes.byref(n), ctypes.byref(info))
+    if check:
+        _check(s, h)
+        return n.value, info
+    return s, n.value, info

@@ -1,0 +1,252 @@
+"""GPU parity of the learned preconditioner: network forward and gradients
+against the FP64 oracle network, the Adam step, deterministic training, the
+preconditioner application (block-Jacobi part to 1e-12) and the solver pairs
+against the oracle operator, and flexible GMRES."""
+import numpy as np
+import pytest
+
+from gpu_common import lib
+
+pytestmark = pytest.mark.gpu
+
+
+def _params64(ibem, c):
+    return ibem.ibem_cnn_params(c).astype(np.float64)
+
+
+def _dev32(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("C", [8, 32])
+def test_forward_fp32_and_bf16_against_oracle(C):
+    import torch
+    from oracle import cnn
+    ibem = lib()
+    c = ibem.ibem_cnn_create(C, seed=3)
+    p = _params64(ibem, c)
+    rng = np.random.default_rng(1)
+    p[cnn.n_params(C) - 2:] = [0.1, -0.2]     # nonzero last biases
+    ibem.ibem_cnn_params(c, p)
+    # ragged tiles: 37 = 2 * 16 + 5, 21 = 16 + 5
+    x = rng.normal(size=(3, 2, 37, 21)).astype(np.float32)
+    ref = cnn.forward(p.astype(np.float32).astype(np.float64), x.astype(np.float64), C)
+    out = torch.empty((3, 2, 37, 21), dtype=torch.float32, device="cuda")
+    ibem.ibem_cnn_forward(c, _dev32(x), out, ibem.IBEM_FP32)
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy(), ref) < 1e-5
+    ibem.ibem_cnn_forward(c, _dev32(x), out, ibem.IBEM_BF16)
+    torch.cuda.synchronize()
+    assert _rel(out.cpu().numpy(), ref) < 2e-2
+    ibem.ibem_cnn_destroy(c)
+
+
+@pytest.mark.parametrize("C", [8, 32])
+def test_gradients_against_oracle(C):
+    from oracle import cnn
+    ibem = lib()
+    c = ibem.ibem_cnn_create(C, seed=5)
+    p = _params64(ibem, c)
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=(2, 2, 19, 18)).astype(np.float32)
+    t = rng.normal(size=(2, 2, 19, 18)).astype(np.float32)
+    loss0, g0 = cnn.loss_and_grad(p, x.astype(np.float64), t.astype(np.float64), C)
+    loss, g = ibem.ibem_cnn_gradients(c, _dev32(x), _dev32(t), ibem.IBEM_FP32)
+    assert loss == pytest.approx(loss0, rel=1e-6)
+    lossb, gb = ibem.ibem_cnn_gradients(c, _dev32(x), _dev32(t), ibem.IBEM_BF16)
+    assert lossb == pytest.approx(loss0, rel=2e-2)
+    off = 0
+    for ci, co in cnn.layer_channels(C):
+        for n in (co * ci * 9, co):           # weights, then biases of the layer
+            sl = slice(off, off + n)
+            assert _rel(g[sl], g0[sl]) < 1e-4
+            # BF16: activations rounded (relative 2^-9) after each of four layers,
+            # weights rounded, ReLU masks flipped near zero; the error of the
+            # gradient compounds over the forward and backward chain
+            assert _rel(gb[sl], g0[sl]) < 1e-1
+            off += n
+    ibem.ibem_cnn_destroy(c)
+
+
+def test_adam_step_against_oracle():
+    from oracle import cnn
+    ibem = lib()
+    C = 8
+    c = ibem.ibem_cnn_create(C, seed=7)
+    p = _params64(ibem, c)
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(2, 2, 17, 17)).astype(np.float32)
+    t = rng.normal(size=(2, 2, 17, 17)).astype(np.float32)
+    lr = 1e-3
+    loss = ibem.ibem_cnn_train_step(c, _dev32(x), _dev32(t), lr, ibem.IBEM_FP32)
+    loss0, g0 = cnn.loss_and_grad(p, x.astype(np.float64), t.astype(np.float64), C)
+    assert loss == pytest.approx(loss0, rel=1e-6)
+    p1 = cnn.Adam(len(p), lr).step(p, g0)
+    q = _params64(ibem, c)
+    big = np.abs(g0) > 1e-3 * np.max(np.abs(g0))
+    assert np.max(np.abs((q - p) - (p1 - p))[big]) < 1e-3 * lr
+    assert np.max(np.abs(q - p)) <= lr * (1 + 1e-5)
+    ibem.ibem_cnn_destroy(c)
+
+
+def test_training_is_deterministic_and_learns():
+    import torch
+    ibem = lib()
+    rng = np.random.default_rng(4)
+    # a learnable map: target = 0.5 * (shifted input) rotated by i
+    x = rng.normal(size=(48, 2, 20, 20)).astype(np.float32)
+    t = np.zeros_like(x)
+    t[:, 0, :, 1:] = -0.5 * x[:, 1, :, :-1]
+    t[:, 1, :, 1:] = 0.5 * x[:, 0, :, :-1]
+    xd, td = _dev32(x), _dev32(t)
+    res = []
+    for _ in range(2):
+        c = ibem.ibem_cnn_create(16, seed=11)
+        l0 = ibem.ibem_cnn_gradients(c, xd, td, ibem.IBEM_BF16)[0]
+        l1 = ibem.ibem_cnn_train(c, xd, td, batch=16, epochs=30, lr=3e-3, seed=5, augment=ibem.IBEM_AUGMENT_PHASE)
+        res.append((l0, l1, ibem.ibem_cnn_params(c)))
+        ibem.ibem_cnn_destroy(c)
+    torch.cuda.synchronize()
+    assert np.array_equal(res[0][2], res[1][2])
+    assert res[0][1] == res[1][1]
+    assert res[0][1] < 0.2 * res[0][0]
+
+
+@pytest.fixture(scope="module")
+def helm_m2():
+    """Oracle FMM operator, near matrix and block-Jacobi at p = 2, m = 2."""
+    from oracle import fmm, galerkin, geometry, learned
+    disc = galerkin.Discretisation(geometry.unit_sphere(), 2, 2, galerkin.HelmholtzKernel(3.0))
+    op = fmm.FMMOperator(disc, 6, 1.6)
+    An = learned.near_matrix(op)
+    bj = learned.BlockJacobi(An, learned.block_jacobi_groups(op.mesh))
+    return op, An, bj
+
+
+def _helm_handle(ibem, p, m, q, k):
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=1, kappa=k))
+    ibem.ibem_assemble(h)
+    return h
+
+
+def _cplx_dev(v):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1))).cuda()
+
+
+def _cplx_host(t):
+    a = t.cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def test_learned_apply_against_oracle(helm_m2):
+    import torch
+    from oracle import cnn, learned
+    op, _, bj = helm_m2
+    ibem = lib()
+    h = _helm_handle(ibem, 2, 2, 6, 3.0)
+    C = 32
+    c = ibem.ibem_cnn_create(C, seed=2)
+    ibem.ibem_set_learned_preconditioner(h, c)
+    n1 = op.mesh.n1
+    rng = np.random.default_rng(8)
+    v = rng.normal(size=op.mesh.n_dofs) + 1j * rng.normal(size=op.mesh.n_dofs)
+    vd = _cplx_dev(v)
+    zd = torch.empty_like(vd)
+    # zero last layer: exactly block-Jacobi
+    p = _params64(ibem, c)
+    p0 = p.copy()
+    p0[-(2 * C * 9 + 2):] = 0.0
+    ibem.ibem_cnn_params(c, p0)
+    ibem.ibem_learned_apply(h, vd, zd)
+    torch.cuda.synchronize()
+    s = bj(v)
+    assert np.max(np.abs(_cplx_host(zd) - s)) < 1e-12 * np.max(np.abs(s))
+    # trained-like parameters: correction within BF16 accuracy
+    p[-2:] = [0.05, -0.03]
+    ibem.ibem_cnn_params(c, p)
+    ibem.ibem_learned_apply(h, vd, zd)
+    torch.cuda.synchronize()
+    z0 = learned.learned_apply(v, bj, p.astype(np.float32).astype(np.float64), C, n1)
+    z = _cplx_host(zd)
+    assert _rel(z - s, z0 - s) < 2e-2
+    assert _rel(z, z0) < 2e-2 * np.linalg.norm(z0 - s) / np.linalg.norm(z0) + 1e-12
+    ibem.ibem_set_learned_preconditioner(h, None)
+    ibem.ibem_cnn_destroy(c)
+    ibem.ibem_destroy(h)
+
+
+def test_solver_pairs_against_oracle(helm_m2):
+    """Pairs of the GPU solver against pairs formed from the oracle's flexible
+    GMRES iterates with the oracle block-Jacobi (GMRES iterates are unique)."""
+    import torch
+    from oracle import learned, solve
+    op, _, bj = helm_m2
+    ibem = lib()
+    h = _helm_handle(ibem, 2, 2, 6, 3.0)
+    N, n1, npatch = op.mesh.n_dofs, op.mesh.n1, 6
+    rng = np.random.default_rng(9)
+    maxp, stride = 8, 2
+    checked = 0
+    for r in range(2):
+        b = rng.normal(size=N) + 1j * rng.normal(size=N)
+        img = torch.zeros((maxp * npatch, 2, n1, n1), dtype=torch.float32, device="cuda")
+        tgt = torch.zeros_like(img)
+        n, info = ibem.ibem_solver_pairs(h, _cplx_dev(b[None]), 1, img, tgt, rtol=1e-12, maxit=400, stride=stride,
+                                         max_pairs=maxp)
+        assert n >= 2 and info.rel_residual <= 1e-12
+        rec = []
+        xs, _ = solve.fgmres(op.matvec, b, bj, rtol=1e-13, restart=400, maxit=400, record=rec)
+        inp = img.cpu().numpy().astype(np.float64)
+        out = tgt.cpu().numpy().astype(np.float64)
+        for k in range(n):
+            xk = rec[(k + 1) * stride - 1]
+            rk = b - op.matvec(xk)
+            if np.linalg.norm(rk) < 1e-8 * np.linalg.norm(b):
+                continue
+            i0, t0 = learned.training_pair(rk, xs - xk, bj, n1)
+            sl = slice(k * npatch, (k + 1) * npatch)
+            assert _rel(inp[sl], i0) < 1e-5
+            assert _rel(out[sl], t0) < 1e-4 * max(1.0, np.linalg.norm(i0) / np.linalg.norm(t0))
+            checked += 1
+    assert checked >= 4
+    ibem.ibem_destroy(h)
+
+
+def test_fgmres_learned_solves_and_untrained_correction_is_harmless():
+    import torch
+    ibem = lib()
+    h = _helm_handle(ibem, 2, 3, 6, 6.0)
+    info = ibem.ibem_get_info(h)
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    gv = -np.exp(1j * 6.0 * (qp.cpu().numpy() @ np.array([0.0, 0.6, 0.8])))
+    b = torch.empty((info.ndof, 2), dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, _cplx_dev(gv), 1, b)
+    w = torch.empty_like(b)
+    wl = torch.empty_like(b)
+    sb = ibem.ibem_solve(h, b, w, 1, rtol=1e-10, maxit=2000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI)
+    c = ibem.ibem_cnn_create(32, seed=1)
+    p = ibem.ibem_cnn_params(c)
+    p[-(2 * 32 * 9 + 2):] = 0.0                 # correction switched off: FGMRES = GMRES with block-Jacobi
+    ibem.ibem_cnn_params(c, p)
+    ibem.ibem_set_learned_preconditioner(h, c)
+    s0 = ibem.ibem_solve(h, b, wl, 1, rtol=1e-10, maxit=2000, precond=ibem.IBEM_PRECOND_LEARNED)
+    assert abs(s0.iterations - sb.iterations) <= 1
+    assert s0.rel_residual <= 1e-10
+    assert _rel(_cplx_host(wl), _cplx_host(w)) < 1e-8
+    c1 = ibem.ibem_cnn_create(32, seed=1)
+    ibem.ibem_cnn_params(c, ibem.ibem_cnn_params(c1))
+    ibem.ibem_cnn_destroy(c1)
+    s1 = ibem.ibem_solve(h, b, wl, 1, rtol=1e-10, maxit=2000, precond=ibem.IBEM_PRECOND_LEARNED)
+    assert s1.rel_residual <= 1e-10
+    ibem.ibem_set_learned_preconditioner(h, None)
+    with pytest.raises(ibem.IbemError):
+        ibem.ibem_solve(h, b, wl, 1, precond=ibem.IBEM_PRECOND_LEARNED)
+    ibem.ibem_cnn_destroy(c)
+    ibem.ibem_destroy(h)

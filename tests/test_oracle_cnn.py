@@ -177,3 +177,27 @@ def test_learned_apply_and_pairs_identities():
     assert np.allclose(sig * cnn.images_to_vector(inp + tgt), e, atol=1e-12)
     assert np.allclose(sig * cnn.images_to_vector(inp), s, atol=1e-12)
     assert np.sqrt(np.mean(inp ** 2)) == pytest.approx(1.0)
+
+
+def test_operator_loss_gradient_matches_central_differences():
+    """dL/dparams of the residual-norm objective against central differences,
+    with a random complex A (A^H its conjugate transpose) and a block-Jacobi of
+    its diagonal blocks."""
+    rng = np.random.default_rng(13)
+    n1, npatch, C = 4, 2, 3
+    N = npatch * n1 * n1
+    A = np.eye(N) * 2 + 0.3 * (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N)))
+    bj = learned.BlockJacobi(A, [np.arange(0, N // 2), np.arange(N // 2, N)])
+    rs = rng.normal(size=(3, N)) + 1j * rng.normal(size=(3, N))
+    rs /= np.linalg.norm(rs, axis=1)[:, None]
+    params = rng.normal(0.0, 0.3, cnn.n_params(C))
+    f = lambda p: learned.operator_loss_and_grad(p, rs, lambda z: A @ z, lambda z: A.conj().T @ z, bj, C, n1)
+    loss, g = f(params)
+    # the loss is the residual of the preconditioned vectors
+    z0 = [learned.learned_apply(r, bj, params, C, n1) for r in rs]
+    assert loss == pytest.approx(sum(np.linalg.norm(A @ z - r) ** 2 for z, r in zip(z0, rs)) / 6.0, rel=1e-12)
+    eps = 1e-6
+    for _ in range(3):
+        d = rng.normal(size=params.shape)
+        fd = (f(params + eps * d)[0] - f(params - eps * d)[0]) / (2 * eps)
+        assert fd == pytest.approx(g @ d, rel=1e-6)
