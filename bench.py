@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--config3-only", action="store_true", help="run only the many-right-hand-side section")
     ap.add_argument("--config3-m", type=int, default=6, help="refinement level of that section (profiling)")
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
+    ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
+    ap.add_argument("--learn-train-m", type=int, default=5, help="level of the training solves")
+    ap.add_argument("--learn-m", type=int, default=6, help="level of the compared solves")
+    ap.add_argument("--learn-nrhs", type=int, default=2, help="plane waves of the compared solves")
     ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -260,6 +265,101 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
                                "for it"}}
 
 
+def learned_preconditioner(ibem, stream, args):
+    """Learned right preconditioner, Helmholtz sound-soft scattering on the
+    6-patch sphere, p = 2, q = 6, k drawn uniformly from [8, 16] (seeded):
+    the network (32 channels) is trained on unit-norm residuals of plain
+    block-Jacobi GMRES solves at level args.learn_train_m (three wavenumbers,
+    two plane waves each) with the residual-norm objective, then flexible GMRES
+    with it is compared with block-Jacobi GMRES at level args.learn_m on
+    args.learn_nrhs plane waves, both on the FP64 operator to relative residual
+    1e-8.  Also the network's forward pass on 16 right-hand sides' worth of
+    130 x 130 images (level 7)."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(SEED + 5)
+    p, q = 2, 6
+
+    def make(m, k):
+        h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=1.6,
+                                                                     kernel=ibem.IBEM_HELMHOLTZ, kappa=k), stream)
+        ibem.ibem_assemble(h)
+        return h
+
+    def plane_rhs(h, k, n):
+        info = ibem.ibem_get_info(h)
+        d = rng.normal(size=(n, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+        ibem.ibem_quad_points(h, qp)
+        torch.cuda.synchronize()
+        g = -np.exp(1j * k * (qp.cpu().numpy() @ d.T)).T
+        gq = torch.from_numpy(np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))).cuda()
+        b = torch.empty((n, info.ndof, 2), dtype=torch.float64, device="cuda")
+        ibem.ibem_rhs(h, gq, n, b)
+        return b
+
+    c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
+    t0 = time.perf_counter()
+    train = []
+    for k in rng.uniform(8.0, 16.0, size=3):
+        h = make(args.learn_train_m, k)
+        info = ibem.ibem_get_info(h)
+        b = plane_rhs(h, k, 2)
+        r = torch.zeros((2 * 60, info.ndof, 2), dtype=torch.float64, device="cuda")
+        n, _ = ibem.ibem_solver_residuals(h, b, 2, r, rtol=1e-10, maxit=400, stride=1, max_vecs=60)
+        l0 = ibem.ibem_cnn_operator_gradients(h, c, r[:min(n, 64)].contiguous(), min(n, 64), ibem.IBEM_BF16,
+                                              ibem.IBEM_FP32)[0]
+        l1 = ibem.ibem_cnn_train_operator(h, c, r, n, batch=16, epochs=8, lr=1e-3, seed=len(train))
+        train.append({"k": float(k), "vectors": n, "objective_before": l0, "objective_after": l1})
+        ibem.ibem_destroy(h)
+    train_s = time.perf_counter() - t0
+    k = float(rng.uniform(8.0, 16.0))
+    h = make(args.learn_m, k)
+    info = ibem.ibem_get_info(h)
+    b = plane_rhs(h, k, args.learn_nrhs)
+    w = torch.empty_like(b)
+    res = {}
+    for name, pc in (("block_jacobi", ibem.IBEM_PRECOND_BLOCK_JACOBI), ("learned", ibem.IBEM_PRECOND_LEARNED)):
+        ibem.ibem_set_learned_preconditioner(h, c if pc == ibem.IBEM_PRECOND_LEARNED else None)
+        s, si = ibem.ibem_solve(h, b, w, args.learn_nrhs, rtol=1e-8, maxit=3000, precond=pc, check=False)
+        res[name] = {"status": ibem.ibem_status_string(s), "iterations": si.iterations,
+                     "rel_residual_fp64": si.rel_residual, "seconds": si.seconds}
+    ibem.ibem_set_learned_preconditioner(h, None)
+    ibem.ibem_destroy(h)
+    # forward pass of the network on 96 images of 130 x 130 (level 7, 16 right-hand sides)
+    B, H = 96, 130
+    x = torch.randn((B, 2, H, H), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    ev0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / reps
+    C = 32
+    flops = 2.0 * 9 * (2 * C + C * C + C * C + C * 2) * B * H * H
+    _, mhz, src = _peaks()
+    fp32_peak = 152 * 128 * 2 * mhz * 1e6
+    ibem.ibem_cnn_destroy(c)
+    it_b, it_l = res["block_jacobi"]["iterations"], res["learned"]["iterations"]
+    return {"workload": "helmholtz-sphere-p2-q6-k[8,16]: train level %d, solve level %d, %d plane waves"
+                        % (args.learn_train_m, args.learn_m, args.learn_nrhs),
+            "k_solve": k, "ndof": info.ndof, "train": train, "train_s": train_s, "solve": res,
+            "iterations_learned_over_block_jacobi": it_l / max(1, it_b),
+            "seconds_learned_over_block_jacobi": res["learned"]["seconds"] / max(1e-9, res["block_jacobi"]["seconds"]),
+            "cnn_forward": {"images": B, "size": H, "ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12,
+                            "bound": "alu", "peak_tflops": fp32_peak / 1e12,
+                            "frac": flops / (fwd_ms * 1e-3) / fp32_peak,
+                            "peak_note": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (%s clock)" % (mhz, src)}}
+
+
 # ---------------------------------------------------------------- our arm
 def ours(args, rank, world, local_rank):
     import numpy as np
@@ -283,6 +383,11 @@ def ours(args, rank, world, local_rank):
         out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
         if rank == 0:
             print(json.dumps({"helmholtz_64rhs": out}), flush=True)
+        return
+    if args.learned_only:
+        out = learned_preconditioner(ibem, stream, args)
+        if rank == 0:
+            print(json.dumps({"learned_preconditioner": out}), flush=True)
         return
     prm = ibem.make_params(WORKLOAD["p"], WORKLOAD["m"], q_cheb=WORKLOAD["q_cheb"], eta=WORKLOAD["eta"])
     t0 = time.perf_counter()
@@ -432,6 +537,9 @@ def ours(args, rank, world, local_rank):
     # ---- Helmholtz, 64 plane waves: tensor-core coupling ----
     config3 = None if args.no_config3 else helmholtz_many_rhs(ibem, stream, world, barrier, args)
 
+    # ---- learned preconditioner vs block-Jacobi ----
+    learned = None if args.no_learned else learned_preconditioner(ibem, stream, args)
+
     # ---- oracle on the host cores (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -456,6 +564,7 @@ def ours(args, rank, world, local_rank):
             "roofline": roof,
             "cpu_baseline": cpu,
             "helmholtz_64rhs": config3,
+            "learned_preconditioner": learned,
             "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
                     "d2h_bytes_per_step": N * R * 8},
             "gpu_launches": prof["launches"],

@@ -370,6 +370,36 @@ ibem_status ibem_solver_pairs(ibem_handle* h, const double* b_dev, int nrhs, dou
                               int stride, int max_pairs, float* in_img_dev, float* tgt_img_dev,
                               int* n_pairs, ibem_solve_info* info);
 
+/* Unit-norm residuals of the plain solver: for every right-hand side
+ * block-Jacobi GMRES on the FP64 operator runs to rtol, and after every
+ * `stride`-th step of its first cycle (at most max_vecs per right-hand side)
+ * r_k / |r_k| (r_k = b - A x_k from the Arnoldi relation) is written to
+ * r_out_dev (complex [nrhs * max_vecs][ndof]); *n_out = vectors written.
+ * Synchronises.  IBEM_ERR_NOCONV (vectors kept) if a solve missed rtol. */
+ibem_status ibem_solver_residuals(ibem_handle* h, const double* b_dev, int nrhs, double rtol, int maxit,
+                                  int stride, int max_vecs, double* r_out_dev, int* n_out,
+                                  ibem_solve_info* info);
+
+/* Residual-norm objective of the learned preconditioner on unit-norm residuals
+ * r_j (complex [n][ndof], n <= 256) of a Helmholtz handle:
+ *   L = 1/(2n) sum_j |A z_j - r_j|^2,  z_j = s_j + sigma_j net(s_j / sigma_j),
+ * s_j = B^-1 r_j.  Since A e_j = r_j this is the error z_j - e_j of the
+ * residual/error pair measured in the norm |A .|.  The gradient passes through
+ * A^H = conj(A conj(.)) (the Galerkin matrix is complex symmetric).
+ * precision (network): IBEM_FP32 or IBEM_BF16; op_precision (operator):
+ * IBEM_FP64 or IBEM_FP32.  grad_host / loss may be null.  Synchronises. */
+ibem_status ibem_cnn_operator_gradients(ibem_handle* h, ibem_cnn* cnn, const double* r_dev, int n,
+                                        int precision, int op_precision, float* grad_host, double* loss);
+
+/* Adam training on that objective: `epochs` passes over the n residuals in a
+ * seeded random order, minibatches of `batch` (<= 256) vectors, optional random
+ * phase (IBEM_AUGMENT_PHASE), network in BF16, operator in op_precision.
+ * *last_epoch_loss = mean over the vectors of the last epoch of
+ * (1/2) |A z - r|^2.  Synchronises. */
+ibem_status ibem_cnn_train_operator(ibem_handle* h, ibem_cnn* cnn, const double* r_dev, int n, int batch,
+                                    int epochs, float lr, unsigned long long seed, int augment,
+                                    int op_precision, double* last_epoch_loss);
+
 /* Text of the last error recorded on the handle ("" if none).  NULL handle:
  * the last error of ibem_create / ibem_block_tree in this thread. */
 const char* ibem_last_error(const ibem_handle* h);

@@ -538,6 +538,23 @@ ibem_status ibem_solver_pairs(ibem_handle* h, const double* b_dev, int nrhs, dou
     return s;
 }
 
+ibem_status ibem_solver_residuals(ibem_handle* h, const double* b_dev, int nrhs, double rtol, int maxit, int stride,
+                                  int max_vecs, double* r_out_dev, int* n_out, ibem_solve_info* info) {
+    ibem_status s = check_ready(h);
+    if (s) return s;
+    if (!h->helm) return fail(h, IBEM_ERR_ARG, "solver residuals are generated for Helmholtz handles");
+    if (nrhs < 1 || !b_dev || !r_out_dev || !n_out || !(rtol > 0.0) || maxit < 1 || stride < 1 || max_vecs < 1)
+        return fail(h, IBEM_ERR_ARG, "bad solver_residuals arguments");
+    if (!fp64_available(h)) return fail(h, IBEM_ERR_STATE, "no FP64 coupling stored (IBEM_COUPLING_NONE)");
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    *n_out = 0;
+    s = solver_residuals_impl(h, b_dev, nrhs, rtol, maxit, stride, max_vecs, r_out_dev, n_out, info);
+    if (s == IBEM_ERR_NOCONV) h->err = "a solve of the residual generation did not reach rtol (vectors kept)";
+    else if (s != IBEM_OK) h->err = "residual generation failed";
+    return s;
+}
+
 ibem_status ibem_profile_enable(ibem_handle* h, int enable) {
     if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
     ibem_profile_data scratch;

@@ -54,6 +54,10 @@ struct ibem_cnn {
     size_t img_floats = 0;
     void* d_items = nullptr;     // training minibatch items of one epoch
     size_t items_bytes = 0;
+    void* d_opvec = nullptr;     // residual-norm objective: vectors
+    size_t opvec_bytes = 0;
+    void* d_opimg = nullptr;     // residual-norm objective: images
+    size_t opimg_bytes = 0;
     double* d_red = nullptr;     // [0] loss, [1] |s|^2, [2] loss sum of an epoch
     cudaStream_t stream = nullptr;
     int64_t launches = 0;
@@ -420,11 +424,13 @@ cudaError_t forward(ibem_cnn* c, const float* in, int B, int H, int W, int bf) {
 // backward from the loss against target (forward must have run on the same
 // batch); gradients into d_grad, loss into d_red[0]
 template <typename T>
-cudaError_t backward(ibem_cnn* c, const float* target, int B, int H, int W, int bf) {
+cudaError_t backward(ibem_cnn* c, const float* target, int B, int H, int W, int bf, const float* gout = nullptr) {
     const size_t per = c->act_slot;
     T* act = reinterpret_cast<T*>(c->d_act);
-    float* g0 = c->d_gbuf;
+    // g0 is only read below (the ReLU mask is fused into the next gradient)
+    float* g0 = gout ? const_cast<float*>(gout) : c->d_gbuf;
     float* g1 = c->d_gbuf + per;
+    float* g2 = c->d_gbuf;
     const int64_t HW = (int64_t)H * W;
     const int tiles = ((H + TS - 1) / TS) * ((W + TS - 1) / TS);
     const int64_t items = (int64_t)B * tiles;
@@ -436,8 +442,10 @@ cudaError_t backward(ibem_cnn* c, const float* target, int B, int H, int W, int 
     size_t pb = c->part_floats * sizeof(float);
     if ((e = grow(reinterpret_cast<void**>(&c->d_part), &pb, (size_t)nx * maxw * sizeof(float)))) return e;
     c->part_floats = pb / sizeof(float);
-    loss_kernel<T><<<1, 1024, 0, c->stream>>>((int64_t)B * 2 * HW, B, act + c->L * per, target, g0, c->d_red);
-    ++c->launches;
+    if (!gout) {
+        loss_kernel<T><<<1, 1024, 0, c->stream>>>((int64_t)B * 2 * HW, B, act + c->L * per, target, g0, c->d_red);
+        ++c->launches;
+    }
     for (int l = c->L - 1; l >= 0; --l) {
         const int Cin = c->cin[l], Cout = c->cout[l];
         // g0 = dL / d(pre-activation of layer l)
@@ -452,7 +460,10 @@ cudaError_t backward(ibem_cnn* c, const float* target, int B, int H, int W, int 
             // dL/d(pre-activation of layer l-1): through the flipped convolution, masked by ReLU'
             launch_conv<float, float, T>(c, g0, B, Cout, H, W, c->d_wt, nullptr, Cin, 0, 0, act + l * per, g1);
             c->launches += 1;
-            std::swap(g0, g1);
+            // next input gradient goes to the buffer that is not g1 (the caller's gout is never written)
+            float* nxt = (g1 == c->d_gbuf + per) ? g2 : c->d_gbuf + per;
+            g0 = g1;
+            g1 = nxt;
         }
     }
     return cudaGetLastError();
@@ -470,6 +481,183 @@ void adam(ibem_cnn* c, float lr) {
 
 bool dims_ok(int B, int H, int W) {
     return B >= 1 && H >= 1 && W >= 1 && B <= 65535 && (int64_t)H * W <= (1ll << 24);
+}
+
+}  // namespace
+
+// ---- residual-norm objective: L = 1/(2 nb) sum_j |A (s_j + sigma_j net(s_j / sigma_j)) - r_j|^2 ----
+
+// dst[j] = e^{i theta_j} src[items[j].src] (complex vectors of N dofs)
+__global__ void rot_gather_vec_kernel(int nb, int64_t N, const TrainItem* __restrict__ items,
+                                      const double* __restrict__ src, double* __restrict__ dst) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nb * N) return;
+    const int j = (int)(idx / N);
+    const int64_t i = idx % N;
+    const TrainItem it = items[j];
+    const double re = src[((int64_t)it.src * N + i) * 2], im = src[((int64_t)it.src * N + i) * 2 + 1];
+    dst[idx * 2] = (double)it.c * re - (double)it.s * im;
+    dst[idx * 2 + 1] = (double)it.s * re + (double)it.c * im;
+}
+
+// out[j] = |v_j|^2, one CTA per vector of n doubles
+__global__ void vec_sumsq_kernel(int64_t n, const double* __restrict__ v, double* __restrict__ out) {
+    __shared__ double red[256];
+    const double* vj = v + (int64_t)blockIdx.x * n;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += vj[i] * vj[i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// y_j -= r_j in place and out[j] = |y_j|^2; one CTA per vector of n doubles
+__global__ void residual_sumsq_kernel(int64_t n, const double* __restrict__ r, double* __restrict__ y,
+                                      double* __restrict__ out) {
+    __shared__ double red[256];
+    const int64_t o = (int64_t)blockIdx.x * n;
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = y[o + i] - r[o + i];
+        y[o + i] = d;
+        acc += d * d;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// red[0] = sum_j part[j] / (2 nb); red[2] += sum_j part[j] / 2
+__global__ void op_loss_kernel(int nb, const double* __restrict__ part, double* __restrict__ red) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int j = 0; j < nb; ++j) s += part[j];
+    red[0] = s / (2.0 * nb);
+    red[2] += s / 2.0;
+}
+
+__global__ void conj_kernel(int64_t n_complex, double* __restrict__ v) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_complex) v[2 * i + 1] = -v[2 * i + 1];
+}
+
+// img[(j npatch + patch) 2 + c][pix] = s_j / sigma_j, sigma_j^2 = ss[j] / (2N)
+__global__ void batch_pack_kernel(int nb, int64_t N, int n1, const double* __restrict__ s,
+                                  const double* __restrict__ ss, float* __restrict__ img) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nb * N) return;
+    const int j = (int)(idx / N);
+    const int64_t dof = idx % N, per = (int64_t)n1 * n1, npatch = N / per;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double inv = ss[j] > 0.0 ? 1.0 / sqrt(ss[j] / (2.0 * N)) : 0.0;
+    const int64_t o = ((int64_t)j * npatch + patch) * 2 * per + pix;
+    img[o] = (float)(s[idx * 2] * inv);
+    img[o + per] = (float)(s[idx * 2 + 1] * inv);
+}
+
+// z_j = s_j + sigma_j out_j
+template <typename T>
+__global__ void batch_unpack_kernel(int nb, int64_t N, int n1, const T* __restrict__ out, const double* __restrict__ ss,
+                                    const double* __restrict__ s, double* __restrict__ z) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nb * N) return;
+    const int j = (int)(idx / N);
+    const int64_t dof = idx % N, per = (int64_t)n1 * n1, npatch = N / per;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double sig = sqrt(ss[j] / (2.0 * N));
+    const int64_t o = ((int64_t)j * npatch + patch) * 2 * per + pix;
+    z[idx * 2] = s[idx * 2] + sig * (double)ld_act(out, o);
+    z[idx * 2 + 1] = s[idx * 2 + 1] + sig * (double)ld_act(out, o + per);
+}
+
+// gimg = (sigma_j / nb) (Re, Im) g_j
+__global__ void batch_grad_images_kernel(int nb, int64_t N, int n1, const double* __restrict__ g,
+                                         const double* __restrict__ ss, float* __restrict__ gimg) {
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nb * N) return;
+    const int j = (int)(idx / N);
+    const int64_t dof = idx % N, per = (int64_t)n1 * n1, npatch = N / per;
+    const int64_t patch = dof / per, pix = dof % per;
+    const double f = sqrt(ss[j] / (2.0 * N)) / nb;
+    const int64_t o = ((int64_t)j * npatch + patch) * 2 * per + pix;
+    gimg[o] = (float)(f * g[idx * 2]);
+    gimg[o + per] = (float)(f * g[idx * 2 + 1]);
+}
+
+namespace {
+
+// Scratch of the objective: vectors R, S, Z, Y, G ([nb][2N] each), ss and
+// part ([nb] each), images and their gradient.
+struct OpScratch {
+    double *R, *S, *Z, *Y, *G, *ss, *part;
+    float *img, *gimg;
+};
+
+cudaError_t op_scratch(ibem_cnn* c, int nb, int64_t N, int64_t img_per_vec, OpScratch* o) {
+    const size_t vec = (size_t)2 * N;
+    const size_t nd = 5 * (size_t)nb * vec + 2 * (size_t)nb;
+    const size_t nf = 2 * (size_t)nb * img_per_vec;
+    cudaError_t e;
+    if ((e = grow(&c->d_opvec, &c->opvec_bytes, nd * sizeof(double)))) return e;
+    if ((e = grow(&c->d_opimg, &c->opimg_bytes, nf * sizeof(float)))) return e;
+    double* d = reinterpret_cast<double*>(c->d_opvec);
+    o->R = d;
+    o->S = d + (size_t)nb * vec;
+    o->Z = d + 2 * (size_t)nb * vec;
+    o->Y = d + 3 * (size_t)nb * vec;
+    o->G = d + 4 * (size_t)nb * vec;
+    o->ss = d + 5 * (size_t)nb * vec;
+    o->part = o->ss + nb;
+    o->img = reinterpret_cast<float*>(c->d_opimg);
+    o->gimg = o->img + (size_t)nb * img_per_vec;
+    return cudaSuccess;
+}
+
+// One evaluation of the objective on the nb vectors in o.R (unit norm), and
+// with grad its gradient into c->d_grad; loss into d_red[0].  Runs on c->stream,
+// which must be the handle's stream.
+template <typename T>
+cudaError_t op_batch(ibem_handle* h, ibem_cnn* c, const OpScratch& o, int nb, int bf, int op_prec, bool grad) {
+    Plan& P = h->P;
+    const int64_t N = P.N, vec = 2 * N;
+    const int n1 = P.n1, npatch = P.npatch;
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    for (int j = 0; j < nb; ++j) apply_block_jacobi(h, o.R + (size_t)j * vec, o.S + (size_t)j * vec);
+    vec_sumsq_kernel<<<nb, 256, 0, st>>>(vec, o.S, o.ss);
+    batch_pack_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(nb, N, n1, o.S, o.ss, o.img);
+    c->launches += nb + 2;
+    if ((e = forward<T>(c, o.img, nb * npatch, n1, n1, bf))) return e;
+    batch_unpack_kernel<T><<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(
+        nb, N, n1, reinterpret_cast<const T*>(c->d_act) + c->L * c->act_slot, o.ss, o.S, o.Z);
+    if ((e = apply_operator(h, o.Z, o.Y, nb, op_prec))) return e;
+    residual_sumsq_kernel<<<nb, 256, 0, st>>>(vec, o.R, o.Y, o.part);
+    op_loss_kernel<<<1, 32, 0, st>>>(nb, o.part, c->d_red);
+    c->launches += 3;
+    if (!grad) return cudaGetLastError();
+    // A^H y = conj(A conj(y)): the Galerkin matrix of the symmetric kernel is complex symmetric
+    conj_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>((int64_t)nb * N, o.Y);
+    if ((e = apply_operator(h, o.Y, o.G, nb, op_prec))) return e;
+    conj_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>((int64_t)nb * N, o.G);
+    batch_grad_images_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(nb, N, n1, o.G, o.ss, o.gimg);
+    c->launches += 3;
+    if ((e = backward<T>(c, nullptr, nb * npatch, n1, n1, bf, o.gimg))) return e;
+    return cudaGetLastError();
+}
+
+ibem_status op_checks(ibem_handle* h, ibem_cnn* c) {
+    if (!h || !c) return IBEM_ERR_ARG;
+    if (!h->assembled) return IBEM_ERR_STATE;
+    if (!h->helm) return IBEM_ERR_ARG;
+    return IBEM_OK;
 }
 
 }  // namespace
@@ -565,6 +753,8 @@ ibem_status ibem_cnn_destroy(ibem_cnn* c) {
     cudaFree(c->d_part);
     cudaFree(c->d_img);
     cudaFree(c->d_items);
+    cudaFree(c->d_opvec);
+    cudaFree(c->d_opimg);
     cudaFree(c->d_red);
     delete c;
     return IBEM_OK;
@@ -701,6 +891,85 @@ ibem_status ibem_cnn_train(ibem_cnn* c, const float* in_dev, const float* target
     // d_red[2] sums (1/2) |out - target|^2 over the images of the last epoch
     if (last_epoch_loss) *last_epoch_loss = s / n_images;
     return cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK;
+}
+
+ibem_status ibem_cnn_operator_gradients(ibem_handle* h, ibem_cnn* c, const double* r_dev, int n, int precision,
+                                        int op_precision, float* grad_host, double* loss) {
+    ibem_status s = op_checks(h, c);
+    if (s) return s;
+    if (!r_dev || n < 1 || n > 256 || (precision != IBEM_FP32 && precision != IBEM_BF16) ||
+        (op_precision != IBEM_FP64 && op_precision != IBEM_FP32))
+        return IBEM_ERR_ARG;
+    Plan& P = h->P;
+    cudaStream_t keep = c->stream;
+    c->stream = h->stream;
+    OpScratch o;
+    cudaError_t e = op_scratch(c, n, P.N, (int64_t)P.npatch * 2 * P.n1 * P.n1, &o);
+    if (!e) e = cudaMemcpyAsync(o.R, r_dev, (size_t)n * 2 * P.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (!e) {
+        if (precision == IBEM_BF16) e = op_batch<__nv_bfloat16>(h, c, o, n, 1, op_precision, true);
+        else e = op_batch<float>(h, c, o, n, 0, op_precision, true);
+    }
+    if (!e && grad_host)
+        e = cudaMemcpyAsync(grad_host, c->d_grad, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+    if (!e && loss) e = cudaMemcpyAsync(loss, c->d_red, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    c->stream = keep;
+    if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
+    return IBEM_OK;
+}
+
+ibem_status ibem_cnn_train_operator(ibem_handle* h, ibem_cnn* c, const double* r_dev, int n, int batch, int epochs,
+                                    float lr, unsigned long long seed, int augment, int op_precision,
+                                    double* last_epoch_loss) {
+    ibem_status s = op_checks(h, c);
+    if (s) return s;
+    if (!r_dev || n < 1 || batch < 1 || batch > 256 || epochs < 1 || !(lr > 0.0f) ||
+        (augment & ~IBEM_AUGMENT_PHASE) || (op_precision != IBEM_FP64 && op_precision != IBEM_FP32))
+        return IBEM_ERR_ARG;
+    Plan& P = h->P;
+    const int nb_max = std::min(batch, n);
+    cudaStream_t keep = c->stream;
+    c->stream = h->stream;
+    auto finish = [&](ibem_status r) {
+        c->stream = keep;
+        return r;
+    };
+    OpScratch o;
+    cudaError_t e = op_scratch(c, nb_max, P.N, (int64_t)P.npatch * 2 * P.n1 * P.n1, &o);
+    if (!e) e = grow(&c->d_items, &c->items_bytes, (size_t)n * sizeof(TrainItem));
+    if (e) return finish(IBEM_ERR_OOM);
+    TrainItem* d_items = reinterpret_cast<TrainItem*>(c->d_items);
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> phase(0.0, 2.0 * M_PI);
+    std::vector<TrainItem> items(n);
+    std::vector<int> perm(n);
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::iota(perm.begin(), perm.end(), 0);
+        std::shuffle(perm.begin(), perm.end(), rng);
+        for (int i = 0; i < n; ++i) {
+            const double th = (augment & IBEM_AUGMENT_PHASE) ? phase(rng) : 0.0;
+            items[i] = TrainItem{perm[i], 0, (float)std::cos(th), (float)std::sin(th)};
+        }
+        if (cudaMemcpyAsync(d_items, items.data(), n * sizeof(TrainItem), cudaMemcpyHostToDevice, c->stream) ||
+            cudaMemsetAsync(c->d_red + 2, 0, sizeof(double), c->stream))
+            return finish(IBEM_ERR_CUDA);
+        for (int i0 = 0; i0 < n; i0 += nb_max) {
+            const int nb = std::min(nb_max, n - i0);
+            rot_gather_vec_kernel<<<cblk((int64_t)nb * P.N, 256), 256, 0, c->stream>>>(nb, P.N, d_items + i0, r_dev,
+                                                                                       o.R);
+            ++c->launches;
+            if ((e = op_batch<__nv_bfloat16>(h, c, o, nb, 1, op_precision, true)))
+                return finish(e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA);
+            adam(c, lr);
+        }
+    }
+    double sum = 0.0;
+    if (cudaMemcpyAsync(&sum, c->d_red + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream) ||
+        cudaStreamSynchronize(c->stream))
+        return finish(IBEM_ERR_CUDA);
+    if (last_epoch_loss) *last_epoch_loss = sum / n;
+    return finish(cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK);
 }
 
 ibem_status ibem_cnn_launches(ibem_cnn* c, int64_t* launches) {

@@ -403,4 +403,6 @@ cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, doubl
 // Residual/error training pairs from block-Jacobi GMRES solves (solve.cu).
 ibem_status solver_pairs_impl(ibem_handle* h, const double* b, int nrhs, double rtol, int maxit, int stride,
                               int max_pairs, float* in_img, float* tgt_img, int* n_pairs, ibem_solve_info* info);
+ibem_status solver_residuals_impl(ibem_handle* h, const double* b, int nrhs, double rtol, int maxit, int stride,
+                                  int max_vecs, double* r_out, int* n_out, ibem_solve_info* info);
 }  // namespace ibem

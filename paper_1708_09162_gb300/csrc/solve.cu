@@ -314,7 +314,7 @@ ibem_status cg_reliable(ibem_handle* h, const double* b, double* x, const Work& 
 // r_j = V_{j+1} (beta e_1 - Hbar_j y_j) without an operator application.
 struct Recorder {
     int stride = 1, max = 0, n = 0;
-    double* X = nullptr;  // [max][2N]
+    double* X = nullptr;  // [max][2N], or null: iterates not kept
     double* R = nullptr;  // [max][2N]
 };
 
@@ -458,7 +458,7 @@ ibem_status gmres(ibem_handle* h, const double* b, double* x, double tol_abs, in
                 backsolve(k, y);
                 if (cudaMemcpyAsync(hv, y.data(), 2 * k * sizeof(double), cudaMemcpyHostToDevice, st))
                     return done(IBEM_ERR_CUDA);
-                precond_combine(k, w, rec->X + (size_t)rec->n * 2 * N);
+                if (rec->X) precond_combine(k, w, rec->X + (size_t)rec->n * 2 * N);
                 // r_k = V_{k+1} (beta e_1 - Hbar_k y_k)
                 c[0] = beta;
                 for (int i = 0; i <= k; ++i)
@@ -575,6 +575,67 @@ ibem_status solver_pairs_impl(ibem_handle* h, const double* b, int nrhs, double 
         info->iterations = total_it;
         info->outer = total_outer;
         info->rel_residual = worst;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return release(worst_s);
+}
+
+// dst = src / sqrt(nrm2[0]) (zero if nrm2[0] = 0)
+__global__ void normalize_copy_kernel(int64_t n, const double* __restrict__ src, const double* __restrict__ nrm2,
+                                      double* __restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    dst[i] = nrm2[0] > 0.0 ? src[i] / sqrt(nrm2[0]) : 0.0;
+}
+
+ibem_status solver_residuals_impl(ibem_handle* h, const double* b, int nrhs, double rtol, int maxit, int stride,
+                                  int max_vecs, double* r_out, int* n_out, ibem_solve_info* info) {
+    Plan& P = h->P;
+    const int64_t N = P.N;
+    cudaStream_t st = h->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t vec = (size_t)2 * N;
+    double *R = nullptr, *xs = nullptr;
+    auto release = [&](ibem_status r) {
+        if (R) cudaFreeAsync(R, st);
+        if (xs) cudaFreeAsync(xs, st);
+        cudaStreamSynchronize(st);
+        return r;
+    };
+    if (cudaMallocAsync(&R, (size_t)max_vecs * vec * sizeof(double), st) ||
+        cudaMallocAsync(&xs, vec * sizeof(double), st))
+        return release(IBEM_ERR_OOM);
+    int total = 0, total_it = 0, total_outer = 0;
+    ibem_status worst_s = IBEM_OK;
+    for (int r = 0; r < nrhs; ++r) {
+        const double* bb = b + (size_t)r * vec;
+        double nb;
+        if (norm2(h, bb, vec, &nb) != cudaSuccess) return release(IBEM_ERR_CUDA);
+        if (nb == 0.0) continue;
+        Recorder rec;
+        rec.stride = stride;
+        rec.max = max_vecs;
+        rec.R = R;
+        int its = 0, outer = 0;
+        ibem_status sres = gmres(h, bb, xs, rtol * nb, maxit, IBEM_PRECOND_BLOCK_JACOBI, IBEM_FP64,
+                                 std::max(100, std::min(maxit, 400)), &its, &outer, &rec);
+        if (sres != IBEM_OK && sres != IBEM_ERR_NOCONV) return release(sres);
+        if (sres != IBEM_OK && worst_s == IBEM_OK) worst_s = sres;
+        total_it += its;
+        total_outer += outer;
+        for (int n = 0; n < rec.n; ++n) {
+            dot_kernel<<<1, 1024, 0, st>>>(R + (size_t)n * vec, R + (size_t)n * vec, vec, h->d_red);
+            normalize_copy_kernel<<<nblk(vec, 256), 256, 0, st>>>(vec, R + (size_t)n * vec, h->d_red,
+                                                                  r_out + (size_t)(total + n) * vec);
+        }
+        total += rec.n;
+    }
+    if (cudaGetLastError() != cudaSuccess) return release(IBEM_ERR_CUDA);
+    *n_out = total;
+    if (info) {
+        info->iterations = total_it;
+        info->outer = total_outer;
+        info->rel_residual = 0.0;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return release(worst_s);

@@ -33,7 +33,8 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy",
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
-            "ibem_learned_apply", "ibem_solver_pairs")
+            "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
+            "ibem_cnn_train_operator")
 
 
 class IbemError(RuntimeError):
@@ -116,6 +117,11 @@ def _load():
         "ibem_learned_apply": (I32, [P, P, P]),
         "ibem_solver_pairs": (I32, [P, P, I32, ctypes.c_double, I32, I32, I32, P, P, ctypes.POINTER(I32),
                                     ctypes.POINTER(ibem_solve_info)]),
+        "ibem_solver_residuals": (I32, [P, P, I32, ctypes.c_double, I32, I32, I32, P, ctypes.POINTER(I32),
+                                        ctypes.POINTER(ibem_solve_info)]),
+        "ibem_cnn_operator_gradients": (I32, [P, P, P, I32, I32, I32, P, ctypes.POINTER(ctypes.c_double)]),
+        "ibem_cnn_train_operator": (I32, [P, P, P, I32, I32, I32, ctypes.c_float, ctypes.c_ulonglong, I32, I32,
+                                          ctypes.POINTER(ctypes.c_double)]),
         "ibem_last_error": (ctypes.c_char_p, [P]),
         "ibem_status_string": (ctypes.c_char_p, [I32]),
     }
@@ -418,3 +424,34 @@ def ibem_solver_pairs(h, b, nrhs, in_img, tgt_img, rtol=1e-10, maxit=400, stride
         _check(s, h)
         return n.value, info
     return s, n.value, info
+
+
+def ibem_solver_residuals(h, b, nrhs, r_out, rtol=1e-10, maxit=400, stride=1, max_vecs=32, check=True):
+    """Unit-norm solver residuals into r_out (float64 CUDA [nrhs * max_vecs, ndof, 2]);
+    returns (n, info) or (status, n, info) with check=False."""
+    n = ctypes.c_int()
+    info = ibem_solve_info()
+    s = _lib.ibem_solver_residuals(h, _dptr(b), nrhs, rtol, maxit, stride, max_vecs, _dptr(r_out), ctypes.byref(n),
+                                   ctypes.byref(info))
+    if check:
+        _check(s, h)
+        return n.value, info
+    return s, n.value, info
+
+
+def ibem_cnn_operator_gradients(h, c, r, n, precision=IBEM_FP32, op_precision=IBEM_FP64):
+    """(loss, gradient) of the residual-norm objective on n residuals r (float64 CUDA)."""
+    m = ctypes.c_size_t()
+    _check(_lib.ibem_cnn_params(c, None, None, ctypes.byref(m)))
+    g = np.zeros(m.value, dtype=np.float32)
+    loss = ctypes.c_double()
+    _check(_lib.ibem_cnn_operator_gradients(h, c, _dptr(r), n, precision, op_precision,
+                                            g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss)), h)
+    return loss.value, g
+
+
+def ibem_cnn_train_operator(h, c, r, n, batch, epochs, lr, seed=0, augment=IBEM_AUGMENT_PHASE, op_precision=IBEM_FP32):
+    loss = ctypes.c_double()
+    _check(_lib.ibem_cnn_train_operator(h, c, _dptr(r), n, batch, epochs, lr, seed, augment, op_precision,
+                                        ctypes.byref(loss)), h)
+    return loss.value
