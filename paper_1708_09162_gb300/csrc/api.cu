@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 
+#include <algorithm>
+
 #include "ibem_internal.cuh"
 
 using namespace ibem;
@@ -313,6 +315,11 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
             if (len > 0) h->up_rows.push_back((int32_t)c);
             if (len > h->max_up_row) h->max_up_row = len;
         }
+        // longest rows first: the CTAs of the coupling launch start in this
+        // order, so the last wave holds the short rows (smaller tail)
+        std::stable_sort(h->up_rows.begin(), h->up_rows.end(), [&](int32_t x, int32_t y) {
+            return uptr[x + 1] - uptr[x] > uptr[y + 1] - uptr[y];
+        });
         h->n_up = (int64_t)usrc.size();
         std::vector<int64_t> tptr(P.C + 1, 0);
         for (int32_t v : usrc) tptr[v + 1]++;
@@ -416,6 +423,8 @@ ibem_status ibem_assemble(ibem_handle* h) {
         std::string msg;
         if ((e = build_block_jacobi(h, &msg))) return msg.empty() ? cuda_fail(h, e, "block-Jacobi") : fail(h, IBEM_ERR_BREAKDOWN, msg);
     }
+    if (!h->helm && h->d_Kdf && !h->up_rows.empty())
+        if ((e = tune_coupling_df(h))) return cuda_fail(h, e, "coupling autotune");
     h->assembled = true;
     return IBEM_OK;
 }

@@ -280,6 +280,7 @@ struct ibem_handle {
     double* d_hsy = nullptr;        // Helmholtz: split-layout output [2R][N]
     bool far_on_the_fly = false;    // Helmholtz FP64 coupling generated on the fly (stored K too large)
     int kpt = 0;
+    int df_nst = 0;   // ring depth of the double-float coupling (autotuned at assembly; 0 = default)
     std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
     int max_far_row = 0;            // longest far list
     // upper half of the far field (source id > target id), used with symmetric storage
@@ -397,6 +398,9 @@ cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
 bool mr_supported(const ibem_handle* h, int nrhs);
 cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs);
 void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
+// Double-float coupling launcher and the autotuner of its ring depth (kernels_apply.cu).
+cudaError_t launch_coupling_df(ibem_handle* h, int R, int nst);
+cudaError_t tune_coupling_df(ibem_handle* h);
 
 // Learned preconditioner (cnn.cu): z = s + sigma net(s / sigma), s = B^-1 v.
 cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, double* z);

@@ -291,9 +291,11 @@ __device__ inline void df_fma(float kh, float kl, float xh, float xl, float& hi,
     df_add(hi, lo, p, e);
 }
 
-template <int KPT, int NST>
+// EXACT: q2 == 4 KPT (even q), so every lane's columns and rows exist and the
+// strides are compile-time constants.
+template <int KPT, int NST, bool EXACT>
 __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
-                                   const int32_t* __restrict__ fsrc, const float2* __restrict__ K, int q2,
+                                   const int32_t* __restrict__ fsrc, const float2* __restrict__ K, int q2_rt,
                                    int q2p, int maxrow, int64_t C, const float2* __restrict__ xh,
                                    double* __restrict__ yh, float2* __restrict__ colpart, int64_t nblk_total,
                                    long long wait_limit, int* __restrict__ status) {
@@ -302,6 +304,7 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
     // (coupling block, source moments)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     int32_t* srcs = reinterpret_cast<int32_t*>(smem + 128);
+    const int q2 = EXACT ? 4 * KPT : q2_rt;
     const int stride = 4 * q2;
     const int belems = KPT * stride;
     const int selems = belems + q2p;
@@ -320,7 +323,7 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
         int row = sc + 4 * j;
-        xs[j] = (active && row < q2) ? xr[(int64_t)sigma * q2p + row] : make_float2(0.f, 0.f);
+        xs[j] = (active && (EXACT || row < q2)) ? xr[(int64_t)sigma * q2p + row] : make_float2(0.f, 0.f);
     }
     if (t == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&full[i], 1);
@@ -353,7 +356,7 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
 #pragma unroll
             for (int kk = 0; kk < KPT; ++kk) {
                 int b = s + 4 * kk;
-                if (b < q2) {
+                if (EXACT || b < q2) {
                     float2 kv = Kb[kk * stride + t];
                     float2 x = xt[b];
                     df_fma(kv.x, kv.y, x.x, x.y, hi, lo);
@@ -368,7 +371,7 @@ __global__ void coupling_df_kernel(const int32_t* __restrict__ rows, const int64
             const float2* Kc = Kb + (bc >> 2) * stride + (bc & 3) + 4 * sc;
 #pragma unroll
             for (int j = 0; j < KPT; ++j) {
-                if (sc + 4 * j < q2) {
+                if (EXACT || sc + 4 * j < q2) {
                     float2 kv = Kc[16 * j];
                     df_fma(kv.x, kv.y, xs[j].x, xs[j].y, ch, cl);
                 }
@@ -619,6 +622,113 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
 
 
 
+namespace {
+
+template <int KPT, int NST, bool EXACT>
+cudaError_t launch_df_t(ibem_handle* h, int R) {
+    const int q2 = h->P.q2, q2p = (q2 + 1) & ~1;
+    const int threads = ((4 * q2 + 31) / 32) * 32;
+    const size_t sbytes = ((size_t)KPT * 4 * q2 + q2p) * sizeof(float2);
+    const size_t head = 128 + (((size_t)h->max_up_row * 4 + 15) / 16) * 16;
+    const size_t sm = head + (size_t)NST * sbytes;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(coupling_df_kernel<KPT, NST, EXACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm)))
+        return e;
+    dim3 grid((unsigned)h->up_rows.size(), R);
+    coupling_df_kernel<KPT, NST, EXACT><<<grid, threads, sm, h->stream>>>(
+        h->d_up_rows, h->d_up_ptr, h->d_up_src, h->d_Kdf, q2, q2p, h->max_up_row, h->P.C, h->d_xh2, h->d_yh,
+        h->d_colpart, h->n_up, h->wait_limit, h->d_status);
+    return cudaGetLastError();
+}
+
+// Ring depths instantiated per KPT for even q (q = 2, 4, 6, 8, 10, 12).
+std::vector<int> df_depth_candidates(int kpt) {
+    switch (kpt) {
+        case 1: return {4, 8};
+        case 4: return {4, 6};
+        case 9: return {2, 3, 4};
+        case 16: return {2, 3};
+        case 25: return {2};
+        case 36: return {1};
+        default: return {};
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_coupling_df(ibem_handle* h, int R, int nst) {
+    if (4 * h->kpt == h->P.q2) {
+        if (nst == 0) nst = df_depth_candidates(h->kpt).back();
+        switch (h->kpt * 16 + nst) {
+            case 1 * 16 + 4: return launch_df_t<1, 4, true>(h, R);
+            case 1 * 16 + 8: return launch_df_t<1, 8, true>(h, R);
+            case 4 * 16 + 4: return launch_df_t<4, 4, true>(h, R);
+            case 4 * 16 + 6: return launch_df_t<4, 6, true>(h, R);
+            case 9 * 16 + 2: return launch_df_t<9, 2, true>(h, R);
+            case 9 * 16 + 3: return launch_df_t<9, 3, true>(h, R);
+            case 9 * 16 + 4: return launch_df_t<9, 4, true>(h, R);
+            case 16 * 16 + 2: return launch_df_t<16, 2, true>(h, R);
+            case 16 * 16 + 3: return launch_df_t<16, 3, true>(h, R);
+            case 25 * 16 + 2: return launch_df_t<25, 2, true>(h, R);
+            case 36 * 16 + 1: return launch_df_t<36, 1, true>(h, R);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (h->kpt) {
+        case 3: return launch_df_t<3, 8, false>(h, R);
+        case 7: return launch_df_t<7, 4, false>(h, R);
+        case 13: return launch_df_t<13, 3, false>(h, R);
+        case 21: return launch_df_t<21, 2, false>(h, R);
+        case 31: return launch_df_t<31, 1, false>(h, R);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Autotuner of the ring depth (even q): every candidate depth whose shared
+// memory fits is run twice on the handle's own stored matrices (moments set to
+// zero) and the fastest second run is kept.  Called once, at the end of
+// assembly, outside any stream capture.
+cudaError_t tune_coupling_df(ibem_handle* h) {
+    h->df_nst = 0;
+    if (4 * h->kpt != h->P.q2) return cudaSuccess;
+    const int q2 = h->P.q2, q2p = (q2 + 1) & ~1;
+    const size_t sbytes = ((size_t)h->kpt * 4 * q2 + q2p) * sizeof(float2);
+    const size_t head = 128 + (((size_t)h->max_up_row * 4 + 15) / 16) * 16;
+    std::vector<int> depths;
+    for (int n : df_depth_candidates(h->kpt))
+        if (head + (size_t)n * sbytes <= 227 * 1024) depths.push_back(n);
+    if (depths.empty()) return cudaErrorInvalidValue;
+    h->df_nst = depths.back();
+    if (depths.size() == 1) return cudaSuccess;
+    cudaError_t e;
+    if ((e = ensure_workspace(h, 1))) return e;
+    if ((e = cudaMemsetAsync(h->d_xh2, 0, (size_t)h->P.C * q2p * sizeof(float2), h->stream))) return e;
+    cudaEvent_t a, b;
+    if ((e = cudaEventCreate(&a))) return e;
+    if ((e = cudaEventCreate(&b))) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    float best = 1e30f;
+    for (int n : depths) {
+        if ((e = launch_coupling_df(h, 1, n))) break;
+        cudaEventRecord(a, h->stream);
+        if ((e = launch_coupling_df(h, 1, n))) break;
+        cudaEventRecord(b, h->stream);
+        if ((e = cudaEventSynchronize(b))) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            h->df_nst = n;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
+}
+
 cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs, int precision) {
     Plan& P = h->P;
     cudaStream_t st = h->stream;
@@ -678,39 +788,9 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
                                                                       q2, h->kpt, P.C, h->d_xh, h->d_yh);
                 h->launches++;
             } else {
-                int threads = ((4 * q2 + 31) / 32) * 32;
                 const int q2p = (q2 + 1) & ~1;
                 split_kernel<<<nblk(R * P.C * q2p, T), T, 0, st>>>(R * P.C, q2, q2p, h->d_xh, h->d_xh2);
-                dim3 grid((unsigned)h->up_rows.size(), R);
-                const size_t sbytes = ((size_t)h->kpt * 4 * q2 + q2p) * sizeof(float2);
-                const size_t head = 128 + (((size_t)h->max_up_row * 4 + 15) / 16) * 16;
-#define IBEM_DF_LAUNCH(K_, N_)                                                                                   \
-    {                                                                                                            \
-        size_t sm = head + (size_t)(N_)*sbytes;                                                                  \
-        if ((e = cudaFuncSetAttribute(coupling_df_kernel<K_, N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                      (int)sm)))                                                                 \
-            return e;                                                                                            \
-        coupling_df_kernel<K_, N_><<<grid, threads, sm, st>>>(h->d_up_rows, h->d_up_ptr, h->d_up_src,            \
-                                                              h->d_Kdf, q2, q2p, h->max_up_row, P.C, h->d_xh2,  \
-                                                              h->d_yh, h->d_colpart, h->n_up, h->wait_limit,    \
-                                                              h->d_status);                                      \
-    }                                                                                                            \
-    break;
-                switch (h->kpt) {
-                    case 1: IBEM_DF_LAUNCH(1, 8)
-                    case 3: IBEM_DF_LAUNCH(3, 8)
-                    case 4: IBEM_DF_LAUNCH(4, 6)
-                    case 7: IBEM_DF_LAUNCH(7, 4)
-                    case 9: IBEM_DF_LAUNCH(9, 4)
-                    case 13: IBEM_DF_LAUNCH(13, 3)
-                    case 16: IBEM_DF_LAUNCH(16, 2)
-                    case 21: IBEM_DF_LAUNCH(21, 2)
-                    case 25: IBEM_DF_LAUNCH(25, 2)
-                    case 31: IBEM_DF_LAUNCH(31, 1)
-                    case 36: IBEM_DF_LAUNCH(36, 1)
-                    default: return cudaErrorInvalidValue;
-                }
-#undef IBEM_DF_LAUNCH
+                if ((e = launch_coupling_df(h, R, h->df_nst))) return e;
                 column_gather_kernel<<<nblk((int64_t)R * P.C * q2, T), T, 0, st>>>(R, P.C, q2, h->d_tr_ptr, h->d_tr_blk,
                                                                                    h->d_colpart, h->n_up, h->d_yh);
                 h->launches++;
