@@ -345,8 +345,17 @@ def learned_preconditioner(ibem, stream, args):
     fwd_ms = ev0.elapsed_time(ev1) / reps
     C = 32
     flops = 2.0 * 9 * (2 * C + C * C + C * C + C * 2) * B * H * H
-    _, mhz, src = _peaks()
-    fp32_peak = 152 * 128 * 2 * mhz * 1e6
+    # algorithmic bytes per pixel: FP32 input (8), packed input written and read
+    # (16 + 16), three 32-channel BF16 activations written and read (3 x 128),
+    # BF16 output (4)
+    nbytes = (8 + 16 + 16 + 3 * 128 + 4) * B * H * H
+    hbm, _, src = _peaks()
+    bf16_peak = 1912.6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = json.load(f).get("bf16_tflops", bf16_peak)
+    except OSError:
+        pass
     ibem.ibem_cnn_destroy(c)
     it_b, it_l = res["block_jacobi"]["iterations"], res["learned"]["iterations"]
     return {"workload": "helmholtz-sphere-p2-q6-k[8,16]: train level %d, solve level %d, %d plane waves"
@@ -354,10 +363,13 @@ def learned_preconditioner(ibem, stream, args):
             "k_solve": k, "ndof": info.ndof, "train": train, "train_s": train_s, "solve": res,
             "iterations_learned_over_block_jacobi": it_l / max(1, it_b),
             "seconds_learned_over_block_jacobi": res["learned"]["seconds"] / max(1e-9, res["block_jacobi"]["seconds"]),
-            "cnn_forward": {"images": B, "size": H, "ms": fwd_ms, "tflops": flops / (fwd_ms * 1e-3) / 1e12,
-                            "bound": "alu", "peak_tflops": fp32_peak / 1e12,
-                            "frac": flops / (fwd_ms * 1e-3) / fp32_peak,
-                            "peak_note": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz (%s clock)" % (mhz, src)}}
+            "cnn_forward": {"images": B, "size": H, "ms": fwd_ms, "kernels": "conv_tc_kernel (tcgen05) x 4",
+                            "bound": "hbm", "algorithmic_bytes": nbytes,
+                            "achieved_gbs": nbytes / (fwd_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                            "frac": nbytes / (fwd_ms * 1e-3) / 1e9 / hbm,
+                            "tflops": flops / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16_peak,
+                            "tensor_frac": flops / (fwd_ms * 1e-3) / 1e12 / bf16_peak,
+                            "peak_note": "MEASURED_PEAKS.json (%s)" % src}}
 
 
 # ---------------------------------------------------------------- our arm

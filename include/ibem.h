@@ -321,7 +321,8 @@ ibem_status ibem_cnn_destroy(ibem_cnn* cnn);
 ibem_status ibem_cnn_params(ibem_cnn* cnn, float* get_host, const float* set_host, size_t* count);
 
 /* out_dev = net(in_dev) for B images of H x W; precision IBEM_FP32 or
- * IBEM_BF16.  Enqueues only. */
+ * IBEM_BF16.  In BF16 with C = 32 all four layers run on the tensor cores
+ * (tcgen05, BF16 operands, FP32 accumulation).  Enqueues only. */
 ibem_status ibem_cnn_forward(ibem_cnn* cnn, const float* in_dev, int B, int H, int W, float* out_dev,
                              int precision);
 
@@ -343,6 +344,12 @@ ibem_status ibem_cnn_train_step(ibem_cnn* cnn, const float* in_dev, const float*
 ibem_status ibem_cnn_train(ibem_cnn* cnn, const float* in_dev, const float* target_dev, int n_images, int H,
                            int W, int batch, int epochs, float lr, unsigned long long seed, int augment,
                            double* last_epoch_loss);
+
+/* Status word of the network's own device waits (bounded waits of the
+ * tensor-core layers in ibem_cnn_forward), then cleared: 0 or
+ * IBEM_DEVICE_TIMEOUT.  Synchronises.  Inside the preconditioner the handle's
+ * status word (ibem_device_status) is used instead. */
+ibem_status ibem_cnn_device_status(ibem_cnn* cnn, int* status);
 
 /* Kernel launches of the network since the last call (then reset). */
 ibem_status ibem_cnn_launches(ibem_cnn* cnn, int64_t* launches);

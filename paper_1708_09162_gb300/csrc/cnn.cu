@@ -14,12 +14,14 @@
 // Preconditioner: s = B^-1 v (block-Jacobi), sigma = |s| / sqrt(2N),
 // z = s + sigma * net(s / sigma), the network in BF16.
 //
-// Kernels: one tiled direct convolution (16 x 16 output pixels of one image and
-// 16 output channels per CTA, input halo tile and weights staged in shared
-// memory, FP32 FMA) serves the forward pass and, with flipped transposed
-// weights and the ReLU mask fused, the input gradient; the weight gradient is
-// a tiled reduction over pixels into per-CTA partial sums that a second kernel
-// adds in a fixed order, so training is deterministic.
+// Kernels: inference in BF16 (the preconditioner, ibem_cnn_forward) runs all
+// four layers on the tensor cores (tcgen05 implicit GEMM, conv_tc_kernel).
+// Training and the FP32 mode use one tiled direct convolution (16 x 16 output
+// pixels of one image and 16 output channels per CTA, input halo tile and
+// weights staged in shared memory, FP32 FMA) for the forward pass and, with
+// flipped transposed weights and the ReLU mask fused, the input gradient; the
+// weight gradient is a tiled reduction over pixels into per-CTA partial sums
+// that a second kernel adds in a fixed order, so training is deterministic.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -58,6 +60,9 @@ struct ibem_cnn {
     size_t opvec_bytes = 0;
     void* d_opimg = nullptr;     // residual-norm objective: images
     size_t opimg_bytes = 0;
+    void* d_wtc = nullptr;       // BF16 tensor-core weight tiles of the four layers
+    size_t wtc_bytes = 0;
+    int* d_status = nullptr;     // device-side wait status of the tensor-core layers
     double* d_red = nullptr;     // [0] loss, [1] |s|^2, [2] loss sum of an epoch
     cudaStream_t stream = nullptr;
     int64_t launches = 0;
@@ -139,6 +144,232 @@ __global__ void __launch_bounds__(256) conv_tile_kernel(const TI* __restrict__ i
         if (mask && !(ld_act(mask, o) > 0.0f)) r = 0.0f;
         st_act(out, o, r);
     }
+}
+
+// ---- inference layers on the tensor cores -----------------------------------------
+// Implicit GEMM: D[m][co] = sum over taps (dy, dx) and input channels of
+// A_tap[m][ci] W_tap[co][ci], with m an output position in padded-pitch order
+// o = y * P + x (P = W + 2; columns x >= W are computed and discarded).  The
+// input positions of tap (dy, dx) are o + dy * P + dx in the zero-padded
+// image, so one shared-memory band of padded rows serves all nine taps: tap
+// (dy, dx) is the same band started dy * P + dx rows later.  Band layout
+// (tcgen05 canonical K-major, no swizzle): channel group g (8 channels, 16
+// bytes) of band row r at (g * NBP + r) * 16 bytes, so rows are contiguous
+// (core-matrix stride along M = 128 B) and the channel groups are NBP * 16 B
+// apart (stride along K).  Weights per tap: core (co / 8, ci / 8) at
+// ((co / 8) * KG + ci / 8) * 128 B.  A tile is TC_MB blocks of 128 consecutive
+// positions sharing one band of TC_MB * 128 + 2P + 2 rows (copied with cp.async,
+// zero-filled outside the image); each block accumulates in its own 32 TMEM
+// columns (tcgen05.mma kind::f16, M = 128, N = NP, K = 16, BF16 operands, FP32
+// accumulation), and all MMAs of a tile are committed once.  Epilogue: bias,
+// optional ReLU, BF16 store.
+//   CGI: channel groups of an input pixel (1: the 2-channel input padded to 8
+//        channels, 4: 32 channels); the band holds KG = max(CGI, 2) groups
+//        (the second group of a 1-group input is zero, and so are its weights).
+//   NP:  MMA width (32, or 16 for the 2-channel output layer); NOUT channels kept.
+//   OUT_PLANAR: output [B][NOUT][H][W] (last layer) instead of pixel-major.
+constexpr int TC_M = 128;
+constexpr int TC_MB = 4;
+
+__device__ inline unsigned cnn_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline uint64_t cnn_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ inline bool cnn_wait(uint64_t* bar, unsigned parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(cnn_smem(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// w [Cout][Cin][9] FP32 -> BF16 canonical tiles [9][NP / 8][KG][8][8] (zero padded)
+__global__ void tc_weights_kernel(const float* __restrict__ w, int Cin, int Cout, int NP, int KG,
+                                  __nv_bfloat16* __restrict__ wt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int CI = 8 * KG;
+    if (i >= NP * CI * 9) return;
+    const int k = i % 9, ci = (i / 9) % CI, co = i / (9 * CI);
+    const float v = (co < Cout && ci < Cin) ? w[((int64_t)co * Cin + ci) * 9 + k] : 0.0f;
+    wt[(k * (NP / 8) * KG + (co >> 3) * KG + (ci >> 3)) * 64 + (co & 7) * 8 + (ci & 7)] = __float2bfloat16(v);
+}
+
+// FP32 planar [B][2][H][W] -> BF16 pixel-major [B][H][W][8] (channels 2..7 zero)
+__global__ void pack8_kernel(int64_t npx, int64_t HW, const float* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    const int64_t b = i / HW, pix = i % HW;
+    __nv_bfloat162 v = __floats2bfloat162_rn(in[(b * 2) * HW + pix], in[(b * 2 + 1) * HW + pix]);
+    *reinterpret_cast<uint4*>(out + i * 8) = make_uint4(*reinterpret_cast<uint32_t*>(&v), 0u, 0u, 0u);
+}
+
+// Persistent CTAs of 128 threads (one output position per thread and block).
+template <int CGI, int NP, int NOUT, bool OUT_PLANAR>
+__global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __restrict__ in, int B, int H, int W,
+                                                      const __nv_bfloat16* __restrict__ wt,
+                                                      const float* __restrict__ bias, int relu, int nbp,
+                                                      __nv_bfloat16* __restrict__ out, long long wait_limit,
+                                                      int* __restrict__ status) {
+    constexpr int KG = CGI < 2 ? 2 : CGI;
+    constexpr int WBYTES = 9 * (NP / 8) * KG * 128;
+    constexpr int TILE = TC_M * TC_MB;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* wsm = smem;
+    unsigned char* band = smem + WBYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(band + KG * nbp * 16);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int P = W + 2;
+    const int64_t tiles_img = ((int64_t)H * P + TILE - 1) / TILE;
+    const int64_t ntiles = (int64_t)B * tiles_img;
+    const int nb = TILE + 2 * P + 2;
+    for (int i = t; i < WBYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(wsm)[i] = reinterpret_cast<const uint4*>(wt)[i];
+    if (CGI < KG)   // zero channel group of a 1-group input
+        for (int r = t; r < nbp; r += blockDim.x)
+            *reinterpret_cast<uint4*>(band + ((size_t)1 * nbp + r) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    float bv[NOUT];
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) bv[c] = bias[c];
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(cnn_smem(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cnn_smem(tslot)),
+                     "r"(32 * TC_MB)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+    // descriptors of offset 0; an operand starting k * 16 bytes later is desc + k
+    // (the start-address field counts 16-byte units; all addresses < 256 KB)
+    const uint64_t adesc0 = cnn_desc(cnn_smem(band), nbp * 16, 128);
+    const uint64_t bdesc0 = cnn_desc(cnn_smem(wsm), 128, KG * 128);
+    int it = 0;
+    bool failed = false;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int64_t b = tile / tiles_img;
+        const int o0 = (int)((tile % tiles_img) * TILE);
+        // band of padded rows o0 .. o0 + nb - 1: all 16-byte copies in flight at
+        // once (cp.async), zero-filled outside the image (source size 0)
+        for (int idx = t; idx < nb * CGI; idx += blockDim.x) {
+            const int r = idx / CGI, g = idx % CGI;
+            const int i = o0 + r;
+            const int py = i / P, px = i - py * P;
+            const bool inside = py >= 1 && py <= H && px >= 1 && px <= W;
+            const __nv_bfloat16* s = inside ? in + ((b * H + (py - 1)) * W + (px - 1)) * (8 * CGI) + g * 8 : in;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                             cnn_smem(band + ((size_t)g * nbp + r) * 16)),
+                         "l"(s), "r"(inside ? 16u : 0u)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (t == 0) {
+#pragma unroll 1
+            for (int mb = 0; mb < TC_MB; ++mb)
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int roff = mb * TC_M + (tap / 3) * P + (tap % 3);
+                    for (int s = 0; s < KG / 2; ++s) {
+                        const uint64_t ad = adesc0 + (uint64_t)(2 * s * nbp + roff);
+                        const uint64_t bd = bdesc0 + (uint64_t)(tap * (NP / 8) * KG * 8 + 2 * s * 8);
+                        const uint32_t acc = (tap > 0 || s > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + 32u * mb),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                            : "memory");
+                    }
+                }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             cnn_smem(mbar))
+                         : "memory");
+        }
+        const bool ok = cnn_wait(mbar, (unsigned)(it & 1), wait_limit);
+        if (__syncthreads_or(!ok)) {
+            // the MMAs may still run: wait for them (bounded) before the band is released
+            cnn_wait(mbar, (unsigned)(it & 1), 1LL << 24);
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int mb = 0; mb < TC_MB; ++mb) {
+            const int o = o0 + mb * TC_M + 32 * warp + lane;
+            const int y = o / P, x = o - y * P;
+            uint32_t v[NP];
+#pragma unroll
+            for (int c0 = 0; c0 < NP; c0 += 16) {
+                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * mb + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[c0 + 0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
+                      "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
+                      "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
+                      "=r"(v[c0 + 15])
+                    : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (y < H && x < W) {
+                if constexpr (OUT_PLANAR) {
+#pragma unroll
+                    for (int co = 0; co < NOUT; ++co) {
+                        float f = __uint_as_float(v[co]) + bv[co];
+                        if (relu) f = fmaxf(f, 0.0f);
+                        out[((b * NOUT + co) * H + y) * (int64_t)W + x] = __float2bfloat16(f);
+                    }
+                } else {
+                    uint4* dst = reinterpret_cast<uint4*>(out + ((b * H + y) * W + x) * NOUT);
+#pragma unroll
+                    for (int q4 = 0; q4 < NOUT / 8; ++q4) {
+                        uint32_t pk[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float f0 = __uint_as_float(v[q4 * 8 + 2 * j]) + bv[q4 * 8 + 2 * j];
+                            float f1 = __uint_as_float(v[q4 * 8 + 2 * j + 1]) + bv[q4 * 8 + 2 * j + 1];
+                            if (relu) {
+                                f0 = fmaxf(f0, 0.0f);
+                                f1 = fmaxf(f1, 0.0f);
+                            }
+                            __nv_bfloat162 h2 = __floats2bfloat162_rn(f0, f1);
+                            pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+                        }
+                        dst[q4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    }
+                }
+            }
+        }
+        // the next tile rewrites the band and the accumulators
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (failed && t == 0) atomicOr(status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32 * TC_MB)
+                     : "memory");
 }
 
 // wt[ci][co][k] = w[co][ci][8 - k] (rounded to BF16 in BF16 mode): the kernel of
@@ -421,6 +652,72 @@ cudaError_t forward(ibem_cnn* c, const float* in, int B, int H, int W, int bf) {
     return cudaGetLastError();
 }
 
+// Inference forward in BF16 on the tensor cores (C = 32 and a band that fits in
+// shared memory; otherwise the FMA path).  Slots: 0 the input as BF16 pixel-major
+// 8-channel pixels, 1..3 hidden outputs (pixel-major), 4 the output (planar), so
+// the output sits where forward() leaves it.
+template <int CGI, int NP, int NOUT, bool OUT_PLANAR>
+cudaError_t launch_tc(ibem_cnn* c, const __nv_bfloat16* in, int B, int H, int W, const __nv_bfloat16* wt,
+                      const float* bias, int relu, __nv_bfloat16* out, int* status, long long wait_limit) {
+    constexpr int KG = CGI < 2 ? 2 : CGI;
+    const int P = W + 2, nb = TC_M * TC_MB + 2 * P + 2, nbp = ((nb + 7) & ~7) + 2;
+    const size_t sm = (size_t)9 * (NP / 8) * KG * 128 + (size_t)KG * nbp * 16 + 16;
+    auto kern = conv_tc_kernel<CGI, NP, NOUT, OUT_PLANAR>;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern))) return e;
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    // resident CTAs per SM from shared memory (1 KB reserved per CTA), registers
+    // and TMEM (512 columns, 32 * TC_MB per CTA)
+    int per_sm = (int)std::min<size_t>(512 / (32 * TC_MB), (size_t)233472 / (sm + 1024));
+    per_sm = std::min(per_sm, 65536 / std::max(1, fa.numRegs * 128));
+    per_sm = std::max(per_sm, 1);
+    const int64_t ntiles = (int64_t)B * (((int64_t)H * P + TC_M * TC_MB - 1) / (TC_M * TC_MB));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)per_sm * nsm));
+    kern<<<grid, 128, sm, c->stream>>>(in, B, H, W, wt, bias, relu, nbp, out, wait_limit, status);
+    ++c->launches;
+    return cudaGetLastError();
+}
+
+bool tc_fits(int W) {
+    const int P = W + 2, nb = TC_M * TC_MB + 2 * P + 2, nbp = ((nb + 7) & ~7) + 2;
+    return (size_t)9 * 4 * 4 * 128 + (size_t)4 * nbp * 16 + 16 <= 227 * 1024;
+}
+
+cudaError_t forward_infer(ibem_cnn* c, const float* in, int B, int H, int W, int* status, long long wait_limit) {
+    if (c->C != 32 || c->L != 4 || !tc_fits(W)) return forward<__nv_bfloat16>(c, in, B, H, W, 1);
+    cudaError_t e;
+    if ((e = ensure_buffers(c, B, H, W))) return e;
+    // weight tiles: layer 0 [9][4][2], layers 1, 2 [9][4][4], layer 3 [9][2][4] cores of 64 elements
+    const size_t w0 = 9 * 4 * 2 * 64, w1 = 9 * 4 * 4 * 64, w3 = 9 * 2 * 4 * 64;
+    if ((e = grow(&c->d_wtc, &c->wtc_bytes, (w0 + 2 * w1 + w3) * sizeof(__nv_bfloat16)))) return e;
+    __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(c->d_wtc);
+    __nv_bfloat16* wl[4] = {wt, wt + w0, wt + w0 + w1, wt + w0 + 2 * w1};
+    const int np[4] = {32, 32, 32, 16}, kg[4] = {2, 4, 4, 4};
+    for (int l = 0; l < 4; ++l) {
+        const int n = np[l] * 8 * kg[l] * 9;
+        tc_weights_kernel<<<cblk(n, 256), 256, 0, c->stream>>>(c->d_param + c->woff[l], c->cin[l], c->cout[l], np[l],
+                                                              kg[l], wl[l]);
+    }
+    const size_t per = c->act_slot;
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(c->d_act);
+    const int64_t npx = (int64_t)B * H * W;
+    pack8_kernel<<<cblk(npx, 256), 256, 0, c->stream>>>(npx, (int64_t)H * W, in, act);
+    c->launches += 5;
+    if ((e = launch_tc<1, 32, 32, false>(c, act, B, H, W, wl[0], c->d_param + c->boff[0], 1, act + per, status,
+                                         wait_limit)))
+        return e;
+    for (int l = 1; l <= 2; ++l)
+        if ((e = launch_tc<4, 32, 32, false>(c, act + l * per, B, H, W, wl[l], c->d_param + c->boff[l], 1,
+                                             act + (l + 1) * per, status, wait_limit)))
+            return e;
+    return launch_tc<4, 16, 2, true>(c, act + 3 * per, B, H, W, wl[3], c->d_param + c->boff[3], 0, act + 4 * per,
+                                     status, wait_limit);
+}
+
 // backward from the loss against target (forward must have run on the same
 // batch); gradients into d_grad, loss into d_red[0]
 template <typename T>
@@ -679,7 +976,7 @@ cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, doubl
     apply_block_jacobi(h, v, z);
     sumsq_kernel<<<1, 1024, 0, h->stream>>>(2 * P.N, z, c->d_red + 1);
     pack_images_kernel<<<cblk(P.N, 256), 256, 0, h->stream>>>(P.N, n1, z, c->d_red + 1, c->d_img);
-    e = forward<__nv_bfloat16>(c, c->d_img, B, n1, n1, 1);
+    e = forward_infer(c, c->d_img, B, n1, n1, h->d_status, h->wait_limit);
     if (!e) {
         unpack_add_kernel<__nv_bfloat16><<<cblk(P.N, 256), 256, 0, h->stream>>>(
             P.N, n1, reinterpret_cast<const __nv_bfloat16*>(c->d_act) + c->L * c->act_slot, c->d_red + 1, z);
@@ -724,7 +1021,8 @@ ibem_status ibem_cnn_create(int channels, unsigned long long seed, void* cuda_st
     }
     if (cudaMalloc(&c->d_param, off * sizeof(float)) || cudaMalloc(&c->d_grad, off * sizeof(float)) ||
         cudaMalloc(&c->d_m, off * sizeof(float)) || cudaMalloc(&c->d_v, off * sizeof(float)) ||
-        cudaMalloc(&c->d_wt, maxw * sizeof(float)) || cudaMalloc(&c->d_red, 8 * sizeof(double))) {
+        cudaMalloc(&c->d_wt, maxw * sizeof(float)) || cudaMalloc(&c->d_red, 8 * sizeof(double)) ||
+        cudaMalloc(&c->d_status, sizeof(int))) {
         ibem_cnn_destroy(c);
         return IBEM_ERR_OOM;
     }
@@ -732,7 +1030,8 @@ ibem_status ibem_cnn_create(int channels, unsigned long long seed, void* cuda_st
         cudaMemsetAsync(c->d_grad, 0, off * sizeof(float), c->stream) ||
         cudaMemsetAsync(c->d_m, 0, off * sizeof(float), c->stream) ||
         cudaMemsetAsync(c->d_v, 0, off * sizeof(float), c->stream) ||
-        cudaMemsetAsync(c->d_red, 0, 8 * sizeof(double), c->stream) || cudaStreamSynchronize(c->stream)) {
+        cudaMemsetAsync(c->d_red, 0, 8 * sizeof(double), c->stream) ||
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) || cudaStreamSynchronize(c->stream)) {
         ibem_cnn_destroy(c);
         return IBEM_ERR_CUDA;
     }
@@ -755,6 +1054,8 @@ ibem_status ibem_cnn_destroy(ibem_cnn* c) {
     cudaFree(c->d_items);
     cudaFree(c->d_opvec);
     cudaFree(c->d_opimg);
+    cudaFree(c->d_wtc);
+    cudaFree(c->d_status);
     cudaFree(c->d_red);
     delete c;
     return IBEM_OK;
@@ -781,7 +1082,7 @@ ibem_status ibem_cnn_forward(ibem_cnn* c, const float* in_dev, int B, int H, int
     if (!c || !in_dev || !out_dev || !dims_ok(B, H, W)) return IBEM_ERR_ARG;
     if (precision != IBEM_FP32 && precision != IBEM_BF16) return IBEM_ERR_ARG;
     const int bf = precision == IBEM_BF16;
-    cudaError_t e = bf ? forward<__nv_bfloat16>(c, in_dev, B, H, W, 1) : forward<float>(c, in_dev, B, H, W, 0);
+    cudaError_t e = bf ? forward_infer(c, in_dev, B, H, W, c->d_status, 1LL << 26) : forward<float>(c, in_dev, B, H, W, 0);
     if (e) return e == cudaErrorMemoryAllocation ? IBEM_ERR_OOM : IBEM_ERR_CUDA;
     const int64_t n = (int64_t)B * 2 * H * W;
     if (bf)
@@ -970,6 +1271,14 @@ ibem_status ibem_cnn_train_operator(ibem_handle* h, ibem_cnn* c, const double* r
         return finish(IBEM_ERR_CUDA);
     if (last_epoch_loss) *last_epoch_loss = sum / n;
     return finish(cudaGetLastError() ? IBEM_ERR_CUDA : IBEM_OK);
+}
+
+ibem_status ibem_cnn_device_status(ibem_cnn* c, int* status) {
+    if (!c || !status) return IBEM_ERR_ARG;
+    if (cudaMemcpyAsync(status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream) ||
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream) || cudaStreamSynchronize(c->stream))
+        return IBEM_ERR_CUDA;
+    return IBEM_OK;
 }
 
 ibem_status ibem_cnn_launches(ibem_cnn* c, int64_t* launches) {

@@ -34,7 +34,7 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
             "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
-            "ibem_cnn_train_operator")
+            "ibem_cnn_train_operator", "ibem_cnn_device_status")
 
 
 class IbemError(RuntimeError):
@@ -113,6 +113,7 @@ def _load():
         "ibem_cnn_train": (I32, [P, P, P, I32, I32, I32, I32, I32, ctypes.c_float, ctypes.c_ulonglong, I32,
                                  ctypes.POINTER(ctypes.c_double)]),
         "ibem_cnn_launches": (I32, [P, ctypes.POINTER(I64)]),
+        "ibem_cnn_device_status": (I32, [P, ctypes.POINTER(I32)]),
         "ibem_set_learned_preconditioner": (I32, [P, P]),
         "ibem_learned_apply": (I32, [P, P, P]),
         "ibem_solver_pairs": (I32, [P, P, I32, ctypes.c_double, I32, I32, I32, P, P, ctypes.POINTER(I32),
@@ -455,3 +456,9 @@ def ibem_cnn_train_operator(h, c, r, n, batch, epochs, lr, seed=0, augment=IBEM_
     _check(_lib.ibem_cnn_train_operator(h, c, _dptr(r), n, batch, epochs, lr, seed, augment, op_precision,
                                         ctypes.byref(loss)), h)
     return loss.value
+
+
+def ibem_cnn_device_status(c):
+    st = ctypes.c_int()
+    _check(_lib.ibem_cnn_device_status(c, ctypes.byref(st)))
+    return st.value
