@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
+    ap.add_argument("--cnn-forward-only", action="store_true", help="time only the network's forward pass")
     ap.add_argument("--learn-train-m", type=int, default=5, help="level of the training solves")
     ap.add_argument("--learn-m", type=int, default=6, help="level of the compared solves")
     ap.add_argument("--learn-nrhs", type=int, default=2, help="plane waves of the compared solves")
@@ -265,6 +266,50 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
                                "for it"}}
 
 
+def cnn_forward_timing(ibem, stream, c):
+    """The network's BF16 forward pass (tensor cores) on 96 images of 130 x 130
+    (level 7, 16 right-hand sides x 6 patches), CUDA events on the bench stream,
+    20 repetitions after 3 warm-up, against the measured HBM bandwidth (the
+    convolutions are memory-bound) and the measured BF16 tensor peak."""
+    import torch
+    B, H = 96, 130
+    x = torch.randn((B, 2, H, H), dtype=torch.float32, device="cuda")
+    out = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    ev0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / reps
+    C = 32
+    flops = 2.0 * 9 * (2 * C + C * C + C * C + C * 2) * B * H * H
+    # algorithmic bytes per pixel: FP32 input (8), packed input written and read
+    # (16 + 16), three 32-channel BF16 activations written and read (3 x 128),
+    # BF16 output (4)
+    nbytes = (8 + 16 + 16 + 3 * 128 + 4) * B * H * H
+    hbm, _, src = _peaks()
+    bf16_peak = 1912.6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = json.load(f).get("bf16_tflops", bf16_peak)
+    except OSError:
+        pass
+    return {"images": B, "size": H, "ms": fwd_ms, "kernels": "conv_tc_kernel (tcgen05) x 4",
+            "bound": "hbm", "algorithmic_bytes": nbytes,
+            "achieved_gbs": nbytes / (fwd_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+            "frac": nbytes / (fwd_ms * 1e-3) / 1e9 / hbm,
+            "tflops": flops / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16_peak,
+            "tensor_frac": flops / (fwd_ms * 1e-3) / 1e12 / bf16_peak,
+            "peak_note": "MEASURED_PEAKS.json (%s)" % src,
+            "device_status": ibem.ibem_cnn_device_status(c)}
+
+
 def learned_preconditioner(ibem, stream, args):
     """Learned right preconditioner, Helmholtz sound-soft scattering on the
     6-patch sphere, p = 2, q = 6, k drawn uniformly from [8, 16] (seeded):
@@ -327,35 +372,7 @@ def learned_preconditioner(ibem, stream, args):
                      "rel_residual_fp64": si.rel_residual, "seconds": si.seconds}
     ibem.ibem_set_learned_preconditioner(h, None)
     ibem.ibem_destroy(h)
-    # forward pass of the network on 96 images of 130 x 130 (level 7, 16 right-hand sides)
-    B, H = 96, 130
-    x = torch.randn((B, 2, H, H), dtype=torch.float32, device="cuda")
-    out = torch.empty_like(x)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    ev0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(reps):
-            ibem.ibem_cnn_forward(c, x, out, ibem.IBEM_BF16)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = ev0.elapsed_time(ev1) / reps
-    C = 32
-    flops = 2.0 * 9 * (2 * C + C * C + C * C + C * 2) * B * H * H
-    # algorithmic bytes per pixel: FP32 input (8), packed input written and read
-    # (16 + 16), three 32-channel BF16 activations written and read (3 x 128),
-    # BF16 output (4)
-    nbytes = (8 + 16 + 16 + 3 * 128 + 4) * B * H * H
-    hbm, _, src = _peaks()
-    bf16_peak = 1912.6
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16_peak = json.load(f).get("bf16_tflops", bf16_peak)
-    except OSError:
-        pass
+    fwd = cnn_forward_timing(ibem, stream, c)
     ibem.ibem_cnn_destroy(c)
     it_b, it_l = res["block_jacobi"]["iterations"], res["learned"]["iterations"]
     return {"workload": "helmholtz-sphere-p2-q6-k[8,16]: train level %d, solve level %d, %d plane waves"
@@ -363,13 +380,7 @@ def learned_preconditioner(ibem, stream, args):
             "k_solve": k, "ndof": info.ndof, "train": train, "train_s": train_s, "solve": res,
             "iterations_learned_over_block_jacobi": it_l / max(1, it_b),
             "seconds_learned_over_block_jacobi": res["learned"]["seconds"] / max(1e-9, res["block_jacobi"]["seconds"]),
-            "cnn_forward": {"images": B, "size": H, "ms": fwd_ms, "kernels": "conv_tc_kernel (tcgen05) x 4",
-                            "bound": "hbm", "algorithmic_bytes": nbytes,
-                            "achieved_gbs": nbytes / (fwd_ms * 1e-3) / 1e9, "peak_gbs": hbm,
-                            "frac": nbytes / (fwd_ms * 1e-3) / 1e9 / hbm,
-                            "tflops": flops / (fwd_ms * 1e-3) / 1e12, "bf16_peak_tflops": bf16_peak,
-                            "tensor_frac": flops / (fwd_ms * 1e-3) / 1e12 / bf16_peak,
-                            "peak_note": "MEASURED_PEAKS.json (%s)" % src}}
+            "cnn_forward": fwd}
 
 
 # ---------------------------------------------------------------- our arm
@@ -395,6 +406,13 @@ def ours(args, rank, world, local_rank):
         out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
         if rank == 0:
             print(json.dumps({"helmholtz_64rhs": out}), flush=True)
+        return
+    if args.cnn_forward_only:
+        c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
+        out = cnn_forward_timing(ibem, stream, c)
+        ibem.ibem_cnn_destroy(c)
+        if rank == 0:
+            print(json.dumps({"cnn_forward": out}), flush=True)
         return
     if args.learned_only:
         out = learned_preconditioner(ibem, stream, args)
