@@ -424,6 +424,7 @@ __global__ void column_gather_kernel(int R, int64_t C, int q2, const int64_t* __
     int b = (int)(rem % q2);
     if (tptr[tau + 1] == tptr[tau]) return;
     float hi = 0.0f, lo = 0.0f;
+#pragma unroll 4
     for (int64_t k = tptr[tau]; k < tptr[tau + 1]; ++k) {
         float2 v = colpart[(r * nblk_total + tblk[k]) * q2 + b];
         df_add(hi, lo, v.x, v.y);
