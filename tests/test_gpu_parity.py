@@ -49,6 +49,24 @@ def test_fmm_matvec_p2_m2(coupling):
     lib().ibem_destroy(h)
 
 
+_NEAR_CACHE = {}
+
+
+@pytest.mark.parametrize("q", [3, 4, 5, 8])
+def test_fmm_matvec_double_float_other_q(q):
+    """The double-float coupling for odd q (bounds-checked lanes, fixed ring
+    depth) and for even q other than 6 (specialised lanes, ring depth chosen by
+    the autotuner at assembly) against the oracle FMM at equal q."""
+    from oracle import fmm, galerkin, geometry
+    disc = galerkin.Discretisation(geometry.unit_sphere(), 2, 2, galerkin.LaplaceKernel())
+    op = fmm.FMMOperator(disc, q, 1.6, near_block_cache=_NEAR_CACHE)
+    h = handle(2, 2, q=q, fp64_coupling=0)
+    x = _x(op.mesh.n_dofs, 2, 30 + q)
+    y0 = np.stack([op.matvec(xi) for xi in x])
+    assert rel_err(gpu_matvec(h, x), y0) < TOL64
+    lib().ibem_destroy(h)
+
+
 def test_native_and_double_float_coupling_agree_config2():
     hd = handle(3, 5, q=6, fp64_coupling=0)
     x = _x(7350, 1, 19)
