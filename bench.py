@@ -243,6 +243,27 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
     torch.cuda.synchronize()
     fp64_s = time.perf_counter() - t1
     err = float((y[0] - y64[0]).abs().max() / y64[0].abs().max())
+    # potential of the 64 densities (the right-hand sides stand in for them) at 200
+    # points on the sphere of radius 3 (seeded): one e^{ikr}/r per point, source
+    # and chunk of 16 densities, FP64
+    npt = 200
+    dp = rng.normal(size=(npt, 3))
+    pts = torch.from_numpy(3.0 * dp / np.linalg.norm(dp, axis=1)[:, None]).cuda()
+    u = torch.empty((R, npt, 2), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        ibem.ibem_potential(h, b, R, pts, u)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ibem.ibem_potential(h, b, R, pts, u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pot_ms = e0.elapsed_time(e1) / 2
+    nsrc = info.n_elements * 64
+    potential = {"points": npt, "densities": R, "sources": nsrc, "ms": pot_ms,
+                 "pair_density_evals_per_s": npt * nsrc * R / (pot_ms * 1e-3),
+                 "kernel_evals_per_s": npt * nsrc * ((R + 15) // 16) / (pot_ms * 1e-3)}
     q2 = q * q
     flops = 2.0 * 128 * 128 * 64 * info.n_far                      # real-form GEMM per far block
     peak = 1912.6
@@ -258,7 +279,7 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
             "n_near": info.n_near, "n_far": info.n_far, "nrhs": R, "setup_s": setup_s,
             "value": world * N * R / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "coupling_ms": coup_ms,
             "phase_ms": phases,
-            "rel_err_vs_fp64_rhs0": err, "fp64_one_rhs_s": fp64_s,
+            "rel_err_vs_fp64_rhs0": err, "fp64_one_rhs_s": fp64_s, "potential": potential,
             "tensor": {"kernel": "mr_coupling_tc_kernel", "achieved_tflops": flops / (coup_ms * 1e-3) / 1e12,
                        "peak_tflops": peak, "frac": flops / (coup_ms * 1e-3) / 1e12 / peak,
                        "sfu_frac": sfu / (coup_ms * 1e-3) / sfu_peak,

@@ -632,10 +632,14 @@ __global__ void helm_join_vec_kernel(int R, int64_t n, const double* __restrict_
 // ---- potential (complex) -------------------------------------------------------------
 // u(x) = sum over Gauss points of W mu exp(i kappa |x - y|) / (4 pi |x - y|);
 // srcs[g] = (x, y, z, W mu_re / 4pi), mu_im in srci[g].
-__global__ void helm_density_kernel(int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
-                                    const double* __restrict__ phi, const double* __restrict__ wre,
-                                    const double* __restrict__ wim, double4_32a* __restrict__ srcs,
-                                    double* __restrict__ srci) {
+// Densities of up to HP_RC right-hand sides at once: mu[s][j] = w_s k_s (mu_re, mu_im) / (4 pi)
+// for slot j; positions are written once (pos[s] = (x, y, z, 0)).
+constexpr int HP_RC = 16;
+
+__global__ void helm_density_slot_kernel(int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
+                                         const double* __restrict__ phi, const double* __restrict__ wre,
+                                         const double* __restrict__ wim, int j, double2* __restrict__ mu,
+                                         double4_32a* __restrict__ pos) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= E * QQ) return;
     int64_t e = idx / QQ;
@@ -646,30 +650,49 @@ __global__ void helm_density_kernel(int64_t E, int QQ, int nb, const double* __r
         mi += phi[q * nb + i] * wim[e * nb + i];
     }
     const double* X = qgeo + 4 * idx;
-    srcs[idx] = make_double4_32a(X[0], X[1], X[2], X[3] * mr / (4.0 * IBEM_PI));
-    srci[idx] = X[3] * mi / (4.0 * IBEM_PI);
+    const double s = X[3] / (4.0 * IBEM_PI);
+    mu[idx * HP_RC + j] = make_double2(s * mr, s * mi);
+    if (pos) pos[idx] = make_double4_32a(X[0], X[1], X[2], 0.0);
 }
 
-__global__ void helm_potential_kernel(int64_t npts, const double* __restrict__ pts, int64_t nsrc,
-                                      const double4_32a* __restrict__ srcs, const double* __restrict__ srci,
-                                      int64_t chunk, double kappa, double* __restrict__ u) {
+// u_j(x) += sum_s e^{i kappa r} / r mu[s][j] for the nc densities of a chunk: the
+// complex exponential is evaluated once per (point, source) and applied to all
+// of them.  Grid: (points, source splits); atomics combine the splits.
+__global__ void helm_potential_multi_kernel(int64_t npts, const double* __restrict__ pts, int64_t nsrc,
+                                            const double4_32a* __restrict__ pos, const double2* __restrict__ mu,
+                                            int nc, int64_t chunk, double kappa, double* __restrict__ u) {
     int64_t ip = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (ip >= npts) return;
     double x0 = pts[3 * ip], x1 = pts[3 * ip + 1], x2 = pts[3 * ip + 2];
     int64_t s0 = blockIdx.y * chunk, s1 = s0 + chunk < nsrc ? s0 + chunk : nsrc;
-    double ar = 0.0, ai = 0.0;
+    double ar[HP_RC], ai[HP_RC];
+#pragma unroll
+    for (int j = 0; j < HP_RC; ++j) ar[j] = ai[j] = 0.0;
     for (int64_t s = s0; s < s1; ++s) {
-        double4_32a y = srcs[s];
-        double d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
-        double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        const double4_32a y = pos[s];
+        const double d0 = x0 - y.x, d1 = x1 - y.y, d2 = x2 - y.z;
+        const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
         double sn, cs;
         sincos(kappa * r, &sn, &cs);
-        double mi = srci[s];
-        ar += (y.w * cs - mi * sn) / r;
-        ai += (y.w * sn + mi * cs) / r;
+        const double ir = 1.0 / r;
+        const double gr = cs * ir, gi = sn * ir;
+        const double2* m = mu + s * HP_RC;
+#pragma unroll
+        for (int j = 0; j < HP_RC; ++j) {
+            if (j < nc) {
+                const double2 v = m[j];
+                ar[j] += gr * v.x - gi * v.y;
+                ai[j] += gr * v.y + gi * v.x;
+            }
+        }
     }
-    atomicAdd(u + 2 * ip, ar);
-    atomicAdd(u + 2 * ip + 1, ai);
+#pragma unroll
+    for (int j = 0; j < HP_RC; ++j) {
+        if (j < nc) {
+            atomicAdd(u + (size_t)2 * j * npts + 2 * ip, ar[j]);
+            atomicAdd(u + (size_t)2 * j * npts + 2 * ip + 1, ai[j]);
+        }
+    }
 }
 
 // ---- host launchers ----------------------------------------------------------------------
@@ -850,28 +873,36 @@ cudaError_t helm_launch_potential(ibem_handle* h, const double* w, int nrhs, con
     const int T = 256;
     int QQ = P.Q * P.Q;
     int64_t nsrc = P.E * QQ;
-    double4_32a* srcs = nullptr;
-    double* srci = nullptr;
-    if ((e = cudaMallocAsync(&srcs, (size_t)nsrc * sizeof(double4_32a), h->stream))) return e;
-    if ((e = cudaMallocAsync(&srci, (size_t)nsrc * sizeof(double), h->stream))) return e;
+    double4_32a* pos = nullptr;
+    double2* mu = nullptr;
+    if ((e = cudaMallocAsync(&pos, (size_t)nsrc * sizeof(double4_32a), h->stream))) return e;
+    if ((e = cudaMallocAsync(&mu, (size_t)nsrc * HP_RC * sizeof(double2), h->stream))) {
+        cudaFreeAsync(pos, h->stream);
+        return e;
+    }
     if ((e = cudaMemsetAsync(u, 0, (size_t)2 * nrhs * npts * sizeof(double), h->stream))) return e;
-    int64_t nsplit = (608 * 128) / npts;
+    int64_t nsplit = (608 * 128) / (npts > 0 ? npts : 1);
     if (nsplit < 1) nsplit = 1;
     if (nsplit > 65535) nsplit = 65535;
     int64_t chunk = (nsrc + nsplit - 1) / nsplit;
     nsplit = (nsrc + chunk - 1) / chunk;
     helm_split_vec_kernel<<<nblk((int64_t)nrhs * P.N, T), T, 0, h->stream>>>(nrhs, P.N, w, wsplit);
-    for (int r = 0; r < nrhs; ++r) {
-        lift_kernel<<<nblk(2 * P.E * P.nb, T), T, 0, h->stream>>>(2, P.E, P.p, P.ne1, h->d_ext,
-                                                                  wsplit + (size_t)2 * r * P.N, P.N, h->d_xs);
-        helm_density_kernel<<<nblk(nsrc, T), T, 0, h->stream>>>(P.E, QQ, P.nb, h->d_qgeo, h->d_phi, h->d_xs,
-                                                                h->d_xs + P.Nstar, srcs, srci);
-        helm_potential_kernel<<<dim3(nblk(npts, 128), (unsigned)nsplit), 128, 0, h->stream>>>(
-            npts, pts, nsrc, srcs, srci, chunk, P.prm.kappa, u + (size_t)2 * r * npts);
+    for (int r0 = 0; r0 < nrhs && npts > 0; r0 += HP_RC) {
+        const int nc = nrhs - r0 < HP_RC ? nrhs - r0 : HP_RC;
+        for (int j = 0; j < nc; ++j) {
+            lift_kernel<<<nblk(2 * P.E * P.nb, T), T, 0, h->stream>>>(2, P.E, P.p, P.ne1, h->d_ext,
+                                                                      wsplit + (size_t)2 * (r0 + j) * P.N, P.N,
+                                                                      h->d_xs);
+            helm_density_slot_kernel<<<nblk(nsrc, T), T, 0, h->stream>>>(
+                P.E, QQ, P.nb, h->d_qgeo, h->d_phi, h->d_xs, h->d_xs + P.Nstar, j, mu,
+                (r0 == 0 && j == 0) ? pos : nullptr);
+        }
+        helm_potential_multi_kernel<<<dim3(nblk(npts, 128), (unsigned)nsplit), 128, 0, h->stream>>>(
+            npts, pts, nsrc, pos, mu, nc, chunk, P.prm.kappa, u + (size_t)2 * r0 * npts);
     }
     cudaError_t le = cudaGetLastError();
-    cudaFreeAsync(srcs, h->stream);
-    cudaFreeAsync(srci, h->stream);
+    cudaFreeAsync(pos, h->stream);
+    cudaFreeAsync(mu, h->stream);
     return le;
 }
 

@@ -161,3 +161,26 @@ def test_gmres_block_jacobi():
     assert sb.rel_residual <= 1e-8 and sm.rel_residual <= 1e-8
     assert sb.iterations <= sj.iterations
     ibem.ibem_destroy(h)
+
+
+def test_potential_many_densities(helm_p1m1):
+    """Potentials of 20 densities at once (one chunk of 16 sharing each kernel
+    evaluation, then a ragged chunk of 4) against the oracle, column by column."""
+    import torch
+    from oracle import solve
+    ibem = lib()
+    disc, _ = helm_p1m1
+    h = _handle(1, 1, 0, 2.0)
+    N = disc.mesh.n_dofs
+    w = _x(N, 20, 41)
+    rng = np.random.default_rng(42)
+    d = rng.normal(size=(25, 3))
+    pts = 2.5 * d / np.linalg.norm(d, axis=1)[:, None]
+    wd = torch.from_numpy(np.ascontiguousarray(np.stack([w.real, w.imag], axis=-1))).cuda()
+    u = torch.empty((20, 25, 2), dtype=torch.float64, device="cuda")
+    ibem.ibem_potential(h, wd, 20, torch.from_numpy(pts).cuda(), u)
+    uc = u.cpu().numpy()
+    uc = uc[..., 0] + 1j * uc[..., 1]
+    u0 = solve.potential(disc, w.T, pts).T
+    assert rel_err(uc, u0) < TOL64
+    ibem.ibem_destroy(h)
