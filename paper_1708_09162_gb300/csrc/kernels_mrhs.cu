@@ -229,13 +229,17 @@ __device__ inline bool tc_wait(uint64_t* bar, unsigned parity, long long limit) 
     return false;
 }
 
-template <bool CPLX>
+// Q > 0: compiled for q = Q (index arithmetic of the K generation by shifts and
+// constants); Q = 0: q and KAP at run time.
+template <bool CPLX, int Q>
 __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
-    const float4* __restrict__ geo, int q, int R, int RP, int KAP, int tcols, float kappa,
+    const float4* __restrict__ geo, int q_rt, int R, int RP, int KAP_rt, int tcols, float kappa,
     const __nv_bfloat16* __restrict__ xb, typename MrType<CPLX>::T* __restrict__ yh, long long wait_limit,
     int* __restrict__ status) {
     constexpr int MAP = 128;
+    const int q = Q > 0 ? Q : q_rt;
+    const int KAP = Q > 0 ? (((CPLX ? 2 * Q * Q : Q * Q) + 15) & ~15) : KAP_rt;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bfull = reinterpret_cast<uint64_t*>(smem);        // [2]
     uint64_t* mdone = bfull + 2;                                 // [2]
@@ -577,12 +581,12 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
             while (tcols < RP) tcols <<= 1;
             const size_t sm = 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024) + 2 * (size_t)128 * KAP * 2 +
                               2 * (size_t)RP * KAP * 2;
-            if ((e = cudaFuncSetAttribute(mr_coupling_tc_kernel<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm)))
-                return e;
-            mr_coupling_tc_kernel<CPLX><<<nrows, 512, sm, st>>>(
-                h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const float4*>(h->d_igeo32), P.q, R, RP,
-                KAP, tcols, (float)P.prm.kappa, xb, yh, h->wait_limit, h->d_status);
+            auto kern = P.q == 8 ? mr_coupling_tc_kernel<CPLX, 8>
+                                 : (P.q == 6 ? mr_coupling_tc_kernel<CPLX, 6> : mr_coupling_tc_kernel<CPLX, 0>);
+            if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
+            kern<<<nrows, 512, sm, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src,
+                                         reinterpret_cast<const float4*>(h->d_igeo32), P.q, R, RP, KAP, tcols,
+                                         (float)P.prm.kappa, xb, yh, h->wait_limit, h->d_status);
             h->launches += 2;
         }
         PhaseTimer pt(h, 3);
