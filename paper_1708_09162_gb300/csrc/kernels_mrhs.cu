@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     const size_t abytes = (size_t)MAP * KAP * 2, bbytes = (size_t)RP * KAP * 2;
     unsigned char* tiles = smem + 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024);
     // buffer b: A tile at tiles + b * abytes, B tile at tiles + 2 * abytes + b * bbytes
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31, nwarps = blockDim.x >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;   // 512 threads = 16 warps
     const int sigma = rows[blockIdx.x];
     const int64_t b0 = fptr[sigma];
     const int n = (int)(fptr[sigma + 1] - b0);
@@ -307,7 +307,10 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
         // quadrant offsets of the real form when q2 is a multiple of 8
         const int offR = (q2 >> 3) * 64, offD = (q2 >> 3) * K8 * 64;
         const bool aligned8 = (q2 & 7) == 0;
-        for (int cm = warp; cm < q8 * q8; cm += nwarps) {
+        // 512 threads: 16 warps; with q fixed the trip count is known and the
+        // loop unrolls, so a warp keeps several core matrices' SFU work in flight
+#pragma unroll
+        for (int cm = warp; cm < q8 * q8; cm += 16) {
             const int ca = cm / q8, cb = cm - ca * q8;
             const int a = 8 * ca + (lane >> 2), b = 8 * cb + 2 * (lane & 3);
             if (a >= q2 || b >= q2) continue;   // q2 is even, so b + 1 < q2 as well
