@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* bfull = reinterpret_cast<uint64_t*>(smem);        // [2]
     uint64_t* mdone = bfull + 2;                                 // [2]
+    uint64_t* afull = bfull + 4;                                 // [2]: 16 warp arrivals per A tile
+    int* issued_sh = reinterpret_cast<int*>(smem + 76);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 64);
     int* flag = reinterpret_cast<int*>(smem + 72);
     float4* Xs = reinterpret_cast<float4*>(smem + 128);
@@ -259,8 +261,10 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
         for (int i = 0; i < 2; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&bfull[i])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&mdone[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 16;" ::"r"(tsm(&afull[i])) : "memory");
         }
         *flag = 0;
+        *issued_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -281,13 +285,22 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(MAP >> 4) << 24);
-    int issued = 0;          // blocks whose MMAs were committed
+    // No CTA barrier inside the loop: every thread waits by itself until the MMAs
+    // of block i - 2 have released buffer i & 1, each warp announces its part of
+    // the A tile on afull, and thread 0 issues the MMAs once afull and the moments'
+    // copy (bfull) are complete.  A failed (bounded) wait raises the shared flag,
+    // which every thread checks at the top of each block.
+    volatile int* vflag = flag;
+    int issued = 0;          // blocks whose MMAs were committed (thread 0)
     bool failed = false;
     for (int i = 0; i < n; ++i) {
         const int buf = i & 1;
-        bool ok = true;
-        if (i >= 2) ok = tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
+        if (*vflag) { failed = true; break; }
+        if (i >= 2 && !tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit)) {
+            atomicOr(flag, 1);
+            failed = true;
+            break;
+        }
         const int tau = fsrc[b0 + i];
         if (t == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tsm(&bfull[buf])),
@@ -356,18 +369,24 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
                 }
             }
         }
+        // this warp's part of the A tile is written: make it visible to the tensor
+        // core (async proxy) and announce it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        bool bok = true;
-        if (t == 0) bok = tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), wait_limit);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        if (__syncthreads_or(!bok)) {
-            failed = true;
-            // the copy for this block may still land: wait for it before leaving
-            if (t == 0) tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), 1LL << 24);
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tsm(&afull[buf])) : "memory");
         if (t == 0) {
+            const bool aok = tc_wait(&afull[buf], (unsigned)((i >> 1) & 1), wait_limit);
+            const bool bok = aok && tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), wait_limit);
+            if (!aok || !bok) {
+                atomicOr(flag, 1);
+                // the copy for this block may still land: wait for it before leaving
+                tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), 1LL << 24);
+                failed = true;
+            }
+        }
+        if (failed) break;
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int kk = 0; kk < KAP / 16; ++kk) {
                 const uint64_t ad = umma_desc(tsm(A) + kk * 256, 128, K8 * 128);
                 const uint64_t bd = umma_desc(tsm(tiles + 2 * abytes + buf * bbytes) + kk * 256, 128, K8 * 128);
@@ -384,6 +403,9 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
         }
         issued = i + 1;
     }
+    if (t == 0) *issued_sh = issued;
+    if (__syncthreads_or(failed)) failed = true;
+    issued = *issued_sh;
     // wait for the last committed MMAs (bounded), then read the accumulator
     bool ok = true;
     if (issued > 0) {
