@@ -505,6 +505,68 @@ __global__ void mr_near_kernel(int R, int nb, const int64_t* __restrict__ nptr, 
     }
 }
 
+// Same product with one thread per right-hand side holding all NB rows of its
+// element: the element's blocks pass through shared memory in chunks of KC
+// (broadcast reads, 4 FMA per complex entry and load), each source value is
+// loaded once per block (coalesced over the right-hand sides).  The sums run in
+// the same order (blocks, then columns) as in mr_near_kernel.
+template <bool CPLX, int NB>
+__global__ void __launch_bounds__(256) mr_near_rows_kernel(int R, const int64_t* __restrict__ nptr,
+                                                           const int32_t* __restrict__ nsrc,
+                                                           const float* __restrict__ blocks,
+                                                           const typename MrType<CPLX>::T* __restrict__ xs,
+                                                           typename MrType<CPLX>::T* __restrict__ ys) {
+    typedef typename MrType<CPLX>::T T;
+    constexpr int CW = CPLX ? 2 : 1;
+    constexpr int BF = NB * NB * CW;                             // floats per block
+    constexpr int KC = (NB == 9 ? 32 : 8) * (CPLX ? 1 : 2);      // blocks per shared-memory chunk
+    __shared__ float sb[KC * BF];
+    __shared__ int ss[KC];
+    const int64_t e = blockIdx.x;
+    const int r = threadIdx.x;
+    const bool act = r < R;
+    float ar[NB], ai[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) ar[i] = ai[i] = 0.0f;
+    const int64_t k0 = nptr[e], k1 = nptr[e + 1];
+    for (int64_t kb = k0; kb < k1; kb += KC) {
+        const int kc = (int)(k1 - kb < KC ? k1 - kb : KC);
+        for (int i = threadIdx.x; i < kc * BF; i += blockDim.x) sb[i] = blocks[kb * BF + i];
+        for (int i = threadIdx.x; i < kc; i += blockDim.x) ss[i] = nsrc[kb + i];
+        __syncthreads();
+        if (act) {
+            for (int kk = 0; kk < kc; ++kk) {
+                const int64_t s = ss[kk];
+                T xv[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) xv[j] = xs[(s * NB + j) * R + r];
+                const float* B = sb + kk * BF;
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) {
+                        if constexpr (CPLX) {
+                            const float br = B[2 * (i * NB + j)], bi = B[2 * (i * NB + j) + 1];
+                            ar[i] = fmaf(br, xv[j].x, fmaf(-bi, xv[j].y, ar[i]));
+                            ai[i] = fmaf(br, xv[j].y, fmaf(bi, xv[j].x, ai[i]));
+                        } else {
+                            ar[i] = fmaf(B[i * NB + j], xv[j], ar[i]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (!act) return;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        T* out = ys + (e * NB + i) * R + r;
+        if constexpr (CPLX) *out = make_float2(out->x + ar[i], out->y + ai[i]);
+        else *out += ar[i];
+    }
+}
+
 // y [R][N] (doubles, interleaved complex) = T y*
 template <bool CPLX>
 __global__ void mr_restrict_kernel(int R, int64_t N, int p, int ne1, const double* __restrict__ ext,
@@ -628,8 +690,16 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
     int nthreads = P.nb * R < 512 ? ((P.nb * R + 31) / 32) * 32 : 512;
     {
         PhaseTimer pt(h, 4);
-        mr_near_kernel<CPLX><<<(unsigned)P.E, nthreads, 0, st>>>(R, P.nb, h->d_near_ptr, h->d_near_src, h->d_near32, xs,
-                                                                 ys);
+        const int tr = ((R + 31) / 32) * 32;
+        if (P.nb == 9)
+            mr_near_rows_kernel<CPLX, 9><<<(unsigned)P.E, tr, 0, st>>>(R, h->d_near_ptr, h->d_near_src, h->d_near32,
+                                                                       xs, ys);
+        else if (P.nb == 16)
+            mr_near_rows_kernel<CPLX, 16><<<(unsigned)P.E, tr, 0, st>>>(R, h->d_near_ptr, h->d_near_src, h->d_near32,
+                                                                        xs, ys);
+        else
+            mr_near_kernel<CPLX><<<(unsigned)P.E, nthreads, 0, st>>>(R, P.nb, h->d_near_ptr, h->d_near_src,
+                                                                     h->d_near32, xs, ys);
     }
     {
         PhaseTimer pt(h, 5);

@@ -57,12 +57,15 @@ def test_helmholtz_tensor_core_coupling_q8():
     lib().ibem_destroy(h)
 
 
-def test_multi_rhs_near_only_matches_fp64():
+@pytest.mark.parametrize("p,kernel,R", [(1, 0, 16), (2, 0, 40), (3, 0, 16), (2, 1, 24), (3, 1, 16)])
+def test_multi_rhs_near_only_matches_fp64(p, kernel, R):
     # no far field (dense mode): the many-RHS path is the FP32 near product alone
-    h = _handle(1, 2, 0)
+    # (generic kernel for p = 1; one thread per right-hand side for p = 2, 3)
+    h = _handle(p, 2 if p < 3 else 1, 0, kernel=kernel, kappa=3.0 if kernel else 0.0)
     N = lib().ibem_get_info(h).ndof
-    x = np.random.default_rng(5).normal(size=(16, N))
-    assert rel_err(_apply(h, x, 1, False), _per_rhs_fp64(h, x, False)) < 1e-5
+    rng = np.random.default_rng(5 + p)
+    x = rng.normal(size=(R, N)) + (1j * rng.normal(size=(R, N)) if kernel else 0.0)
+    assert rel_err(_apply(h, x, 1, bool(kernel)), _per_rhs_fp64(h, x, bool(kernel))) < 1e-5
     lib().ibem_destroy(h)
 
 
