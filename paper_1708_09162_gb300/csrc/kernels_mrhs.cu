@@ -232,7 +232,7 @@ __device__ inline bool tc_wait(uint64_t* bar, unsigned parity, long long limit) 
 // Q > 0: compiled for q = Q (index arithmetic of the K generation by shifts and
 // constants); Q = 0: q and KAP at run time.
 template <bool CPLX, int Q>
-__global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
+__global__ void __launch_bounds__(544) mr_coupling_tc_kernel(
     const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
     const float4* __restrict__ geo, int q_rt, int R, int RP, int KAP_rt, int tcols, float kappa,
     const __nv_bfloat16* __restrict__ xb, typename MrType<CPLX>::T* __restrict__ yh, long long wait_limit,
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     const size_t abytes = (size_t)MAP * KAP * 2, bbytes = (size_t)RP * KAP * 2;
     unsigned char* tiles = smem + 1024 * ((128 + (size_t)q2 * 16 + 1023) / 1024);
     // buffer b: A tile at tiles + b * abytes, B tile at tiles + 2 * abytes + b * bbytes
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;   // 512 threads = 16 warps
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;   // 544 threads: 16 generating warps + 1
     const int sigma = rows[blockIdx.x];
     const int64_t b0 = fptr[sigma];
     const int n = (int)(fptr[sigma + 1] - b0);
@@ -285,24 +285,99 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(RP >> 3) << 17) | ((uint32_t)(MAP >> 4) << 24);
-    // No CTA barrier inside the loop: every thread waits by itself until the MMAs
-    // of block i - 2 have released buffer i & 1, each warp announces its part of
-    // the A tile on afull, and thread 0 issues the MMAs once afull and the moments'
-    // copy (bfull) are complete.  A failed (bounded) wait raises the shared flag,
-    // which every thread checks at the top of each block.
+    // Warps 0..15 generate the A tiles, warp 16 (lane 0) issues the moments' copy
+    // and the MMAs.  No CTA barrier inside the loops: a generating thread waits by
+    // itself until the MMAs of block i - 2 have released buffer i & 1, each warp
+    // announces its part of the A tile on afull, and the issuing lane waits for
+    // afull and for the copy (bfull).  A failed (bounded) wait raises the shared
+    // flag, which every loop checks at the top of each block.
     volatile int* vflag = flag;
-    int issued = 0;          // blocks whose MMAs were committed (thread 0)
+    int issued = 0;          // blocks whose MMAs were committed (issuing lane)
     bool failed = false;
-    for (int i = 0; i < n; ++i) {
-        const int buf = i & 1;
-        if (*vflag) { failed = true; break; }
-        if (i >= 2 && !tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit)) {
-            atomicOr(flag, 1);
-            failed = true;
-            break;
+    if (warp < 16) {
+        for (int i = 0; i < n; ++i) {
+            const int buf = i & 1;
+            if (*vflag) { failed = true; break; }
+            if (i >= 2 && !tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit)) {
+                atomicOr(flag, 1);
+                failed = true;
+                break;
+            }
+            const int tau = fsrc[b0 + i];
+            // A tile: the coupling block in FP32, stored as BF16.  A warp fills one
+            // 8 x 8 core matrix per step (lane -> row lane / 4, columns 2 (lane % 4)
+            // and +1) with packed 4-byte stores: 128 contiguous bytes, no bank conflicts.
+            __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tiles + buf * abytes);
+            const float4* Y = geo + (int64_t)tau * q2;
+            const int q8 = (q2 + 7) >> 3;
+            // quadrant offsets of the real form when q2 is a multiple of 8
+            const int offR = (q2 >> 3) * 64, offD = (q2 >> 3) * K8 * 64;
+            const bool aligned8 = (q2 & 7) == 0;
+            // 512 threads: 16 warps; with q fixed the trip count is known and the
+            // loop unrolls, so a warp keeps several core matrices' SFU work in flight
+    #pragma unroll
+            for (int cm = warp; cm < q8 * q8; cm += 16) {
+                const int ca = cm / q8, cb = cm - ca * q8;
+                const int a = 8 * ca + (lane >> 2), b = 8 * cb + 2 * (lane & 3);
+                if (a >= q2 || b >= q2) continue;   // q2 is even, so b + 1 < q2 as well
+                const float4 X = Xs[a];
+                float wr[2], wi[2];
+    #pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const float4 Yb = Y[b + u];
+                    const float d0 = X.x - Yb.x, d1 = X.y - Yb.y, d2 = X.z - Yb.z;
+                    const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+                    const float rinv = rsqrtf(r2);
+                    const float w = X.w * Yb.w * rinv;          // X.w holds k / (4 pi)
+                    if constexpr (CPLX) {
+                        // |kappa r| stays within a few periods here; the hardware sine
+                        // and cosine are accurate far below the BF16 rounding of K
+                        float sn, cs;
+                        __sincosf(kappa * (r2 * rinv), &sn, &cs);
+                        wr[u] = w * cs;
+                        wi[u] = w * sn;
+                    } else {
+                        wr[u] = w;
+                        wi[u] = 0.0f;
+                    }
+                }
+                const int base = (ca * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7);
+                const __nv_bfloat162 kr = __floats2bfloat162_rn(wr[0], wr[1]);
+                reinterpret_cast<__nv_bfloat162*>(A + base)[0] = kr;
+                if constexpr (CPLX) {
+                    const __nv_bfloat162 mki = __floats2bfloat162_rn(-wi[0], -wi[1]);
+                    const __nv_bfloat162 ki = __floats2bfloat162_rn(wi[0], wi[1]);
+                    if (aligned8) {
+                        reinterpret_cast<__nv_bfloat162*>(A + base + offR)[0] = mki;
+                        reinterpret_cast<__nv_bfloat162*>(A + base + offD)[0] = ki;
+                        reinterpret_cast<__nv_bfloat162*>(A + base + offD + offR)[0] = kr;
+                    } else {
+                        auto at = [&](int m, int k) -> __nv_bfloat162* {
+                            return reinterpret_cast<__nv_bfloat162*>(A + ((m >> 3) * K8 + (k >> 3)) * 64 + (m & 7) * 8 +
+                                                                     (k & 7));
+                        };
+                        *at(a, b + q2) = mki;
+                        *at(a + q2, b) = ki;
+                        *at(a + q2, b + q2) = kr;
+                    }
+                }
+            }
+            // this warp's part of the A tile is written: make it visible to the
+            // tensor core (async proxy) and announce it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tsm(&afull[buf])) : "memory");
         }
-        const int tau = fsrc[b0 + i];
-        if (t == 0) {
+    } else if (lane == 0) {
+        for (int i = 0; i < n; ++i) {
+            const int buf = i & 1;
+            if (*vflag) { failed = true; break; }
+            if (i >= 2 && !tc_wait(&mdone[buf], (unsigned)(((i - 2) >> 1) & 1), wait_limit)) {
+                atomicOr(flag, 1);
+                failed = true;
+                break;
+            }
+            const int tau = fsrc[b0 + i];
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tsm(&bfull[buf])),
                          "r"((unsigned)bbytes)
                          : "memory");
@@ -310,71 +385,6 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
                              tsm(tiles + 2 * abytes + buf * bbytes)),
                          "l"(xb + (int64_t)tau * RP * KAP), "r"((unsigned)bbytes), "r"(tsm(&bfull[buf]))
                          : "memory");
-        }
-        // A tile: the coupling block in FP32, stored as BF16.  A warp fills one
-        // 8 x 8 core matrix per step (lane -> row lane / 4, columns 2 (lane % 4)
-        // and +1) with packed 4-byte stores: 128 contiguous bytes, no bank conflicts.
-        __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tiles + buf * abytes);
-        const float4* Y = geo + (int64_t)tau * q2;
-        const int q8 = (q2 + 7) >> 3;
-        // quadrant offsets of the real form when q2 is a multiple of 8
-        const int offR = (q2 >> 3) * 64, offD = (q2 >> 3) * K8 * 64;
-        const bool aligned8 = (q2 & 7) == 0;
-        // 512 threads: 16 warps; with q fixed the trip count is known and the
-        // loop unrolls, so a warp keeps several core matrices' SFU work in flight
-#pragma unroll
-        for (int cm = warp; cm < q8 * q8; cm += 16) {
-            const int ca = cm / q8, cb = cm - ca * q8;
-            const int a = 8 * ca + (lane >> 2), b = 8 * cb + 2 * (lane & 3);
-            if (a >= q2 || b >= q2) continue;   // q2 is even, so b + 1 < q2 as well
-            const float4 X = Xs[a];
-            float wr[2], wi[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const float4 Yb = Y[b + u];
-                const float d0 = X.x - Yb.x, d1 = X.y - Yb.y, d2 = X.z - Yb.z;
-                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-                const float rinv = rsqrtf(r2);
-                const float w = X.w * Yb.w * rinv;          // X.w holds k / (4 pi)
-                if constexpr (CPLX) {
-                    // |kappa r| stays within a few periods here; the hardware sine
-                    // and cosine are accurate far below the BF16 rounding of K
-                    float sn, cs;
-                    __sincosf(kappa * (r2 * rinv), &sn, &cs);
-                    wr[u] = w * cs;
-                    wi[u] = w * sn;
-                } else {
-                    wr[u] = w;
-                    wi[u] = 0.0f;
-                }
-            }
-            const int base = (ca * K8 + (b >> 3)) * 64 + (a & 7) * 8 + (b & 7);
-            const __nv_bfloat162 kr = __floats2bfloat162_rn(wr[0], wr[1]);
-            reinterpret_cast<__nv_bfloat162*>(A + base)[0] = kr;
-            if constexpr (CPLX) {
-                const __nv_bfloat162 mki = __floats2bfloat162_rn(-wi[0], -wi[1]);
-                const __nv_bfloat162 ki = __floats2bfloat162_rn(wi[0], wi[1]);
-                if (aligned8) {
-                    reinterpret_cast<__nv_bfloat162*>(A + base + offR)[0] = mki;
-                    reinterpret_cast<__nv_bfloat162*>(A + base + offD)[0] = ki;
-                    reinterpret_cast<__nv_bfloat162*>(A + base + offD + offR)[0] = kr;
-                } else {
-                    auto at = [&](int m, int k) -> __nv_bfloat162* {
-                        return reinterpret_cast<__nv_bfloat162*>(A + ((m >> 3) * K8 + (k >> 3)) * 64 + (m & 7) * 8 +
-                                                                 (k & 7));
-                    };
-                    *at(a, b + q2) = mki;
-                    *at(a + q2, b) = ki;
-                    *at(a + q2, b + q2) = kr;
-                }
-            }
-        }
-        // this warp's part of the A tile is written: make it visible to the tensor
-        // core (async proxy) and announce it
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tsm(&afull[buf])) : "memory");
-        if (t == 0) {
             const bool aok = tc_wait(&afull[buf], (unsigned)((i >> 1) & 1), wait_limit);
             const bool bok = aok && tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), wait_limit);
             if (!aok || !bok) {
@@ -382,10 +392,9 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
                 // the copy for this block may still land: wait for it before leaving
                 tc_wait(&bfull[buf], (unsigned)((i >> 1) & 1), 1LL << 24);
                 failed = true;
+                break;
             }
-        }
-        if (failed) break;
-        if (t == 0) {
+            __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(tiles + buf * abytes);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             for (int kk = 0; kk < KAP / 16; ++kk) {
                 const uint64_t ad = umma_desc(tsm(A) + kk * 256, 128, K8 * 128);
@@ -400,10 +409,10 @@ __global__ void __launch_bounds__(512) mr_coupling_tc_kernel(
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              tsm(&mdone[buf]))
                          : "memory");
+            issued = i + 1;
         }
-        issued = i + 1;
     }
-    if (t == 0) *issued_sh = issued;
+    if (t == 16 * 32) *issued_sh = issued;
     if (__syncthreads_or(failed)) failed = true;
     issued = *issued_sh;
     // wait for the last committed MMAs (bounded), then read the accumulator
@@ -671,7 +680,7 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
             auto kern = P.q == 8 ? mr_coupling_tc_kernel<CPLX, 8>
                                  : (P.q == 6 ? mr_coupling_tc_kernel<CPLX, 6> : mr_coupling_tc_kernel<CPLX, 0>);
             if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-            kern<<<nrows, 512, sm, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src,
+            kern<<<nrows, 544, sm, st>>>(h->d_far_rows, h->d_far_ptr, h->d_far_src,
                                          reinterpret_cast<const float4*>(h->d_igeo32), P.q, R, RP, KAP, tcols,
                                          (float)P.prm.kappa, xb, yh, h->wait_limit, h->d_status);
             h->launches += 2;
