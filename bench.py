@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
     ap.add_argument("--cnn-forward-only", action="store_true", help="time only the network's forward pass")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances section")
+    ap.add_argument("--batch-only", action="store_true", help="run only the batched-instances section")
     ap.add_argument("--learn-train-m", type=int, default=5, help="level of the training solves")
     ap.add_argument("--learn-m", type=int, default=6, help="level of the compared solves")
     ap.add_argument("--learn-nrhs", type=int, default=2, help="plane waves of the compared solves")
@@ -287,6 +289,68 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
                                "for it"}}
 
 
+def batched_instances(ibem, stream, args):
+    """Many uneven problem instances in one application: 24 seeded instances
+    (levels 2-4, degrees 1-3, Laplace or Helmholtz with kappa in [2, 8], q 6 or
+    8, 1-16 right-hand sides, spheres of radius 0.5-2), the FP32 operator with
+    the coupling generated on the fly (no FP64 coupling stored).  The batched,
+    graph-captured application is timed against the same instances applied one
+    after another through ibem_matvec."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(SEED + 7)
+    handles, nrhs, dofs = [], [], 0
+    t0 = time.perf_counter()
+    for _ in range(24):
+        kern = int(rng.integers(0, 2))
+        p, m, q = int(rng.integers(1, 4)), int(rng.integers(2, 5)), int(rng.choice([6, 8]))
+        R = int(rng.integers(1, 17))
+        kappa = float(rng.uniform(2.0, 8.0)) if kern else 0.0
+        rad = float(rng.uniform(0.5, 2.0))
+        h = ibem.ibem_create(ibem.sphere_patches(rad), ibem.make_params(p, m, q_cheb=q, kernel=kern, kappa=kappa,
+                                                                        fp64_coupling=ibem.IBEM_COUPLING_NONE), stream)
+        ibem.ibem_assemble(h)
+        handles.append(h)
+        nrhs.append(R)
+        dofs += ibem.ibem_get_info(h).ndof * R
+    setup_s = time.perf_counter() - t0
+    b = ibem.ibem_batch_create(handles, nrhs, stream)
+    off = ibem.ibem_batch_offsets(b, len(handles))
+    x = torch.from_numpy(rng.normal(size=off[-1])).cuda()
+    y = torch.zeros_like(x)
+    ys = torch.zeros_like(x)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                fn()
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def one_by_one():
+        for i, h in enumerate(handles):
+            ibem.ibem_matvec(h, x[off[i]:off[i + 1]], ys[off[i]:off[i + 1]], nrhs[i], ibem.IBEM_FP32)
+
+    batched_ms = timed(lambda: ibem.ibem_batch_matvec(b, x, y))
+    single_ms = timed(one_by_one)
+    diff = float((y - ys).abs().max() / ys.abs().max())
+    info = ibem.ibem_batch_info(b)
+    ibem.ibem_batch_destroy(b)
+    for h in handles:
+        ibem.ibem_destroy(h)
+    return {"instances": len(handles), "dof_rhs_per_apply": dofs, "setup_s": setup_s,
+            "batched_ms": batched_ms, "one_by_one_ms": single_ms, "speedup": single_ms / batched_ms,
+            "value": dofs / (batched_ms * 1e-3), "unit": UNIT, "rel_diff_batched_vs_one_by_one": diff,
+            "launches_per_apply": info["launches_per_apply"], "coupling_threads": info["coupling_threads"]}
+
+
 def cnn_forward_timing(ibem, stream, c):
     """The network's BF16 forward pass (tensor cores) on 96 images of 130 x 130
     (level 7, 16 right-hand sides x 6 patches), CUDA events on the bench stream,
@@ -427,6 +491,11 @@ def ours(args, rank, world, local_rank):
         out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
         if rank == 0:
             print(json.dumps({"helmholtz_64rhs": out}), flush=True)
+        return
+    if args.batch_only:
+        out = batched_instances(ibem, stream, args)
+        if rank == 0:
+            print(json.dumps({"batched_instances": out}), flush=True)
         return
     if args.cnn_forward_only:
         c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
@@ -588,6 +657,9 @@ def ours(args, rank, world, local_rank):
     # ---- Helmholtz, 64 plane waves: tensor-core coupling ----
     config3 = None if args.no_config3 else helmholtz_many_rhs(ibem, stream, world, barrier, args)
 
+    # ---- many uneven instances in one application ----
+    batched = None if args.no_batch else batched_instances(ibem, stream, args)
+
     # ---- learned preconditioner vs block-Jacobi ----
     learned = None if args.no_learned else learned_preconditioner(ibem, stream, args)
 
@@ -616,6 +688,7 @@ def ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "helmholtz_64rhs": config3,
             "learned_preconditioner": learned,
+            "batched_instances": batched,
             "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
                     "d2h_bytes_per_step": N * R * 8},
             "gpu_launches": prof["launches"],

@@ -189,9 +189,13 @@ __global__ void b_m2m_kernel(const BatchInst* __restrict__ B, int n, const int64
 // Persistent coupling: CTAs take (instance, r, row) items from *counter.
 // Thread t = g * q2 + a (g < G = blockDim / q2) sums target point a against the
 // blocks g, g + G, ... of the row; partial sums meet in shared memory.
+// Right-hand sides per coupling work item: every kernel value generated for a
+// far block serves up to BC_RB right-hand sides of the instance.
+constexpr int BC_RB = 8;
+
 __global__ void b_coupling_kernel(const BatchInst* __restrict__ B, int n, const int64_t* __restrict__ pre,
                                   int64_t total, int* __restrict__ counter) {
-    extern __shared__ float red[];
+    extern __shared__ float red[];   // [BC_RB][blockDim][2]
     __shared__ int64_t item;
     for (;;) {
         if (threadIdx.x == 0) item = atomicAdd(counter, 1);
@@ -201,16 +205,21 @@ __global__ void b_coupling_kernel(const BatchInst* __restrict__ B, int n, const 
         const int k = find_inst(pre, n, it);
         const BatchInst& I = B[k];
         const int64_t loc = it - pre[k];
-        const int64_t nrows = pre[k + 1] - pre[k];
-        const int r = (int)(loc / (nrows / I.R));
-        const int sigma = I.far_rows[loc % (nrows / I.R)];
+        const int nch = (I.R + BC_RB - 1) / BC_RB;
+        const int64_t nrows = (pre[k + 1] - pre[k]) / nch;
+        const int r0 = (int)(loc / nrows) * BC_RB;
+        const int nr = I.R - r0 < BC_RB ? I.R - r0 : BC_RB;
+        const int sigma = I.far_rows[loc % nrows];
         const int q2 = I.q2, cw = I.helm ? 2 : 1;
         const int G = blockDim.x / q2;
         const int t = threadIdx.x, gg = t / q2, a = t % q2;
-        float sr = 0.0f, si = 0.0f;
+        float sr[BC_RB], si[BC_RB];
+#pragma unroll
+        for (int j = 0; j < BC_RB; ++j) sr[j] = si[j] = 0.0f;
         if (gg < G) {
             const float4 X = reinterpret_cast<const float4*>(I.igeo32)[(int64_t)sigma * q2 + a];
-            const float* xr = I.xh + (int64_t)r * I.C * q2 * cw;
+            const int64_t rstride = (int64_t)I.C * q2 * cw;      // between right-hand sides
+            const float* xr = I.xh + (int64_t)r0 * rstride;
             for (int64_t blk = I.far_ptr[sigma] + gg; blk < I.far_ptr[sigma + 1]; blk += G) {
                 const int64_t tau = I.far_src[blk];
                 const float4* Y = reinterpret_cast<const float4*>(I.igeo32) + tau * q2;
@@ -225,28 +234,40 @@ __global__ void b_coupling_kernel(const BatchInst* __restrict__ B, int n, const 
                         float sn, cs;
                         __sincosf(I.kappa * (r2 * rinv), &sn, &cs);
                         const float kr = w * cs, ki = w * sn;
-                        const float vr = V[2 * b], vi = V[2 * b + 1];
-                        sr = fmaf(kr, vr, fmaf(-ki, vi, sr));
-                        si = fmaf(kr, vi, fmaf(ki, vr, si));
+#pragma unroll
+                        for (int j = 0; j < BC_RB; ++j) {
+                            if (j < nr) {
+                                const float vr = V[j * rstride + 2 * b], vi = V[j * rstride + 2 * b + 1];
+                                sr[j] = fmaf(kr, vr, fmaf(-ki, vi, sr[j]));
+                                si[j] = fmaf(kr, vi, fmaf(ki, vr, si[j]));
+                            }
+                        }
                     } else {
-                        sr = fmaf(w, V[b], sr);
+#pragma unroll
+                        for (int j = 0; j < BC_RB; ++j)
+                            if (j < nr) sr[j] = fmaf(w, V[j * rstride + b], sr[j]);
                     }
                 }
             }
         }
-        red[2 * t] = sr;
-        red[2 * t + 1] = si;
+#pragma unroll
+        for (int j = 0; j < BC_RB; ++j) {
+            red[2 * (j * blockDim.x + t)] = sr[j];
+            red[2 * (j * blockDim.x + t) + 1] = si[j];
+        }
         __syncthreads();
         if (t < q2) {
-            float vr = 0.0f, vi = 0.0f;
-            for (int j = 0; j < G; ++j) {
-                vr += red[2 * (j * q2 + t)];
-                vi += red[2 * (j * q2 + t) + 1];
-            }
             const float ka = reinterpret_cast<const float4*>(I.igeo32)[(int64_t)sigma * q2 + t].w * 0.07957747154594767f;
-            float* o = I.yh + (((int64_t)r * I.C + sigma) * q2 + t) * cw;
-            o[0] = vr * ka;
-            if (cw == 2) o[1] = vi * ka;
+            for (int j = 0; j < nr; ++j) {
+                float vr = 0.0f, vi = 0.0f;
+                for (int g = 0; g < G; ++g) {
+                    vr += red[2 * (j * blockDim.x + g * q2 + t)];
+                    vi += red[2 * (j * blockDim.x + g * q2 + t) + 1];
+                }
+                float* o = I.yh + (((int64_t)(r0 + j) * I.C + sigma) * q2 + t) * cw;
+                o[0] = vr * ka;
+                if (cw == 2) o[1] = vi * ka;
+            }
         }
         __syncthreads();
     }
@@ -385,7 +406,7 @@ cudaError_t batch_enqueue(ibem_batch* b, const double* x, double* y, int couplin
         ++launches;
     }
     if (total(B::ST_COUPLE) > 0) {
-        b_coupling_kernel<<<b->couple_ctas, coupling_threads, 2 * coupling_threads * sizeof(float), st>>>(
+        b_coupling_kernel<<<b->couple_ctas, coupling_threads, 2 * BC_RB * coupling_threads * sizeof(float), st>>>(
             b->d_inst, b->n, b->d_pre[B::ST_COUPLE], total(B::ST_COUPLE), b->d_counter);
         ++launches;
     }
@@ -505,7 +526,7 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
         cnt[ibem_batch::ST_BACK] = R * I.E * I.nb;
         cnt[ibem_batch::ST_NEAR] = 0;
         cnt[ibem_batch::ST_RESTRICT] = R * I.N;
-        cnt[ibem_batch::ST_COUPLE] = R * (int64_t)handles[i]->far_rows.size();
+        cnt[ibem_batch::ST_COUPLE] = ((R + BC_RB - 1) / BC_RB) * (int64_t)handles[i]->far_rows.size();
         for (int kk = 1; kk <= b->max_m; ++kk) {
             if (I.m >= kk) {
                 const int L = I.m - kk;
@@ -543,7 +564,7 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
         for (int threads : {128, 256, 512}) {
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel, threads,
-                                                          2 * threads * sizeof(float));
+                                                          2 * BC_RB * threads * sizeof(float));
             b->couple_ctas = sms * std::max(1, per_sm);
             batch_enqueue(b, xs_tmp, ys_tmp, threads);
             cudaEventRecord(e0, b->stream);
@@ -564,7 +585,7 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel, b->couple_threads,
-                                                  2 * b->couple_threads * sizeof(float));
+                                                  2 * BC_RB * b->couple_threads * sizeof(float));
     b->couple_ctas = sms * std::max(1, per_sm);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         ibem_batch_destroy(b);
