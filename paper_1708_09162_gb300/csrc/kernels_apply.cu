@@ -549,28 +549,43 @@ __global__ void leaf_back_kernel(int R, int64_t E, int pp, int q, const double* 
 // ---- near field product ------------------------------------------------------
 // One CTA per target element; thread t = i * nb + j accumulates B[i][j] x*_s[j]
 // over the row's blocks (one coalesced nb^2 read per block), then rows are
-// summed through shared memory.
+// summed through shared memory.  The row's source elements are staged in shared
+// memory (so a source value's load does not wait for a dependent global load)
+// and the sum over blocks runs in four independent partial sums.
 template <typename T>
 __global__ void near_apply_kernel(const int64_t* __restrict__ nptr, const int32_t* __restrict__ nsrc,
                                   const T* __restrict__ blocks, int nb, int64_t E, const T* __restrict__ xs,
                                   double* __restrict__ ys) {
     extern __shared__ double red[];
-    int64_t e = blockIdx.x, r = blockIdx.y;
-    int t = threadIdx.x, nbb = nb * nb;
-    double acc = 0.0;
-    if (t < nbb) {
-        int j = t % nb;
-        const T* xr = xs + r * E * nb;
-        T part = (T)0;
-        for (int64_t k = nptr[e]; k < nptr[e + 1]; ++k)
-            part += blocks[k * nbb + t] * xr[(int64_t)nsrc[k] * nb + j];
-        acc = (double)part;
+    __shared__ int32_t srcs[256];
+    const int64_t e = blockIdx.x, r = blockIdx.y;
+    const int t = threadIdx.x, nbb = nb * nb;
+    const int64_t k0 = nptr[e], k1 = nptr[e + 1];
+    const int j = t % nb;
+    const T* xr = xs + r * E * nb;
+    T p0 = (T)0, p1 = (T)0, p2 = (T)0, p3 = (T)0;
+    for (int64_t kb = k0; kb < k1; kb += 256) {
+        const int kc = (int)(k1 - kb < 256 ? k1 - kb : 256);
+        __syncthreads();   // the previous chunk's source list is consumed
+        for (int i = t; i < kc; i += blockDim.x) srcs[i] = nsrc[kb + i];
+        __syncthreads();
+        if (t < nbb) {
+            const T* bk = blocks + kb * nbb + t;
+            int kk = 0;
+            for (; kk + 3 < kc; kk += 4) {
+                p0 += bk[(int64_t)kk * nbb] * xr[(int64_t)srcs[kk] * nb + j];
+                p1 += bk[(int64_t)(kk + 1) * nbb] * xr[(int64_t)srcs[kk + 1] * nb + j];
+                p2 += bk[(int64_t)(kk + 2) * nbb] * xr[(int64_t)srcs[kk + 2] * nb + j];
+                p3 += bk[(int64_t)(kk + 3) * nbb] * xr[(int64_t)srcs[kk + 3] * nb + j];
+            }
+            for (; kk < kc; ++kk) p0 += bk[(int64_t)kk * nbb] * xr[(int64_t)srcs[kk] * nb + j];
+        }
     }
-    red[t] = acc;
+    red[t] = t < nbb ? (double)((p0 + p1) + (p2 + p3)) : 0.0;
     __syncthreads();
     if (t < nb) {
         double v = 0.0;
-        for (int j = 0; j < nb; ++j) v += red[t * nb + j];
+        for (int jj = 0; jj < nb; ++jj) v += red[t * nb + jj];
         ys[(r * E + e) * nb + t] += v;
     }
 }
