@@ -184,6 +184,24 @@ def _profile_traffic():
     return None
 
 
+def max_over_ranks(value):
+    """The largest of the ranks' values (a time), through the initialised process
+    group (NCCL on the GPUs, or gloo on the host); the value itself with one rank."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if td.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -544,11 +562,8 @@ def ours(args, rank, world, local_rank):
     prof = ibem.ibem_profile_read(h)
     ibem.ibem_profile_enable(h, False)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * R / (ms * 1e-3)
+    ms = max_over_ranks(ms)
+    value = job_throughput(world, N * R, ms * 1e-3)
 
     # ---- roofline of the dominant kernel ----
     # coupling_df_kernel streams the double-float coupling matrices (8 bytes per
@@ -628,10 +643,7 @@ def ours(args, rank, world, local_rank):
     for _ in range(e2e_steps):
         ibem.ibem_matvec_host(h, xh, yh, R)
     e2e_s = (time.perf_counter() - t) / e2e_steps
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        td.all_reduce(tt, op=td.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(e2e_s)
 
     # ---- solves to 1e-8 ----
     solve = None
