@@ -247,8 +247,7 @@ ibem_status ibem_device_status(ibem_handle* h, int* status);
 ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_dev, int nrhs,
                                    const double* pts_dev, int64_t npts, double* u_dev);
 
-/* ---- Batches of uneven instances (spec batching; no counterpart in the
- * paper) ----
+/* ---- Batches of uneven instances (no counterpart in the paper) ----
  * A batch applies the FP32 operator of many assembled handles (different
  * geometry, level, degree, kernel and number of right-hand sides) together:
  * every stage runs as one launch over all instances, the far-field coupling as
@@ -275,8 +274,9 @@ ibem_status ibem_batch_destroy(ibem_batch* b);
  * Call once with null arrays to get the counts.  near: [n_near][8] int32 =
  * (patch_t, ix_t, iy_t, patch_s, ix_s, iy_s, class, orientation) with class
  * 0 identical, 1 common edge, 2 common vertex, 3 subdivided, 4 regular and
- * orientation = 8 * k_target + k_source (symmetries of the square, in the fixed
- * order documented in the design doc).  far: [n_far][8] int32 = (patch, level, ix, iy)
+ * orientation = 8 * k_target + k_source, k indexing the symmetries of the unit
+ * square in the order (s,t), (1-t,s), (1-s,1-t), (t,1-s), (t,s), (1-s,t),
+ * (1-t,1-s), (s,1-t).  far: [n_far][8] int32 = (patch, level, ix, iy)
  * of the target cluster then of the source cluster.  Lists are sorted. */
 ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_params* params,
                             int64_t* n_near, int32_t* near, int64_t* n_far, int32_t* far);
