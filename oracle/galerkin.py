@@ -16,7 +16,8 @@ objects evaluate, so a test can substitute another kernel (for example one that
 is polynomial in the parameters).
 
 Pinned by: V 1 = 1 (Laplace) and V 1 = sin(k) e^{ik} / k (Helmholtz) on the unit
-sphere, the Rayleigh quotients of Y_l against 1 / (2l + 1), symmetry and
+sphere, the Rayleigh quotients of Y_l against 1 / (2l + 1), the l = 1
+densities 3 z (Laplace) and z / (i k j_1(k) h_1(k)) (Helmholtz), symmetry and
 positivity of the Laplace matrix (tests/test_oracle_galerkin.py).
 """
 import numpy as np

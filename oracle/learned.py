@@ -24,6 +24,12 @@ over nb residuals of unit norm (e is not needed).  With z_j = s_j + sigma_j
 net(x_j) and the complex linear A, dL / d(real, imag of z_j) is
 A^H (A z_j - r_j) / nb, and dL / d(net output of x_j) is sigma_j times that,
 in the real / imaginary channels.
+
+Pinned by: the block groups cover every dof once and follow the anchor
+elements, a network whose last layer is zero gives block-Jacobi exactly, z is
+homogeneous of degree one in v, a training pair rebuilds e from its input and
+target, and the gradient of the residual-norm objective against central
+differences (tests/test_oracle_cnn.py).
 """
 import numpy as np
 

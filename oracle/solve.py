@@ -10,7 +10,10 @@
 
 Pinned by: interior Laplace with a point source outside the sphere (u = g in
 the ball) and exterior Helmholtz with a point source inside (u = g outside),
-and CG / GMRES against the direct solve (tests/test_oracle_solve.py).
+and CG / GMRES against the direct solve (tests/test_oracle_solve.py);
+flexible GMRES by one step with the exact inverse, by equality with GMRES for a
+fixed preconditioner and by convergence with a varying one
+(tests/test_oracle_cnn.py).
 """
 import numpy as np
 

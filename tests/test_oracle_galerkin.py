@@ -47,7 +47,8 @@ def test_helmholtz_constant_eigenfunction_and_symmetry(sphere):
     assert np.max(np.abs(A - A.conj().T)) > 1e-3 * np.max(np.abs(A))
 
 
-def _density_error_y1(disc, A):
+def _density_error_y1(disc, A, scale=3.0):
+    # L2 error of the computed density against scale * z for data g = z
     b = disc.rhs(lambda F: F[:, 2])[:, 0]
     w = solve.dense_solve(A, b)
     me = disc.mesh
@@ -55,8 +56,8 @@ def _density_error_y1(disc, A):
     for e in range(me.n_elements):
         _, F, k, wq, bas, _ = disc._product_points(e, "regular")
         dens = bas @ w[me.local_dofs(e)]
-        err2 += np.sum(wq * k * (dens - 3 * F[:, 2]) ** 2)
-        nrm2 += np.sum(wq * k * (3 * F[:, 2]) ** 2)
+        err2 += np.sum(wq * k * np.abs(dens - scale * F[:, 2]) ** 2)
+        nrm2 += np.sum(wq * k * np.abs(scale * F[:, 2]) ** 2)
     return np.sqrt(err2 / nrm2), w
 
 
@@ -73,6 +74,23 @@ def test_laplace_density_of_first_harmonic(sphere, laplace_p2m2):
     P = seeded_ball_points(50, 0.5, 3)
     u = solve.potential(disc, w, P)[:, 0]
     assert np.max(np.abs(u - P[:, 2])) < 5e-6
+
+
+def test_helmholtz_density_of_first_harmonic(sphere):
+    # On the unit sphere the Helmholtz single layer maps Y_l to i k j_l(k) h_l(k) Y_l
+    # (spherical Bessel and first-kind Hankel functions); for g = z the density is
+    # z / (i k j_1(k) h_1(k)).  A sign or phase error in the kernel, a dropped
+    # Jacobian or a conjugated bilinear form changes this l = 1 eigenvalue.
+    from scipy.special import spherical_jn, spherical_yn
+    k = 2.0
+    lam = 1j * k * spherical_jn(1, k) * (spherical_jn(1, k) + 1j * spherical_yn(1, k))
+    errs = []
+    for m in (1, 2):
+        disc = galerkin.Discretisation(sphere, 2, m, galerkin.HelmholtzKernel(k))
+        err, _ = _density_error_y1(disc, disc.dense_matrix(), scale=1.0 / lam)
+        errs.append(err)
+    assert errs[1] < 5e-3
+    assert errs[0] / errs[1] > 4.0
 
 
 def test_pair_classes_counts(laplace_p2m2):
