@@ -58,7 +58,12 @@ enum {
  * NURBS: degrees deg_u, deg_v >= 1 (<= 7), ncp_u x ncp_v control points,
  * knots_u has ncp_u + deg_u + 1 entries (open, non-decreasing, from 0 to 1),
  * ctrl_xyz is [ncp_v][ncp_u][3], weights is [ncp_v][ncp_u] and positive.
- * SPHERE_FACE: face in 0..5, radius > 0, center. */
+ * SPHERE_FACE: face in 0..5, radius > 0, center.
+ * perturbed != 0 (either kind): the patch map becomes F(f(u), f(v)) with the
+ * piecewise-linear f of Sec. 5 (perturbed mappings): f(x) = x / 2 on [0, 0.3],
+ * 1.75 x - 0.375 on (0.3, 0.7), (x + 1) / 2 on [0.7, 1].  Same surface, same
+ * patch corners, a parametrisation with kinks at 0.3 and 0.7 (H^1, not H^2);
+ * its derivatives carry the factors f'(u), f'(v). */
 typedef struct {
     int kind;
     int deg_u, deg_v, ncp_u, ncp_v;
@@ -66,6 +71,7 @@ typedef struct {
     int face;
     double radius;
     double center[3];
+    int perturbed;
 } ibem_patch;
 
 enum { IBEM_LAPLACE = 0, IBEM_HELMHOLTZ = 1 };   /* Eqs. fundament1 / fundament2 */

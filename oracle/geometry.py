@@ -12,8 +12,14 @@ Two kinds of patch are provided:
   used for the unit-sphere workloads: no exact rational biquadratic 6-patch
   sphere exists, so the closed-form sphere pins are run on this exact map.
 
+* ``PerturbedPatch`` - either map composed with the piecewise-linear
+  reparametrisation f of Sec. 5 (perturbed mappings) in both parameters.
+
 Pinned by: |F| = R on the sphere, area 4 pi R^2, finite-difference derivatives,
-and the exact area of a rational-quadratic quarter cylinder
+and the exact area of a rational-quadratic quarter cylinder; for the perturbed
+map, f against its three pieces and its continuity, the image on the sphere,
+the corners of the unperturbed map, one-sided finite differences away from the
+kinks, and the area 4 pi by a Gauss rule split at the kinks
 (tests/test_oracle_geometry.py).
 """
 import numpy as np
@@ -88,6 +94,36 @@ class NurbsPatch:
         Fu = (Pu - F * Wu[:, None]) / W[:, None]
         Fv = (Pv - F * Wv[:, None]) / W[:, None]
         return F, Fu, Fv
+
+
+def perturbation(x):
+    """The piecewise-linear f : [0, 1] -> [0, 1] of Sec. 5 (perturbed mappings),
+    f(x) = x/2 on [0, 0.3], 1.75 x - 0.375 on (0.3, 0.7), (x + 1)/2 on [0.7, 1];
+    returns f(x) and f'(x) (slope of the left piece at the two kinks)."""
+    x = np.asarray(x, dtype=np.float64)
+    f = np.where(x <= 0.3, 0.5 * x, np.where(x < 0.7, 1.75 * x - 0.375, 0.5 * (x + 1.0)))
+    df = np.where(x <= 0.3, 0.5, np.where(x < 0.7, 1.75, 0.5))
+    return f, df
+
+
+class PerturbedPatch:
+    """A patch map composed with f in each parameter (Sec. 5): G(u, v) =
+    F(f(u), f(v)), dG/du = f'(u) dF/du, dG/dv = f'(v) dF/dv.  Same image and
+    corners as F, but a parametrisation that is only H^1."""
+
+    def __init__(self, patch):
+        self.patch = patch
+
+    def eval(self, u, v):
+        fu, du = perturbation(np.atleast_1d(u))
+        fv, dv = perturbation(np.atleast_1d(v))
+        F, Fu, Fv = self.patch.eval(fu, fv)
+        return F, Fu * du[:, None], Fv * dv[:, None]
+
+
+def perturbed_sphere(radius=1.0, center=(0.0, 0.0, 0.0)):
+    """The cube-sphere faces, each composed with the perturbation (Sec. 5)."""
+    return [PerturbedPatch(p) for p in unit_sphere(radius, center)]
 
 
 def surface_measure(Fu, Fv):

@@ -26,6 +26,7 @@ struct PatchDesc {
     int deg_u, deg_v, ncp_u, ncp_v;
     int knot_off_u, knot_off_v, cp_off;   // offsets into knots[] and cpw[] (x w, y w, z w, w)
     double R, c0[3], n[3], t1[3], t2[3];  // sphere face
+    int perturbed;            // parameters mapped by perturbation_f first
 };
 
 struct GeomView {
@@ -83,10 +84,40 @@ __host__ __device__ inline void local_bsplines(const double* xi, int deg, int s,
     }
 }
 
-// F(u, v), dF/du, dF/dv of one patch.
+// The piecewise-linear reparametrisation of [0, 1] of Sec. 5 (perturbed
+// mappings): slopes 1/2, 7/4, 1/2 with kinks at 0.3 and 0.7; returns f(x) and
+// stores f'(x) (the left piece's slope at a kink, which no quadrature or
+// interpolation point of a dyadic mesh hits).
+__host__ __device__ inline double perturbation_f(double x, double* df) {
+    if (x <= 0.3) { *df = 0.5; return 0.5 * x; }
+    if (x < 0.7) { *df = 1.75; return 1.75 * x - 0.375; }
+    *df = 0.5;
+    return 0.5 * (x + 1.0);
+}
+
+__host__ __device__ inline void eval_patch_map(const PatchDesc& P, const GeomView& g, double u, double v,
+                                               double F[3], double Fu[3], double Fv[3]);
+
+// F(u, v), dF/du, dF/dv of one patch (chain rule through f for a perturbed patch).
 __host__ __device__ inline void eval_patch(const GeomView& g, int ip, double u, double v,
                                            double F[3], double Fu[3], double Fv[3]) {
     const PatchDesc& P = g.patches[ip];
+    if (P.perturbed) {
+        double du, dv;
+        const double fu = perturbation_f(u, &du), fv = perturbation_f(v, &dv);
+        eval_patch_map(P, g, fu, fv, F, Fu, Fv);
+        for (int i = 0; i < 3; ++i) {
+            Fu[i] *= du;
+            Fv[i] *= dv;
+        }
+        return;
+    }
+    eval_patch_map(P, g, u, v, F, Fu, Fv);
+}
+
+// The patch map itself: analytic sphere face or NURBS.
+__host__ __device__ inline void eval_patch_map(const PatchDesc& P, const GeomView& g, double u, double v,
+                                               double F[3], double Fu[3], double Fv[3]) {
     if (P.kind == IBEM_PATCH_SPHERE_FACE) {
         double a = 2.0 * u - 1.0, b = 2.0 * v - 1.0;
         double c[3];

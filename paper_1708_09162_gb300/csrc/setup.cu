@@ -255,6 +255,7 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
         PatchDesc d;
         std::memset(&d, 0, sizeof(d));
         d.kind = s.kind;
+        d.perturbed = s.perturbed != 0;
         if (s.kind == IBEM_PATCH_SPHERE_FACE) {
             static const double frames[6][3][3] = {
                 {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},  {{-1, 0, 0}, {0, 0, 1}, {0, 1, 0}},

@@ -48,7 +48,8 @@ class ibem_patch(ctypes.Structure):
                 ("ncp_u", ctypes.c_int), ("ncp_v", ctypes.c_int),
                 ("knots_u", ctypes.POINTER(ctypes.c_double)), ("knots_v", ctypes.POINTER(ctypes.c_double)),
                 ("ctrl_xyz", ctypes.POINTER(ctypes.c_double)), ("weights", ctypes.POINTER(ctypes.c_double)),
-                ("face", ctypes.c_int), ("radius", ctypes.c_double), ("center", ctypes.c_double * 3)]
+                ("face", ctypes.c_int), ("radius", ctypes.c_double), ("center", ctypes.c_double * 3),
+                ("perturbed", ctypes.c_int)]
 
 
 class ibem_params(ctypes.Structure):
@@ -169,13 +170,15 @@ def _hptr(a):
 
 
 # ---- patch and parameter builders -------------------------------------------------
-def sphere_patches(radius=1.0, center=(0.0, 0.0, 0.0)):
-    """The six analytic cube-sphere faces of a sphere."""
+def sphere_patches(radius=1.0, center=(0.0, 0.0, 0.0), perturbed=False):
+    """The six analytic cube-sphere faces of a sphere (perturbed: each face map
+    composed with the piecewise-linear reparametrisation of Sec. 5)."""
     arr = (ibem_patch * 6)()
     for f in range(6):
         arr[f].kind = IBEM_PATCH_SPHERE_FACE
         arr[f].face = f
         arr[f].radius = radius
+        arr[f].perturbed = int(bool(perturbed))
         for k in range(3):
             arr[f].center[k] = center[k]
     return arr

@@ -50,6 +50,19 @@ def test_block_tree_equals_oracle_sphere(ibem, sphere, p, m):
     assert sorted(map(tuple, far.tolist())) == ofar
 
 
+def test_block_tree_equals_oracle_perturbed_sphere(ibem):
+    # the perturbed face maps of Sec. 5 move the bounding balls and the
+    # near-singular pairs; lists still equal the oracle's exactly
+    from oracle import geometry
+    pert = geometry.perturbed_sphere()
+    near, far = ibem.ibem_block_tree(ibem.sphere_patches(perturbed=True), ibem.make_params(2, 3, q_cheb=6, eta=1.6))
+    onear, ofar = _oracle_lists(pert, 2, 3, 1.6)
+    assert sorted(map(tuple, near.tolist())) == onear
+    assert sorted(map(tuple, far.tolist())) == ofar
+    plain, _ = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(2, 3, q_cheb=6, eta=1.6))
+    assert sorted(map(tuple, plain.tolist())) != onear
+
+
 def test_block_tree_dense_mode_has_all_pairs(ibem):
     near, far = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(1, 1, q_cheb=0))
     assert far.shape[0] == 0 and near.shape[0] == 24 * 24

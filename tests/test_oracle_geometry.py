@@ -69,3 +69,53 @@ def test_nurbs_quarter_cylinder_exact():
 def test_nurbs_rejects_nonpositive_weights():
     with pytest.raises(ValueError):
         geometry.NurbsPatch(1, 1, [0, 0, 1, 1], [0, 0, 1, 1], np.zeros((2, 2, 3)), np.array([[1, 1], [0, 1.0]]))
+
+
+def test_perturbation_pieces_and_continuity():
+    # Sec. 5 (perturbed mappings): slopes 1/2, 7/4, 1/2; f(0) = 0, f(1) = 1,
+    # continuous at the kinks 0.3 (value 0.15) and 0.7 (value 0.85)
+    f, df = geometry.perturbation(np.array([0.0, 0.1, 0.3, 0.5, 0.7, 0.9, 1.0]))
+    np.testing.assert_allclose(f, [0.0, 0.05, 0.15, 0.5, 0.85, 0.95, 1.0], atol=1e-15)
+    np.testing.assert_array_equal(df, [0.5, 0.5, 0.5, 1.75, 0.5, 0.5, 0.5])
+    for k in (0.3, 0.7):
+        lo, _ = geometry.perturbation(k - 1e-12)
+        hi, _ = geometry.perturbation(k + 1e-12)
+        assert abs(hi - lo) < 1e-11
+
+
+def test_perturbed_sphere_image_corners_derivatives_area(sphere):
+    pert = geometry.perturbed_sphere()
+    rng = np.random.default_rng(12)
+    u, v = rng.random(300), rng.random(300)
+    c = np.array([0.0, 1.0])
+    for face, pface in zip(sphere, pert):
+        F, Fu, Fv = pface.eval(u, v)
+        np.testing.assert_allclose(np.linalg.norm(F, axis=1), 1.0, atol=1e-15)
+        assert np.all(np.sum(np.cross(Fu, Fv) * F, axis=1) > 0)
+        # same corners, so the faces still meet edge to edge
+        uu, vv = np.repeat(c, 2), np.tile(c, 2)
+        np.testing.assert_allclose(pface.eval(uu, vv)[0], face.eval(uu, vv)[0], atol=1e-15)
+    # central differences at points whose +-h stencil stays inside one piece
+    uu = np.array([0.1, 0.45, 0.62, 0.85])
+    vv = np.array([0.55, 0.2, 0.95, 0.4])
+    h = 1e-6
+    for pface in pert:
+        _, Fu, Fv = pface.eval(uu, vv)
+        fdu = (pface.eval(uu + h, vv)[0] - pface.eval(uu - h, vv)[0]) / (2 * h)
+        fdv = (pface.eval(uu, vv + h)[0] - pface.eval(uu, vv - h)[0]) / (2 * h)
+        np.testing.assert_allclose(Fu, fdu, atol=1e-8)
+        np.testing.assert_allclose(Fv, fdv, atol=1e-8)
+    # the area is invariant under reparametrisation: a Gauss rule split at the
+    # kinks integrates the piecewise-smooth measure to 4 pi
+    from oracle import gauss
+    x, w = gauss.gauss_legendre(16)
+    cuts = [0.0, 0.3, 0.7, 1.0]
+    nodes = np.concatenate([a + (b - a) * x for a, b in zip(cuts, cuts[1:])])
+    wts = np.concatenate([(b - a) * w for a, b in zip(cuts, cuts[1:])])
+    U, V = np.meshgrid(nodes, nodes, indexing="ij")
+    W = np.outer(wts, wts).ravel()
+    area = 0.0
+    for pface in pert:
+        _, Fu, Fv = pface.eval(U.ravel(), V.ravel())
+        area += np.sum(W * geometry.surface_measure(Fu, Fv))
+    assert abs(area - 4 * np.pi) < 1e-12

@@ -52,3 +52,22 @@ def test_exterior_helmholtz_point_source(sphere):
     wg, it = solve.gmres(lambda x: A @ x, b, rtol=1e-10, restart=30, diag=np.diag(A).copy())
     assert np.linalg.norm(b - A @ wg) <= 1.0001e-10 * np.linalg.norm(b)
     assert np.linalg.norm(wg - w) < 1e-7 * np.linalg.norm(w)
+
+
+def test_perturbed_mapping_rate_drop():
+    # Sec. 5 (perturbed mappings): with the kinked reparametrisation the interior
+    # point-source potential converges only like h^3 (the lowest-order rate), and
+    # at equal (p, m) its error is orders of magnitude above the plain sphere's
+    from conftest import seeded_ball_points
+    from oracle import geometry
+    x0 = np.array([0.9, 0.9, 0.9])
+    g = lambda F: 1.0 / (4 * np.pi * np.linalg.norm(F - x0, axis=1))
+    P = seeded_ball_points(50, 0.5, 170809162)
+    err = {}
+    for name, pats in (("plain", geometry.unit_sphere()), ("perturbed", geometry.perturbed_sphere())):
+        for m in (1, 2):
+            disc = galerkin.Discretisation(pats, 1, m, galerkin.LaplaceKernel())
+            w = solve.dense_solve(disc.dense_matrix(), disc.rhs(g)[:, 0])
+            err[name, m] = np.max(np.abs(solve.potential(disc, w, P)[:, 0] - g(P)))
+    assert 6.0 < err["perturbed", 1] / err["perturbed", 2] < 12.0      # h^3 gives 8
+    assert err["perturbed", 2] > 100 * err["plain", 2]
