@@ -15,10 +15,18 @@ tensor index is a = a_v * q + a_u.  Moments are integrated per element with
 ceil((q + p) / 2) + 1 Gauss points per direction, exact for the polynomial
 integrand.  Near blocks are the element-pair blocks of ``galerkin``.
 
+The potential (Eq. repform) takes the same interpolation on every cluster that
+is admissible for the evaluation point (a reading: the point is a ball of radius
+0 in the admissibility test) and the Gauss rule of ``solve.potential`` on the
+remaining elements.
+
 Pinned by: with a kernel that is a polynomial of degree < q in each parameter
 variable the far field is exact, so the FMM operator equals the dense one to
 rounding; with the true kernel the error against the dense matrix falls as q
-grows (tests/test_oracle_fmm.py).
+grows.  Potential: a point kernel polynomial of degree < q in the parameters
+gives the direct quadrature to rounding with both branches taken; with nothing
+admissible it is the direct potential; with the true kernel its error against
+the direct potential falls as q grows (tests/test_oracle_fmm.py).
 """
 import math
 from collections import defaultdict
@@ -149,6 +157,67 @@ class FMMOperator:
             y[patch * n1 * n1:(patch + 1) * n1 * n1] += np.einsum(
                 "vb,uc,bcr->vur", mu_v, mu_u, Yh).reshape(n1 * n1, -1)
         return y.reshape(x.shape) if x.ndim == 1 else y
+
+    # ---- potential (Eq. repform) with the far field interpolated -----------
+    def cluster_moments(self, x2, cl):
+        """x^_tau[b] = int_tau L_b^tau(y^) w(y^) dy^ for one cluster (shape (q^2, R))."""
+        patch, level, ix, iy = cl
+        X = self._grid(x2, patch)
+        mu_u = self.moments_1d(level, ix)
+        mu_v = self.moments_1d(level, iy)
+        return np.einsum("vb,uc,vur->bcr", mu_v, mu_u, X).reshape(self.q * self.q, -1)
+
+    def point_admissible(self, x, cl):
+        """Reading of Def. 4.1 for a point and a cluster (the point as a ball of
+        radius 0): eta * diam(tau) < dist(x, tau) = max(0, |x - c_tau| - r_tau)."""
+        c, r = self.cg.ball(cl)
+        d = np.sqrt(np.sum((x - c) ** 2)) - r
+        return self.eta * 2.0 * r < (d if d > 0.0 else 0.0)
+
+    def potential(self, w, points, point_kernel=None):
+        """u(x) = int_Gamma u*(x, y) w(y) dy (Eq. repform), with the interpolation
+        of Sec. 4.2 on every cluster that is admissible for x:
+            int_tau u*(x, F(y^)) k(y^) w(y^) dy^
+              ~ sum_b u*(x, F(z_b^tau)) k(z_b^tau) x^_tau[b].
+        For each point the clusters are visited from the patch roots down: an
+        admissible cluster is taken in the far field, a non-admissible element
+        with the n x n Gauss rule of ``solve.potential``, any other cluster is
+        split into its four children.  ``point_kernel(X (P,3), F (n,3), k (n,),
+        uv (n,2), patch)`` replaces u*(x, F) k (a test hook); w is (N,) or (N, R)."""
+        from .galerkin import fundamental_solution
+        from .tree import children, element_index
+        me = self.mesh
+        w2 = w.reshape(me.n_dofs, -1)
+        if point_kernel is None:
+            kern = self.disc.kernel
+
+            def point_kernel(X, F, k, uv, patch):
+                return fundamental_solution(kern, X[:, None, :], F[None, :, :]) * k[None, :]
+        dt = np.result_type(w2, np.complex128 if self.disc.kernel.is_complex else np.float64)
+        u = np.zeros((len(points), w2.shape[1]), dtype=dt)
+        moments = {}
+        self.potential_counts = []
+        for i, x in enumerate(np.asarray(points, dtype=np.float64)):
+            nfar = nnear = 0
+            stack = [(patch, 0, 0, 0) for patch in range(len(me.patches))]
+            while stack:
+                cl = stack.pop()
+                if self.point_admissible(x, cl):
+                    if cl not in moments:
+                        moments[cl] = self.cluster_moments(w2, cl)
+                    uv, F, k, patch = self.interpolation_geometry(cl)
+                    u[i] += point_kernel(x[None, :], F, k, uv, patch)[0] @ moments[cl]
+                    nfar += 1
+                elif cl[1] == me.m:
+                    e = element_index(cl, me.m)
+                    uvq, F, k, wq, b, patch = self.disc._product_points(e, "regular")
+                    dens = b @ w2[me.local_dofs(e)]
+                    u[i] += point_kernel(x[None, :], F, k, uvq, patch)[0] @ (wq[:, None] * dens)
+                    nnear += 1
+                else:
+                    stack.extend(children(cl))
+            self.potential_counts.append((nfar, nnear))
+        return u
 
     def rows(self, rows, x):
         """Selected rows of the FMM operator applied to x (exact per row)."""
