@@ -46,9 +46,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64-coupling comparison")
-    ap.add_argument("--no-config3", action="store_true", help="skip the many-right-hand-side Helmholtz section")
-    ap.add_argument("--config3-only", action="store_true", help="run only the many-right-hand-side section")
-    ap.add_argument("--config3-m", type=int, default=6, help="refinement level of that section (profiling)")
+    ap.add_argument("--no-helmholtz-many", action="store_true", help="skip the many-right-hand-side Helmholtz section")
+    ap.add_argument("--helmholtz-many-only", action="store_true", help="run only the many-right-hand-side section")
+    ap.add_argument("--helmholtz-many-m", type=int, default=6, help="refinement level of that section (profiling)")
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
@@ -218,7 +218,7 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
     and the roofline of the tensor-core coupling kernel."""
     import numpy as np
     import torch
-    p, m, q, kappa, R = 2, args.config3_m, 8, 4.0, 64
+    p, m, q, kappa, R = 2, args.helmholtz_many_m, 8, 4.0, 64
     t0 = time.perf_counter()
     h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=ibem.IBEM_HELMHOLTZ,
                                                                  kappa=kappa), stream)
@@ -281,9 +281,24 @@ def helmholtz_many_rhs(ibem, stream, world, barrier, args):
     torch.cuda.synchronize()
     pot_ms = e0.elapsed_time(e1) / 2
     nsrc = info.n_elements * 64
+    # the same potentials with the far field interpolated (forward moments of the
+    # 64 densities, per-point tree walk, q^2 kernel values per admissible cluster)
+    uf = torch.empty_like(u)
+    with torch.cuda.stream(stream):
+        nf, nn = ibem.ibem_potential_fmm(h, b, R, pts, uf)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            ibem.ibem_potential_fmm(h, b, R, pts, uf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fmm_ms = e0.elapsed_time(e1) / 5
+    fmm_err = float((uf - u).abs().max() / u.abs().max())
     potential = {"points": npt, "densities": R, "sources": nsrc, "ms": pot_ms,
                  "pair_density_evals_per_s": npt * nsrc * R / (pot_ms * 1e-3),
-                 "kernel_evals_per_s": npt * nsrc * ((R + 15) // 16) / (pot_ms * 1e-3)}
+                 "kernel_evals_per_s": npt * nsrc * ((R + 15) // 16) / (pot_ms * 1e-3),
+                 "interpolated": {"ms": fmm_ms, "far_terms": nf, "near_terms": nn, "speedup": pot_ms / fmm_ms,
+                                  "rel_err_vs_direct": fmm_err}}
     q2 = q * q
     flops = 2.0 * 128 * 128 * 64 * info.n_far                      # real-form GEMM per far block
     peak = 1912.6
@@ -505,7 +520,7 @@ def ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     stream = torch.cuda.Stream()
-    if args.config3_only:
+    if args.helmholtz_many_only:
         out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
         if rank == 0:
             print(json.dumps({"helmholtz_64rhs": out}), flush=True)
@@ -667,7 +682,7 @@ def ours(args, rank, world, local_rank):
                            "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}
 
     # ---- Helmholtz, 64 plane waves: tensor-core coupling ----
-    config3 = None if args.no_config3 else helmholtz_many_rhs(ibem, stream, world, barrier, args)
+    helm_many = None if args.no_helmholtz_many else helmholtz_many_rhs(ibem, stream, world, barrier, args)
 
     # ---- many uneven instances in one application ----
     batched = None if args.no_batch else batched_instances(ibem, stream, args)
@@ -698,7 +713,7 @@ def ours(args, rank, world, local_rank):
             "solve": solve,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "helmholtz_64rhs": config3,
+            "helmholtz_64rhs": helm_many,
             "learned_preconditioner": learned,
             "batched_instances": batched,
             "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,

@@ -201,6 +201,31 @@ ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int n
 ibem_status ibem_potential(ibem_handle* h, const double* w_dev, int nrhs,
                            const double* pts_dev, int64_t npts, double* u_dev);
 
+/* The same potential with the far field interpolated (Sec. 4.2 applied to
+ * Eq. repform).  Per point the cluster tree is walked from the patch roots: a
+ * cluster tau with eta * diam(tau) < max(0, |x - c_tau| - r_tau) (the point as a
+ * ball of radius 0 in Def. 4.1; c, r the cluster's bounding ball) contributes
+ * sum_b u*(x, F(z_b)) k(z_b) x^_tau[b] from the density's forward moments
+ * x^_tau (the q x q Chebyshev points z_b of the handle), an element that is
+ * never admissible contributes its n x n Gauss sum as in ibem_potential, any
+ * other cluster is split into its four children.  Same arguments, layouts and
+ * units as ibem_potential; needs a compressed handle (q_cheb > 0; IBEM_ERR_ARG
+ * otherwise), not the assembled operator.  The error against ibem_potential is
+ * the interpolation error of the kernel on admissible clusters (it falls
+ * geometrically in q).  Builds per-point interaction lists on the device, with
+ * one host synchronisation to size them, and forms the moments of the clusters
+ * the lists use only; temporary device memory (released on the stream): the
+ * lists, the moments (8 q^2 bytes per used cluster and real density vector;
+ * complex densities count twice), the split complex densities and, when some
+ * element is near a point, the lifted densities (8 ndof_super bytes per real
+ * vector).  The first call also builds the handle's 1D moment tables.  n_far_terms and
+ * n_near_terms (may be null) receive the total number of (point, cluster) and
+ * (point, element) terms.  A device-side overflow of the fixed traversal stack
+ * (not reachable for m <= 10) records IBEM_DEVICE_OVERFLOW in the status word. */
+ibem_status ibem_potential_fmm(ibem_handle* h, const double* w_dev, int nrhs,
+                               const double* pts_dev, int64_t npts, double* u_dev,
+                               int64_t* n_far_terms, int64_t* n_near_terms);
+
 /* Per-phase timing of operator applications (tracing).  Phases: 0 lift (T^T),
  * 1 upward pass (leaf moments, M2M), 2 far-field coupling, 3 downward pass
  * (L2L, back-projection), 4 near-field product, 5 restriction (T).  While
@@ -225,7 +250,9 @@ ibem_status ibem_profile_read(ibem_handle* h, ibem_profile_data* out);
  * for its copies in flight and return without finishing its output, so the
  * CUDA context stays usable.  limit = 0 makes every such wait fail at once
  * (used to test the failure path). */
-enum { IBEM_DEVICE_OK = 0, IBEM_DEVICE_TIMEOUT = 1 };
+enum { IBEM_DEVICE_OK = 0, IBEM_DEVICE_TIMEOUT = 1,
+       IBEM_DEVICE_OVERFLOW = 2   /* a fixed-size device work list would have
+                                     overflowed; the kernel stopped that item */ };
 ibem_status ibem_set_wait_limit(ibem_handle* h, long long limit);
 
 /* Synchronise the stream, return the status word (IBEM_DEVICE_* bits) that the

@@ -93,7 +93,7 @@ std::vector<double> bezier_extraction(int p, int m) {
 
 void free_handle(ibem_handle* h) {
     void* ptrs[] = {h->d_patches, h->d_knots, h->d_cpw, h->d_ext, h->d_qgeo, h->d_igeo, h->d_igeo32, h->d_phi,
-                    h->d_phi_sub, h->d_rule[0], h->d_rule[1], h->d_rule[2], h->d_M, h->d_S, h->d_near_ptr,
+                    h->d_phi_sub, h->d_rule[0], h->d_rule[1], h->d_rule[2], h->d_M, h->d_S, h->d_balls, h->d_mu1d, h->d_mu1d_off, h->d_near_ptr,
                     h->d_near_src, h->d_near_tgt, h->d_near_cls, h->d_near_orient, h->d_pairs_by_cls[0],
                     h->d_pairs_by_cls[1], h->d_pairs_by_cls[2], h->d_pairs_by_cls[3], h->d_pairs_by_cls[4],
                     h->d_near, h->d_near32, h->d_far_ptr, h->d_far_src, h->d_far_tgt, h->d_K, h->d_Kdf, h->d_xh2, h->d_far_rows,
@@ -272,6 +272,7 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
             }
         TRY(upload(&h->d_M, M, st), "upload M");
         TRY(upload(&h->d_S, S, st), "upload S");
+        TRY(upload(&h->d_balls, P.balls, st), "upload cluster balls");
         std::vector<float> Mf(M.begin(), M.end()), Sf(S.begin(), S.end());
         TRY(upload(&h->d_Mf, Mf, st), "upload Mf");
         TRY(upload(&h->d_Sf, Sf, st), "upload Sf");
@@ -620,6 +621,22 @@ ibem_status ibem_potential(ibem_handle* h, const double* w_dev, int nrhs, const 
     cudaError_t e;
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
     if ((e = launch_potential(h, w_dev, nrhs, pts_dev, npts, u_dev))) return cuda_fail(h, e, "potential");
+    return IBEM_OK;
+}
+
+ibem_status ibem_potential_fmm(ibem_handle* h, const double* w_dev, int nrhs, const double* pts_dev, int64_t npts,
+                               double* u_dev, int64_t* n_far_terms, int64_t* n_near_terms) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (nrhs < 0 || npts < 0 || (nrhs > 0 && npts > 0 && (!w_dev || !pts_dev || !u_dev)))
+        return fail(h, IBEM_ERR_ARG, "bad potential arguments");
+    if (h->P.q == 0) return fail(h, IBEM_ERR_ARG, "ibem_potential_fmm needs a compressed handle (q_cheb > 0)");
+    if (n_far_terms) *n_far_terms = 0;
+    if (n_near_terms) *n_near_terms = 0;
+    if (nrhs == 0 || npts == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = launch_potential_fmm(h, w_dev, nrhs, pts_dev, npts, u_dev, n_far_terms, n_near_terms)))
+        return cuda_fail(h, e, "potential_fmm");
     return IBEM_OK;
 }
 

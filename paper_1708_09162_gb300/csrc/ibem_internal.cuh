@@ -245,6 +245,8 @@ struct Plan {
     std::vector<int64_t> far_ptr;
     std::vector<int32_t> far_src;
     int64_t n_near = 0, n_far = 0, n_cls[5] = {0, 0, 0, 0, 0};
+    // bounding ball of every cluster, [C][4] = (centre x, y, z, radius)
+    std::vector<double> balls;
 };
 
 std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params* prm, Plan& P);
@@ -278,6 +280,9 @@ struct ibem_handle {
     double* d_ext = nullptr;        // Bezier extraction [ne1][pp][pp]: b_{ix+r} = sum_i ext[ix][r][i] B_i
     double* d_qgeo = nullptr;       // [E][Q*Q][4] = (x, y, z, gauss weight * k * h^2)
     double* d_igeo = nullptr;       // [C][q2][4]  = (x, y, z, k) at interpolation points
+    double* d_balls = nullptr;      // [C][4] cluster bounding balls (centre, radius)
+    double* d_mu1d = nullptr;       // 1D cluster moment tables of every level (interpolated potential)
+    int64_t* d_mu1d_off = nullptr;  // their offsets per level
     float* d_igeo32 = nullptr;      // same in FP32
     double* d_phi = nullptr;        // [Q*Q][nb] Bernstein products at the regular Gauss points
     double* d_phi_sub = nullptr;    // [4][Q*Q][nb] at the 2x2-subdivided Gauss points
@@ -413,6 +418,10 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
 cudaError_t helm_launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b, double* gsplit, double* bsplit);
 cudaError_t helm_launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                                   double* u, double* wsplit);
+__global__ void helm_split_vec_kernel(int R, int64_t n, const double* __restrict__ in, double* __restrict__ out);
+// potential_fmm.cu
+cudaError_t launch_potential_fmm(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
+                                 double* u, int64_t* n_far_terms, int64_t* n_near_terms);
 // kernels_*.cu entry points (launch on h->stream; return cudaError_t)
 cudaError_t launch_geometry_tables(ibem_handle* h);
 cudaError_t launch_near_assembly(ibem_handle* h);

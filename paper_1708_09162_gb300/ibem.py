@@ -30,6 +30,7 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_rhs", "ibem_matvec", "ibem_matvec_host", "ibem_solve", "ibem_potential",
             "ibem_block_tree", "ibem_last_error", "ibem_status_string", "ibem_profile_enable",
             "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc",
+            "ibem_potential_fmm",
             "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy",
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
@@ -94,6 +95,7 @@ def _load():
         "ibem_solve": (I32, [P, P, P, I32, ctypes.c_double, I32, I32, I32, ctypes.POINTER(ibem_solve_info)]),
         "ibem_potential": (I32, [P, P, I32, P, I64, P]),
         "ibem_potential_noalloc": (I32, [P, P, I32, P, I64, P]),
+        "ibem_potential_fmm": (I32, [P, P, I32, P, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "ibem_block_tree": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
                                   ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
         "ibem_profile_enable": (I32, [P, I32]),
@@ -263,6 +265,14 @@ def ibem_potential(h, w, nrhs, pts, u):
     _check(_lib.ibem_potential(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
 
 
+def ibem_potential_fmm(h, w, nrhs, pts, u):
+    """Potential with the interpolated far field; returns (far terms, near terms)."""
+    nf, nn = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.ibem_potential_fmm(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u), ctypes.byref(nf),
+                                   ctypes.byref(nn)), h)
+    return nf.value, nn.value
+
+
 def ibem_potential_noalloc(h, w, nrhs, pts, u):
     """ibem_potential without device allocation (fixed scratch inside libibem)."""
     _check(_lib.ibem_potential_noalloc(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
@@ -293,7 +303,7 @@ def ibem_profile_read(h):
             "ms": {name: d.ms[i] for i, name in enumerate(PHASES)}}
 
 
-IBEM_DEVICE_OK, IBEM_DEVICE_TIMEOUT = 0, 1
+IBEM_DEVICE_OK, IBEM_DEVICE_TIMEOUT, IBEM_DEVICE_OVERFLOW = 0, 1, 2
 
 
 def ibem_set_wait_limit(h, limit):

@@ -17,7 +17,7 @@ def _x(n, r, seed):
     return np.random.default_rng(seed).normal(size=(r, n))
 
 
-def test_dense_matvec_config1(laplace_p2m2):
+def test_dense_matvec_p2_m2(laplace_p2m2):
     # p = 2, m = 2, no compression: y = A x with A the oracle's dense matrix
     disc, A = laplace_p2m2
     h = handle(2, 2, q=0)
@@ -67,7 +67,7 @@ def test_fmm_matvec_double_float_other_q(q):
     lib().ibem_destroy(h)
 
 
-def test_native_and_double_float_coupling_agree_config2():
+def test_native_and_double_float_coupling_agree_p3_m5():
     hd = handle(3, 5, q=6, fp64_coupling=0)
     x = _x(7350, 1, 19)
     yd = gpu_matvec(hd, x)
@@ -90,7 +90,7 @@ def test_fmm_rows_p3_m3():
     lib().ibem_destroy(h)
 
 
-def test_fmm_rows_config2_full_size():
+def test_fmm_rows_p3_m5_full_size():
     # the benchmark workload: p = 3, m = 5, q = 6, eta = 1.6 (7350 dofs)
     op = oracle_fmm(3, 5, 6, 1.6)
     h = handle(3, 5, q=6)
@@ -129,7 +129,7 @@ def test_multi_rhs_matches_columns_and_host_entry():
     ibem.ibem_destroy(h)
 
 
-def test_rhs_solve_potential_config1(laplace_p2m2):
+def test_rhs_solve_potential_p2_m2(laplace_p2m2):
     import torch
     from conftest import seeded_ball_points
     from oracle import solve
@@ -161,7 +161,7 @@ def test_rhs_solve_potential_config1(laplace_p2m2):
     ibem.ibem_destroy(h)
 
 
-def test_solve_config2_fp64_and_mixed():
+def test_solve_p3_m5_fp64_and_mixed():
     import torch
     ibem = lib()
     h = handle(3, 5, q=6)
@@ -240,7 +240,7 @@ def test_bounded_wait_failure_path_and_recovery():
     ibem.ibem_destroy(h)
 
 
-def test_block_jacobi_cg_config2():
+def test_block_jacobi_cg_p3_m5():
     # block-Jacobi CG (FP64 and mixed) reaches 1e-8 in fewer iterations than point Jacobi
     import torch
     ibem = lib()

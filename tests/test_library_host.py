@@ -63,6 +63,21 @@ def test_block_tree_equals_oracle_perturbed_sphere(ibem):
     assert sorted(map(tuple, plain.tolist())) != onear
 
 
+@pytest.mark.parametrize("name,p,m", [("torus", 2, 2), ("fichera", 1, 2)])
+def test_block_tree_equals_oracle_torus_fichera(ibem, name, p, m):
+    # rational biquadratic torus (16 patches) and Fichera cube (24 bilinear
+    # squares, re-entrant edges): touching classes across patches in every
+    # relative orientation, admissibility on non-spherical clusters
+    import shapes
+    from oracle import geometry
+    specs = getattr(shapes, name)()
+    near, far = ibem.ibem_block_tree(ibem.nurbs_patches(specs), ibem.make_params(p, m, q_cheb=6, eta=1.6))
+    onear, ofar = _oracle_lists([geometry.NurbsPatch(*sp) for sp in specs], p, m, 1.6)
+    assert sorted(map(tuple, near.tolist())) == onear
+    assert sorted(map(tuple, far.tolist())) == ofar
+    assert len(ofar) > 0 and {r[6] for r in onear} >= {0, 1, 2, 4}
+
+
 def test_block_tree_dense_mode_has_all_pairs(ibem):
     near, far = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(1, 1, q_cheb=0))
     assert far.shape[0] == 0 and near.shape[0] == 24 * 24
@@ -97,4 +112,11 @@ def test_invalid_arguments_rejected(ibem):
     with pytest.raises(ibem.IbemError) as ei:
         ibem.ibem_block_tree(bad, ibem.make_params(1, 1))
     assert "weights" in str(ei.value)
+    # quadrature orders whose near-field tables exceed one CTA's shared memory
+    ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(2, 1, gauss_regular=12))
+    for p, kern, Q in ((2, 0, 13), (4, 0, 12), (2, 1, 11)):
+        with pytest.raises(ibem.IbemError) as ei:
+            ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(p, 1, kernel=kern, kappa=1.0 * kern,
+                                                                        gauss_regular=Q))
+        assert "shared memory" in str(ei.value)
     assert ibem.ibem_status_string(5) == "IBEM_ERR_NOCONV"

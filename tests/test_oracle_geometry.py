@@ -119,3 +119,78 @@ def test_perturbed_sphere_image_corners_derivatives_area(sphere):
         _, Fu, Fv = pface.eval(U.ravel(), V.ravel())
         area += np.sum(W * geometry.surface_measure(Fu, Fv))
     assert abs(area - 4 * np.pi) < 1e-12
+
+
+def _nurbs(specs):
+    return [geometry.NurbsPatch(*s) for s in specs]
+
+
+def _area_and_volume(patches, m=3):
+    """Area sum_e sum_g w k and volume (1/3) int x . n dA by the 8 x 8 Gauss rule
+    per element (n = dF/du x dF/dv / k, so the sign follows the orientation)."""
+    from oracle.mesh import Mesh
+    from oracle import gauss
+    me = Mesh(patches, 0, m)
+    x, w = gauss.gauss_legendre(8)
+    st = np.array([(a, b) for b in x for a in x])
+    ww = np.outer(w, w).ravel()
+    area = vol = 0.0
+    for e in range(me.n_elements):
+        patch, _, _ = me.element(e)
+        uv = me.to_patch(e, st)
+        F, Fu, Fv = patches[patch].eval(uv[:, 0], uv[:, 1])
+        cr = np.cross(Fu, Fv)
+        area += np.sum(ww * np.linalg.norm(cr, axis=1)) * me.h ** 2
+        vol += np.sum(ww * np.sum(F * cr, axis=1)) * me.h ** 2 / 3.0
+    return area, vol
+
+
+def test_torus_patches():
+    # (|(x, y)| - 2)^2 + z^2 = 1/4 everywhere; area 4 pi^2 R r, volume
+    # 2 pi^2 R r^2 with outward normals; 16 patches meeting edge to edge
+    import shapes
+    pats = _nurbs(shapes.torus())
+    assert len(pats) == 16
+    rng = np.random.default_rng(13)
+    u, v = rng.random(200), rng.random(200)
+    for pt in pats:
+        F, _, _ = pt.eval(u, v)
+        np.testing.assert_allclose((np.hypot(F[:, 0], F[:, 1]) - 2.0) ** 2 + F[:, 2] ** 2, 0.25, atol=1e-14)
+    area, vol = _area_and_volume(pats)
+    assert abs(area - 4 * np.pi ** 2 * 2.0 * 0.5) < 1e-9
+    assert abs(vol - 2 * np.pi ** 2 * 2.0 * 0.25) < 1e-9
+    # every patch edge is shared with exactly one other patch's edge
+    edges = []
+    for pt in pats:
+        for uu, vv in (((0.5,), (0.0,)), ((0.5,), (1.0,)), ((0.0,), (0.5,)), ((1.0,), (0.5,))):
+            edges.append(pt.eval(uu, vv)[0][0])
+    E = np.array(edges)
+    d = np.linalg.norm(E[:, None, :] - E[None, :, :], axis=2)
+    assert np.all(np.sum(d < 1e-12, axis=1) == 2)
+
+
+def test_fichera_patches():
+    # 24 unit squares, area 24, volume 8 - 1 with outward normals
+    import shapes
+    pats = _nurbs(shapes.fichera())
+    assert len(pats) == 24
+    area, vol = _area_and_volume(pats, m=1)
+    assert abs(area - 24.0) < 1e-13
+    assert abs(vol - 7.0) < 1e-13
+    mids = np.array([pt.eval([0.5], [0.5])[0][0] for pt in pats])
+    assert len({tuple(np.round(mm, 12)) for mm in mids}) == 24
+    # no square lies on the removed corner's outer faces
+    for mm in mids:
+        assert not (np.max(mm) == 1.0 and np.all(mm >= 0.0))
+
+
+def test_dimensions_on_torus_and_fichera_meshes():
+    # n (2^m (p + 1))^2 superspace functions (Table tab::mat::sph) on the
+    # built meshes, n (2^m + p)^2 B-splines
+    import shapes
+    from oracle.mesh import Mesh
+    for specs, n in ((shapes.torus(), 16), (shapes.fichera(), 24)):
+        for p, m in ((0, 1), (2, 2), (4, 1)):
+            me = Mesh(_nurbs(specs), p, m)
+            assert me.n_elements * (p + 1) ** 2 == n * (2 ** m * (p + 1)) ** 2
+            assert me.n_dofs == n * (2 ** m + p) ** 2
