@@ -104,8 +104,14 @@ typedef struct {
     int q_cheb;          /* Chebyshev points per direction per cluster (2..12); 0 =
                             no compression: every element pair is near field        */
     double eta;          /* admissible iff eta * max(diam) < dist (eta = 1/mu, Def. 4.1) */
-    int gauss_regular;   /* Gauss points per direction, regular pairs (default 8)   */
-    int gauss_singular;  /* Gauss points per variable, Duffy rules (default 8)      */
+    int gauss_regular;   /* Gauss points per direction (1..40, default 8) of regular
+                            pairs, of each sub-square of near-singular pairs, of the
+                            right-hand side and of the potentials (Sec. 4 item 4:
+                            orders up to 40).  Above what a CTA can hold as a kernel
+                            matrix in shared memory (about 12 for Laplace, 10 for
+                            Helmholtz at p = 2) the near field is formed by a
+                            streaming kernel (same sums).                            */
+    int gauss_singular;  /* Gauss points per variable, Duffy rules (1..12, default 8) */
     int fp64_coupling;   /* storage and arithmetic of the FP64 operator's coupling:
                             IBEM_COUPLING_DF (0, default) or IBEM_COUPLING_NATIVE (1) */
 } ibem_params;

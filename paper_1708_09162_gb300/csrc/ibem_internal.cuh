@@ -13,6 +13,8 @@
 #define IBEM_MAX_DEG 7      // NURBS degree limit
 #define IBEM_MAX_P 4        // spline degree limit
 #define IBEM_MAX_NB 25      // (IBEM_MAX_P + 1)^2 Bernstein functions per element
+#define IBEM_MAX_GAUSS 40   // Gauss points per direction of the regular rule
+#define IBEM_MAX_SMEM_BYTES 232448   // dynamic shared memory one CTA may use (227 KB)
 #define IBEM_MAX_Q 12       // Chebyshev points per direction
 #define IBEM_PI 3.14159265358979323846
 
@@ -419,6 +421,11 @@ cudaError_t helm_launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b
 cudaError_t helm_launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                                   double* u, double* wsplit);
 __global__ void helm_split_vec_kernel(int R, int64_t n, const double* __restrict__ in, double* __restrict__ out);
+// near-field assembly (kernels_setup.cu): the streaming form of the regular and
+// subdivided pairs, used where the shared-matrix form needs more than
+// IBEM_MAX_SMEM_BYTES (near_shared_bytes) of shared memory
+cudaError_t launch_near_stream(ibem_handle* h, int cls, bool cplx, double kappa, double* blocks);
+size_t near_shared_bytes(int Q, int nb, bool cplx, bool subdiv);
 // potential_fmm.cu
 cudaError_t launch_potential_fmm(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                                  double* u, int64_t* n_far_terms, int64_t* n_near_terms);

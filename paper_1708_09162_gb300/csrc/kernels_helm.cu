@@ -19,7 +19,7 @@ namespace ibem {
 
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-__constant__ double c_hgx[16], c_hgw[16];
+__constant__ double c_hgx[IBEM_MAX_GAUSS], c_hgw[IBEM_MAX_GAUSS];
 
 __device__ inline void helm_elem(int64_t e, int ne1, int* patch, int* ix, int* iy) {
     int64_t per = (int64_t)ne1 * ne1;
@@ -707,13 +707,18 @@ cudaError_t helm_launch_near_assembly(ibem_handle* h) {
     if ((e = cudaMemcpyToSymbolAsync(c_hgx, gx.data(), P.Q * sizeof(double), 0, cudaMemcpyHostToDevice, h->stream))) return e;
     if ((e = cudaMemcpyToSymbolAsync(c_hgw, gw.data(), P.Q * sizeof(double), 0, cudaMemcpyHostToDevice, h->stream))) return e;
     double2* blocks = reinterpret_cast<double2*>(h->d_near);
-    if (P.n_cls[CLS_REGULAR] > 0) {
+    for (int cls : {CLS_REGULAR, CLS_SUBDIV}) {
+        if (P.n_cls[cls] > 0 && near_shared_bytes(P.Q, nb, true, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
+            (e = launch_near_stream(h, cls, true, kappa, h->d_near)))
+            return e;
+    }
+    if (P.n_cls[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, true, false) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(8 * QQ + 2 * QQ * QQ + 2 * QQ * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(helm_near_regular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
         helm_near_regular_kernel<<<(unsigned)P.n_cls[CLS_REGULAR], 128, sm, h->stream>>>(
             h->d_pairs_by_cls[CLS_REGULAR], h->d_near_tgt, h->d_near_src, h->d_qgeo, h->d_phi, QQ, nb, kappa, blocks);
     }
-    if (P.n_cls[CLS_SUBDIV] > 0) {
+    if (P.n_cls[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, true, true) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(32 * QQ + 2 * QQ * QQ + 2 * QQ * nb + 2 * nb * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(helm_near_subdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
         helm_near_subdiv_kernel<<<(unsigned)P.n_cls[CLS_SUBDIV], 128, sm, h->stream>>>(

@@ -20,7 +20,7 @@
 
 namespace ibem {
 
-__constant__ double c_gx[16], c_gw[16];    // regular Gauss rule on [0, 1]
+__constant__ double c_gx[IBEM_MAX_GAUSS], c_gw[IBEM_MAX_GAUSS];    // regular Gauss rule on [0, 1]
 __constant__ double c_cheb[IBEM_MAX_Q];     // Chebyshev nodes on [0, 1]
 __constant__ long long c_level_off[12];
 
@@ -184,6 +184,178 @@ __global__ void near_subdiv_kernel(GeomView g, const int32_t* __restrict__ list,
             __syncthreads();
         }
     for (int i = threadIdx.x; i < nb * nb; i += blockDim.x) blocks[k * nb * nb + i] = acc[i];
+}
+
+// ---- near field: regular and subdivided pairs, streaming form -------------
+// For Gauss orders whose Q^2 x Q^2 kernel matrix does not fit in shared memory
+// (the forms above keep it there).  One CTA of NS_T threads per pair; for each
+// pair of point sets (the elements themselves, or each of the 2 x 2 x 2 x 2
+// sub-square pairs) the CTA walks the target points in chunks of NS_T: thread t
+// forms H[a][j] = sum_b G(a, b) phi_B[b][j] for its target point a in
+// registers (G = w_a w_b u*(x_a, y_b), complex for Helmholtz), the chunk is
+// stored in shared memory, and the block entries B[r][j] += sum_a phi_A[a][r]
+// H[a][j] are accumulated by their owning threads (entry e = t + NS_T i).
+// The same sums as the shared-matrix forms, in the same order over b for each
+// H[a][j]; the sum over a runs chunk by chunk.  Shared: XA[QQ][4], XB[QQ][4],
+// H[NS_T][NB] (real and imaginary parts for Helmholtz).
+constexpr int NS_T = 128;
+
+template <bool CPLX, int NB>
+__global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int32_t* __restrict__ list,
+                                                           const int32_t* __restrict__ tgt,
+                                                           const int32_t* __restrict__ src,
+                                                           const double* __restrict__ qgeo,
+                                                           const double* __restrict__ phi, int Q, int ne1,
+                                                           bool subdiv, double kappa, double* __restrict__ blocks) {
+    extern __shared__ double sm[];
+    constexpr int CW = CPLX ? 2 : 1;
+    constexpr int NE = (NB * NB + NS_T - 1) / NS_T;     // block entries per thread
+    const int QQ = Q * Q;
+    double* XA = sm;
+    double* XB = XA + 4 * QQ;
+    double* Hr = XB + 4 * QQ;
+    double* Hi = Hr + NS_T * NB;
+    const int64_t k = list[blockIdx.x];
+    const int64_t t = tgt[k], s = src[k];
+    const double h = 1.0 / ne1;
+    const double inv4pi = 1.0 / (4.0 * IBEM_PI);
+    double acc[NE][CW];
+#pragma unroll
+    for (int i = 0; i < NE; ++i)
+#pragma unroll
+        for (int c = 0; c < CW; ++c) acc[i][c] = 0.0;
+    const int nsub = subdiv ? 4 : 1;
+    for (int sa = 0; sa < nsub; ++sa)
+        for (int sb = 0; sb < nsub; ++sb) {
+            __syncthreads();   // the previous pass is done with XA, XB and H
+            for (int i = threadIdx.x; i < 2 * QQ; i += NS_T) {
+                const int which = i / QQ, gq = i % QQ;
+                double* o = (which ? XB : XA) + 4 * gq;
+                if (!subdiv) {
+                    const double* in = qgeo + 4 * (QQ * (which ? s : t) + gq);
+                    o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = in[3];
+                } else {
+                    const int sub = which ? sb : sa;
+                    int patch, ix, iy;
+                    dev_element_of(which ? s : t, ne1, &patch, &ix, &iy);
+                    const double su = 0.5 * (sub & 1) + 0.5 * c_gx[gq % Q];
+                    const double sv = 0.5 * (sub >> 1) + 0.5 * c_gx[gq / Q];
+                    double F[3], Fu[3], Fv[3];
+                    eval_patch(g, patch, (ix + su) * h, (iy + sv) * h, F, Fu, Fv);
+                    o[0] = F[0]; o[1] = F[1]; o[2] = F[2];
+                    o[3] = 0.25 * c_gw[gq % Q] * c_gw[gq / Q] * surface_measure(Fu, Fv) * h * h;
+                }
+            }
+            __syncthreads();
+            const double* pA = phi + (size_t)(subdiv ? sa : 0) * QQ * NB;
+            const double* pB = phi + (size_t)(subdiv ? sb : 0) * QQ * NB;
+            for (int a0 = 0; a0 < QQ; a0 += NS_T) {
+                const int a = a0 + threadIdx.x;
+                double hr[NB], hi[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) hr[j] = hi[j] = 0.0;
+                if (a < QQ) {
+                    const double xa0 = XA[4 * a], xa1 = XA[4 * a + 1], xa2 = XA[4 * a + 2], wa = XA[4 * a + 3];
+                    for (int b = 0; b < QQ; ++b) {
+                        const double d0 = xa0 - XB[4 * b], d1 = xa1 - XB[4 * b + 1], d2 = xa2 - XB[4 * b + 2];
+                        const double r = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                        double gr, gi = 0.0;
+                        if constexpr (CPLX) {
+                            double sn, cs;
+                            sincos(kappa * r, &sn, &cs);
+                            const double f = wa * XB[4 * b + 3] / (4.0 * IBEM_PI * r);
+                            gr = f * cs;
+                            gi = f * sn;
+                        } else {
+                            gr = wa * XB[4 * b + 3] * inv4pi / r;
+                        }
+                        const double* pb = pB + (size_t)b * NB;
+#pragma unroll
+                        for (int j = 0; j < NB; ++j) {
+                            hr[j] += gr * pb[j];
+                            if constexpr (CPLX) hi[j] += gi * pb[j];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    Hr[threadIdx.x * NB + j] = hr[j];
+                    if constexpr (CPLX) Hi[threadIdx.x * NB + j] = hi[j];
+                }
+                __syncthreads();
+                const int na = QQ - a0 < NS_T ? QQ - a0 : NS_T;
+#pragma unroll
+                for (int i = 0; i < NE; ++i) {
+                    const int e = threadIdx.x + NS_T * i;
+                    if (e < NB * NB) {
+                        const int r = e / NB, j = e % NB;
+                        double vr = 0.0, vi = 0.0;
+                        for (int aa = 0; aa < na; ++aa) {
+                            const double pa = pA[(size_t)(a0 + aa) * NB + r];
+                            vr += pa * Hr[aa * NB + j];
+                            if constexpr (CPLX) vi += pa * Hi[aa * NB + j];
+                        }
+                        acc[i][0] += vr;
+                        if constexpr (CPLX) acc[i][CW - 1] += vi;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+        const int e = threadIdx.x + NS_T * i;
+        if (e < NB * NB)
+#pragma unroll
+            for (int c = 0; c < CW; ++c) blocks[(k * NB * NB + e) * CW + c] = acc[i][c];
+    }
+}
+
+template <bool CPLX>
+cudaError_t launch_near_stream_t(ibem_handle* h, int cls, double kappa, double* blocks) {
+    Plan& P = h->P;
+    GeomView g{h->d_patches, h->d_knots, h->d_cpw};
+    const bool subdiv = cls == CLS_SUBDIV;
+    const int QQ = P.Q * P.Q;
+    const size_t sm = (size_t)(8 * QQ + (CPLX ? 2 : 1) * NS_T * P.nb) * sizeof(double);
+    const double* phi = subdiv ? h->d_phi_sub : h->d_phi;
+    const unsigned n = (unsigned)P.n_cls[cls];
+    cudaError_t e;
+#define IBEM_NS_CASE(NB_)                                                                                      \
+    case NB_:                                                                                                  \
+        if ((e = cudaFuncSetAttribute(near_stream_kernel<CPLX, NB_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                      (int)sm)))                                                                \
+            return e;                                                                                          \
+        near_stream_kernel<CPLX, NB_><<<n, NS_T, sm, h->stream>>>(g, h->d_pairs_by_cls[cls], h->d_near_tgt,     \
+                                                                  h->d_near_src, h->d_qgeo, phi, P.Q, P.ne1,    \
+                                                                  subdiv, kappa, blocks);                       \
+        break;
+    switch (P.nb) {
+        IBEM_NS_CASE(1)
+        IBEM_NS_CASE(4)
+        IBEM_NS_CASE(9)
+        IBEM_NS_CASE(16)
+        IBEM_NS_CASE(25)
+        default: return cudaErrorInvalidValue;
+    }
+#undef IBEM_NS_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_stream(ibem_handle* h, int cls, bool cplx, double kappa, double* blocks) {
+    cudaError_t e;
+    std::vector<double> gx, gw;
+    gauss_legendre(h->P.Q, gx, gw);
+    if ((e = cudaMemcpyToSymbolAsync(c_gx, gx.data(), h->P.Q * sizeof(double), 0, cudaMemcpyHostToDevice, h->stream)) ||
+        (e = cudaMemcpyToSymbolAsync(c_gw, gw.data(), h->P.Q * sizeof(double), 0, cudaMemcpyHostToDevice, h->stream)))
+        return e;
+    return cplx ? launch_near_stream_t<true>(h, cls, kappa, blocks) : launch_near_stream_t<false>(h, cls, kappa, blocks);
+}
+
+size_t near_shared_bytes(int Q, int nb, bool cplx, bool subdiv) {
+    const size_t QQ = (size_t)Q * Q, cw = cplx ? 2 : 1;
+    return (subdiv ? 32 * QQ + cw * QQ * QQ + cw * QQ * nb + cw * nb * nb : 8 * QQ + cw * QQ * QQ + cw * QQ * nb) *
+           sizeof(double);
 }
 
 // ---- near field: touching pairs (Duffy-type rules) -------------------------
@@ -366,15 +538,30 @@ cudaError_t launch_near_assembly(ibem_handle* h) {
     GeomView g{h->d_patches, h->d_knots, h->d_cpw};
     int QQ = P.Q * P.Q, nb = P.nb;
     cudaError_t e;
+    // the Gauss rule is module-wide: load this handle's before the subdivided pairs use it
+    {
+        std::vector<double> gx, gw;
+        gauss_legendre(P.Q, gx, gw);
+        if ((e = cudaMemcpyToSymbolAsync(c_gx, gx.data(), P.Q * sizeof(double), 0, cudaMemcpyHostToDevice,
+                                         h->stream)) ||
+            (e = cudaMemcpyToSymbolAsync(c_gw, gw.data(), P.Q * sizeof(double), 0, cudaMemcpyHostToDevice,
+                                         h->stream)))
+            return e;
+    }
+    for (int cls : {CLS_REGULAR, CLS_SUBDIV}) {
+        if (P.n_cls[cls] > 0 && near_shared_bytes(P.Q, nb, false, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
+            (e = launch_near_stream(h, cls, false, 0.0, h->d_near)))
+            return e;
+    }
     // regular
-    if (P.n_cls[CLS_REGULAR] > 0) {
+    if (P.n_cls[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, false, false) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(8 * QQ + QQ * QQ + QQ * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(near_regular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
         near_regular_kernel<<<(unsigned)P.n_cls[CLS_REGULAR], 128, sm, h->stream>>>(
             h->d_pairs_by_cls[CLS_REGULAR], P.n_cls[CLS_REGULAR], h->d_near_tgt, h->d_near_src, h->d_qgeo,
             h->d_phi, QQ, nb, h->d_near);
     }
-    if (P.n_cls[CLS_SUBDIV] > 0) {
+    if (P.n_cls[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, false, true) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(32 * QQ + QQ * QQ + QQ * nb + nb * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(near_subdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
         near_subdiv_kernel<<<(unsigned)P.n_cls[CLS_SUBDIV], 128, sm, h->stream>>>(

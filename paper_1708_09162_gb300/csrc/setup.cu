@@ -221,19 +221,8 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.m < 0 || q.m > 10) return "m must be in 0..10";
     if (q.q_cheb != 0 && (q.q_cheb < 2 || q.q_cheb > IBEM_MAX_Q)) return "q_cheb must be 0 or 2..12";
     if (q.q_cheb != 0 && !(q.eta > 0.0)) return "eta must be > 0";
-    if (q.gauss_regular < 1 || q.gauss_regular > 16) return "gauss_regular must be in 1..16";
+    if (q.gauss_regular < 1 || q.gauss_regular > IBEM_MAX_GAUSS) return "gauss_regular must be in 1..40";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
-    {
-        // the near-field assembly keeps a pair's kernel values and basis tables in
-        // shared memory (regular and 2 x 2-subdivided pairs); refuse what no CTA can hold
-        const int64_t QQ = (int64_t)q.gauss_regular * q.gauss_regular, nb = (int64_t)(q.p + 1) * (q.p + 1);
-        const int64_t cw = q.kernel == IBEM_HELMHOLTZ ? 2 : 1;
-        const int64_t reg = 8 * QQ + cw * QQ * QQ + cw * QQ * nb;
-        const int64_t sub = 32 * QQ + cw * QQ * QQ + cw * QQ * nb + cw * nb * nb;
-        if ((reg > sub ? reg : sub) * (int64_t)sizeof(double) > 232448)
-            return "gauss_regular too large: the near-field assembly needs more than 227 KB of shared memory at "
-                   "this degree and kernel";
-    }
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
         q.fp64_coupling != IBEM_COUPLING_NONE)
         return "fp64_coupling must be IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE or IBEM_COUPLING_NONE";

@@ -112,11 +112,9 @@ def test_invalid_arguments_rejected(ibem):
     with pytest.raises(ibem.IbemError) as ei:
         ibem.ibem_block_tree(bad, ibem.make_params(1, 1))
     assert "weights" in str(ei.value)
-    # quadrature orders whose near-field tables exceed one CTA's shared memory
-    ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(2, 1, gauss_regular=12))
-    for p, kern, Q in ((2, 0, 13), (4, 0, 12), (2, 1, 11)):
-        with pytest.raises(ibem.IbemError) as ei:
-            ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(p, 1, kernel=kern, kappa=1.0 * kern,
-                                                                        gauss_regular=Q))
-        assert "shared memory" in str(ei.value)
+    # regular Gauss orders up to 40 per direction (Sec. 4 item 4)
+    ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(4, 1, kernel=1, kappa=1.0, gauss_regular=40))
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(2, 1, gauss_regular=41))
+    assert "gauss_regular" in str(ei.value)
     assert ibem.ibem_status_string(5) == "IBEM_ERR_NOCONV"
