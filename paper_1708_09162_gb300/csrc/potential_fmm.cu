@@ -154,9 +154,9 @@ __device__ __forceinline__ void pf_kernel_value(double d, double kappa, double* 
 // One CTA per (point, chunk of PF_RC densities).  Far terms: entries (cluster,
 // interpolation point b) of the point's list, flattened over the CTA's
 // threads; the moments of R densities (complex: 2 R real vectors, real part
-// first) are [R][n_used][q2], cluster c at row slot[c].  Near terms: entries (element, Gauss point); the
-// density at a Gauss point is sum_i phi[g][i] x*_e[i] from the lifted
-// coefficients xs [R][E][nb].
+// first) are [R][n_used][q2], cluster c at row slot[c].  Near terms: entries
+// (element, Gauss point); the density at a Gauss point is
+// sum_i phi[g][i] x*_e[i] from the lifted coefficients xs [R][E][nb].
 template <bool CPLX>
 __global__ void __launch_bounds__(PF_T) pf_eval_kernel(
     int64_t npts, const double* __restrict__ pts, int R, const int64_t* __restrict__ far_off,
