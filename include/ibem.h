@@ -228,7 +228,7 @@ ibem_status ibem_potential(ibem_handle* h, const double* w_dev, int nrhs,
  * n_near_terms (may be null) receive the total number of (point, cluster) and
  * (point, element) terms.  A device-side overflow of the fixed traversal stack
  * (not reachable for m <= 10) records IBEM_DEVICE_OVERFLOW in the status word.
- * At most 2^31 - 1 points and 1,048,560 densities per call (IBEM_ERR_ARG). */
+ * At most 2^31 - 1 points and 262,140 densities per call (IBEM_ERR_ARG). */
 ibem_status ibem_potential_fmm(ibem_handle* h, const double* w_dev, int nrhs,
                                const double* pts_dev, int64_t npts, double* u_dev,
                                int64_t* n_far_terms, int64_t* n_near_terms);

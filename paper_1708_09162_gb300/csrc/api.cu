@@ -630,8 +630,8 @@ ibem_status ibem_potential_fmm(ibem_handle* h, const double* w_dev, int nrhs, co
     if (nrhs < 0 || npts < 0 || (nrhs > 0 && npts > 0 && (!w_dev || !pts_dev || !u_dev)))
         return fail(h, IBEM_ERR_ARG, "bad potential arguments");
     if (h->P.q == 0) return fail(h, IBEM_ERR_ARG, "ibem_potential_fmm needs a compressed handle (q_cheb > 0)");
-    if (npts > 2147483647LL || nrhs > 65535 * 16)
-        return fail(h, IBEM_ERR_ARG, "ibem_potential_fmm takes at most 2^31 - 1 points and 1,048,560 densities");
+    if (npts > 2147483647LL || nrhs > 262140)   // grid.x = points; grid.y of the moments = 2 nrhs / 8 <= 65535
+        return fail(h, IBEM_ERR_ARG, "ibem_potential_fmm takes at most 2^31 - 1 points and 262,140 densities");
     if (n_far_terms) *n_far_terms = 0;
     if (n_near_terms) *n_near_terms = 0;
     if (nrhs == 0 || npts == 0) return IBEM_OK;
