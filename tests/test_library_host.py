@@ -118,3 +118,33 @@ def test_invalid_arguments_rejected(ibem):
         ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(2, 1, gauss_regular=41))
     assert "gauss_regular" in str(ei.value)
     assert ibem.ibem_status_string(5) == "IBEM_ERR_NOCONV"
+
+
+def test_block_tree_partitions_every_element_pair(ibem):
+    # near element pairs plus the leaves of the far cluster pairs cover every
+    # (target, source) element pair exactly once, for random eta on the four
+    # geometries (the library's host tree alone, no oracle)
+    import shapes
+    rng = np.random.default_rng(97)
+    geos = [(ibem.sphere_patches(), 6), (ibem.sphere_patches(perturbed=True), 6),
+            (ibem.nurbs_patches(shapes.torus()), 16), (ibem.nurbs_patches(shapes.fichera()), 24)]
+    for pats, npatch in geos:
+        for m in (1, 2):
+            eta = float(rng.uniform(0.3, 3.0))
+            near, far = ibem.ibem_block_tree(pats, ibem.make_params(1, m, q_cheb=4, eta=eta))
+            n1 = 2 ** m
+            E = npatch * n1 * n1
+            cover = np.zeros((E, E), dtype=np.int32)
+            eid = lambda pa, ix, iy: (pa * n1 + iy) * n1 + ix
+            for r in near:
+                cover[eid(r[0], r[1], r[2]), eid(r[3], r[4], r[5])] += 1
+            for r in far:
+                s = 2 ** (m - r[1])
+                ia = [eid(r[0], r[2] * s + dx, r[3] * s + dy) for dy in range(s) for dx in range(s)]
+                t = 2 ** (m - r[5])
+                ib = [eid(r[4], r[6] * t + dx, r[7] * t + dy) for dy in range(t) for dx in range(t)]
+                cover[np.ix_(ia, ib)] += 1
+            assert np.all(cover == 1), (npatch, m, eta)
+            # identical pairs are near and classed as such
+            diag = near[(near[:, 0] == near[:, 3]) & (near[:, 1] == near[:, 4]) & (near[:, 2] == near[:, 5])]
+            assert len(diag) == E and np.all(diag[:, 6] == 0)
