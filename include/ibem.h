@@ -282,7 +282,10 @@ ibem_status ibem_device_status(ibem_handle* h, int* status);
  * calls whose GPU work can overlap (different streams or handles on one device
  * without ordering between them) race on it and must be serialised by the
  * caller.  The output u_dev is cleared by the call.  Laplace handles only
- * (a Helmholtz handle gets IBEM_ERR_ARG). */
+ * (a Helmholtz handle gets IBEM_ERR_ARG).  The looked-up address is kept for
+ * the life of the process: after a device reset (cudaDeviceReset), which also
+ * invalidates every handle on that device, do not call this entry point
+ * again in the same process. */
 #define IBEM_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_dev, int nrhs,
                                    const double* pts_dev, int64_t npts, double* u_dev);

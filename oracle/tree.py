@@ -19,7 +19,8 @@ its far/near sentence is garbled):
 Clusters are identified by (patch, level, ix, iy).
 
 Pinned by: near and far blocks partition all element pairs exactly once, every
-far block is admissible with a non-admissible parent (tests/test_oracle_tree.py).
+far block is admissible with a non-admissible parent
+(tests/test_oracle_fmm.py::test_block_tree_partitions_all_element_pairs).
 """
 import numpy as np
 

@@ -31,6 +31,18 @@ def test_noalloc_potential_matches_allocating_entry_twice():
         torch.cuda.synchronize()
         assert rel_err(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-12
     ibem.ibem_destroy(h)
+    # the property the entry point exists for: a fresh handle (no work vectors
+    # yet) evaluates potentials without the device's free memory changing
+    h2 = handle(3, 4, q=6, assemble=False)
+    u = torch.empty((2, 150), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        ibem.ibem_potential_noalloc(h2, w, 2, pts, u)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert rel_err(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-12
+    ibem.ibem_destroy(h2)
 
 
 def test_noalloc_potential_refuses_oversized_discretisation():
