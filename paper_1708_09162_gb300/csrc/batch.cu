@@ -231,8 +231,12 @@ __global__ void b_coupling_kernel(const BatchInst* __restrict__ B, int n, const 
                     const float rinv = rsqrtf(r2);
                     const float w = y.w * rinv;
                     if (cw == 2) {
+                        // phase reduced to [-pi, pi] first: the hardware sine and
+                        // cosine are accurate on that interval only
+                        float ph = I.kappa * (r2 * rinv);
+                        ph = fmaf(-6.283185307179586f, rintf(ph * 0.15915494309189535f), ph);
                         float sn, cs;
-                        __sincosf(I.kappa * (r2 * rinv), &sn, &cs);
+                        __sincosf(ph, &sn, &cs);
                         const float kr = w * cs, ki = w * sn;
 #pragma unroll
                         for (int j = 0; j < BC_RB; ++j) {

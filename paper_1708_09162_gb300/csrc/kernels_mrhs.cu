@@ -330,10 +330,12 @@ __global__ void __launch_bounds__(544) mr_coupling_tc_kernel(
                     const float rinv = rsqrtf(r2);
                     const float w = X.w * Yb.w * rinv;          // X.w holds k / (4 pi)
                     if constexpr (CPLX) {
-                        // |kappa r| stays within a few periods here; the hardware sine
-                        // and cosine are accurate far below the BF16 rounding of K
+                        // phase reduced to [-pi, pi] first (the hardware sine and
+                        // cosine are accurate on that interval only)
+                        float ph = kappa * (r2 * rinv);
+                        ph = fmaf(-6.283185307179586f, rintf(ph * 0.15915494309189535f), ph);
                         float sn, cs;
-                        __sincosf(kappa * (r2 * rinv), &sn, &cs);
+                        __sincosf(ph, &sn, &cs);
                         wr[u] = w * cs;
                         wi[u] = w * sn;
                     } else {
