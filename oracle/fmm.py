@@ -220,12 +220,20 @@ class FMMOperator:
         return u
 
     def rows(self, rows, x):
-        """Selected rows of the FMM operator applied to x (exact per row)."""
+        """Selected rows of the FMM operator applied to x (exact per row).  The
+        moments x^_t are formed only for the source clusters these rows use, by
+        the same formula as ``forward_moments``."""
         me = self.mesh
         x2 = x.reshape(me.n_dofs, -1)
         dt = np.result_type(x2, np.complex128 if self.disc.kernel.is_complex else np.float64)
         out = np.zeros((len(rows), x2.shape[1]), dtype=dt)
-        xh = self.forward_moments(x2)
+        xh = {}
+
+        def moments(t):
+            if t not in xh:
+                xh[t] = self.cluster_moments(x2, t)
+            return xh[t]
+
         n1 = me.n1
         for r, i in enumerate(rows):
             patch, rem = divmod(int(i), n1 * n1)
@@ -248,7 +256,7 @@ class FMMOperator:
                         targets = self.far_by_target.get(s, [])
                         if not targets:
                             continue
-                        yh = sum(self.coupling(s, t) @ xh[t] for t in targets)
+                        yh = sum(self.coupling(s, t) @ moments(t) for t in targets)
                         mrow = np.outer(self.moments_1d(level, cy)[jv],
                                         self.moments_1d(level, cx)[ju]).ravel()
                         out[r] += mrow @ yh
