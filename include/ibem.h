@@ -124,10 +124,19 @@ typedef struct {
  * generates the coupling on the fly in FP64 (also chosen automatically when the
  * stored complex matrices would exceed half of the free device memory).  All
  * variants reproduce the FP64 oracle to 1e-12. */
-enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2 };
+enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, IBEM_COUPLING_GENERATE = 3 };
 /* IBEM_COUPLING_NONE stores no FP64 coupling matrices (memory for large
  * batches): the FP32 operator is available; the FP64 operator of a Laplace
- * handle then returns IBEM_ERR_STATE, Helmholtz generates it on the fly. */
+ * handle then returns IBEM_ERR_STATE, Helmholtz generates it on the fly.
+ * IBEM_COUPLING_GENERATE (Helmholtz): nothing is stored; every application
+ * generates each far block once in double-float arithmetic (kernel values to
+ * about 1e-13 relative) and applies it to all right-hand sides of the call
+ * (chunks of up to 64), so the cost of the generation is shared by them.  This
+ * is also what a Helmholtz handle with IBEM_COUPLING_DF or NONE does when the
+ * stored matrices would not fit, for q <= 8 and a phase kappa |x - y| below
+ * 90 on every far block;
+ * otherwise the generation runs in native FP64 per right-hand side.  A Laplace
+ * handle treats GENERATE like IBEM_COUPLING_DF. */
 
 typedef struct {
     int64_t ndof;          /* dim S_{p,m} = n (2^m + p)^2                          */
@@ -144,10 +153,13 @@ typedef struct {
 } ibem_info;
 
 typedef struct {
-    int iterations;        /* Krylov iterations (inner iterations for mixed)       */
-    int outer;             /* iterative-refinement sweeps (mixed), else 1          */
-    double rel_residual;   /* |b - A w| / |b| with the FP64 operator, recomputed   */
+    int iterations;        /* Krylov iterations, summed over the right-hand sides  */
+    int outer;             /* restarts / iterative-refinement sweeps               */
+    double rel_residual;   /* max over right-hand sides of |b - A w| / |b| with the
+                              FP64 operator, recomputed at the end                 */
     double seconds;        /* wall time of the call                                 */
+    int steps;             /* operator applications of the Krylov iterations (one
+                              application serves every column of a block)          */
 } ibem_solve_info;
 
 /* Build the discretisation: patches, knot vectors, cluster tree and block
@@ -190,13 +202,25 @@ ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrh
                              int precision);
 
 /* Solve T A T^T w = b (Sec. 4 item 3): Jacobi-preconditioned conjugate
- * gradients (Laplace) or GMRES(100) (Helmholtz), one right-hand side at a
- * time.  precision IBEM_FP64 runs the solver on the FP64 operator;
+ * gradients (Laplace) or GMRES(100) (Helmholtz); flexible GMRES(100) with
+ * IBEM_PRECOND_LEARNED.  Stops when |b - A w| / |b| <= rtol with A the FP64
+ * operator, for every right-hand side.
+ * nrhs = 1: precision IBEM_FP64 runs the solver on the FP64 operator;
  * IBEM_FP32 runs it on the FP32 operator and replaces the recursive residual
- * by the true FP64 residual b - A w whenever it has dropped 100-fold (reliable
- * updates; info->outer counts them).  Stops when |b - A w| / |b| <= rtol with A
- * the FP64 operator.  Synchronises; returns IBEM_ERR_NOCONV if maxit is
- * reached. */
+ * by the true FP64 residual b - A w whenever it has dropped 100-fold (CG,
+ * reliable updates) or at every restart (GMRES); info->outer counts them.
+ * maxit bounds the iterations.
+ * nrhs > 1: all right-hand sides are solved together in lock step (each has
+ * its own Krylov space and stopping test; one operator application per step
+ * serves all of them, so the many-right-hand-side operators run inside the
+ * solve).  Outer loop: the true FP64 residual of every column; converged
+ * columns leave the block; the others take one GMRES(100) cycle (or one CG
+ * run) on A d = r and x += d.  With IBEM_FP64 the inner solve aims at rtol;
+ * with IBEM_FP32 it runs on the FP32 operator (tensor-core coupling from 16
+ * columns on) to max(rtol |b|, 1e-3 |r|), so the outer loop is iterative
+ * refinement with FP64 residuals.  maxit bounds the lock-step operator
+ * applications (info->steps).
+ * Synchronises; returns IBEM_ERR_NOCONV if maxit is reached. */
 ibem_status ibem_solve(ibem_handle* h, const double* b_dev, double* w_dev, int nrhs,
                        double rtol, int maxit, int precond, int precision,
                        ibem_solve_info* info);

@@ -100,7 +100,8 @@ void free_handle(ibem_handle* h) {
                     h->d_xs, h->d_ys, h->d_xh, h->d_yh, h->d_xs32, h->d_ys32, h->d_yh32, h->d_src32, h->d_diag,
                     h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
                     h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv, h->d_up_ptr, h->d_up_src,
-                    h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr, h->d_Mf, h->d_Sf};
+                    h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr, h->d_Mf, h->d_Sf,
+                    h->d_gen_pts, h->d_gen_trig, h->d_gen_x};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -299,6 +300,15 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
         for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k) ftgt[k] = (int32_t)c;
     }
     TRY(upload(&h->d_far_ptr, P.far_ptr, st), "upload far ptr");
+    // bound on the distance of two interpolation points of a far block, from the
+    // cluster balls (the range of the phase kappa r of the coupling)
+    for (int64_t c = 0; c < P.C; ++c)
+        for (int64_t k = P.far_ptr[c]; k < P.far_ptr[c + 1]; ++k) {
+            const double* bi = &P.balls[4 * c];
+            const double* bj = &P.balls[4 * (int64_t)P.far_src[k]];
+            const double dx = bi[0] - bj[0], dy = bi[1] - bj[1], dz = bi[2] - bj[2];
+            h->far_diam = std::max(h->far_diam, std::sqrt(dx * dx + dy * dy + dz * dz) + bi[3] + bj[3]);
+        }
     TRY(upload(&h->d_far_src, P.far_src, st), "upload far src");
     TRY(upload(&h->d_far_tgt, ftgt, st), "upload far tgt");
     TRY(upload(&h->d_far_rows, h->far_rows, st), "upload far rows");
@@ -402,7 +412,7 @@ ibem_status ibem_assemble(ibem_handle* h) {
             h->far_on_the_fly = P.prm.fp64_coupling != IBEM_COUPLING_DF || nk * sizeof(float4) > free_b / 2;
             if (!h->far_on_the_fly)
                 if ((e = cudaMalloc(&h->d_Kc, nk * sizeof(float4)))) return cuda_fail(h, e, "alloc coupling matrices");
-        } else if (P.n_far > 0 && P.prm.fp64_coupling != IBEM_COUPLING_NONE) {
+        } else if (P.n_far > 0 && P.prm.fp64_coupling != IBEM_COUPLING_NONE) {   // Laplace (GENERATE: as DF)
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
                 if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
@@ -420,6 +430,8 @@ ibem_status ibem_assemble(ibem_handle* h) {
         if ((e = launch_far_assembly(h))) return cuda_fail(h, e, "far assembly");
     }
     if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");
+    // work vectors sized before assembly lack the stored coupling's moment buffer
+    if (h->d_Kc && !h->d_xh4) h->ws_nrhs = 0;
     if (!h->d_bj_inv) {
         std::string msg;
         if ((e = build_block_jacobi(h, &msg))) return msg.empty() ? cuda_fail(h, e, "block-Jacobi") : fail(h, IBEM_ERR_BREAKDOWN, msg);

@@ -317,6 +317,11 @@ struct ibem_handle {
     double* d_hsx = nullptr;        // Helmholtz: split-layout input  [2R][max(N, nq)]
     double* d_hsy = nullptr;        // Helmholtz: split-layout output [2R][N]
     bool far_on_the_fly = false;    // Helmholtz FP64 coupling generated on the fly (stored K too large)
+    double far_diam = 0.0;          // bound on the distance of two points of a far block (cluster balls)
+    float4* d_gen_pts = nullptr;    // double-float point tables [C][q2][2] of the generated coupling
+    float4* d_gen_trig = nullptr;   // e^{i j 2 pi / 2048} as double-float pairs
+    float4* d_gen_x = nullptr;      // moments, chunked double-float complex [nch][C][q2][RC]
+    size_t gen_x_bytes = 0;
     int kpt = 0;
     int df_nst = 0;   // ring depth of the double-float coupling (autotuned at assembly; 0 = default)
     std::vector<int32_t> far_rows;  // target clusters with a non-empty far list
@@ -388,11 +393,14 @@ struct PhaseTimer {
         b = take();
         cudaEventRecord(a, h->stream);
     }
-    ~PhaseTimer() {
+    // end the phase now (the destructor then does nothing)
+    void stop() {
         if (!a) return;
         cudaEventRecord(b, h->stream);
         h->ev_used.push_back({phase, {a, b}});
+        a = nullptr;
     }
+    ~PhaseTimer() { stop(); }
 };
 
 // real kernels of kernels_apply.cu reused by the complex (Helmholtz) path
@@ -440,11 +448,17 @@ cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const do
 cudaError_t launch_near_diagonal(ibem_handle* h, double* diag);
 ibem_status solve_impl(ibem_handle* h, const double* b, double* w, int nrhs, double rtol,
                        int maxit, int precond, int precision, ibem_solve_info* info);
+// lock-step solver for several right-hand sides (solve_block.cu)
+ibem_status solve_block_impl(ibem_handle* h, const double* b, double* x, int R, double rtol, int maxit,
+                             int precond, int precision, ibem_solve_info* info);
 cudaError_t ensure_workspace(ibem_handle* h, int nrhs);
 cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
 bool mr_supported(const ibem_handle* h, int nrhs);
 cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs);
 void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
+// Helmholtz coupling generated in double-float for many right-hand sides (kernels_gen.cu).
+bool gen_supported(const ibem_handle* h);
+cudaError_t launch_coupling_gen(ibem_handle* h, int R);
 // Double-float coupling launcher and the autotuner of its ring depth (kernels_apply.cu).
 cudaError_t launch_coupling_df(ibem_handle* h, int R, int nst);
 cudaError_t tune_coupling_df(ibem_handle* h);

@@ -620,7 +620,11 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
     if ((e = cudaMalloc(&h->d_xh2, (size_t)nrhs * P.C * ((P.q2 + 1) & ~1) * sizeof(float2) + 16))) return e;
     cudaFree(h->d_colpart);
     h->d_colpart = nullptr;
-    if ((e = cudaMalloc(&h->d_colpart, (size_t)nrhs * (h->n_up > 0 ? h->n_up : 1) * (P.q2 > 0 ? P.q2 : 1) *
+    // column shares of the stored symmetric Laplace coupling only (a Helmholtz
+    // handle never reads them; at 64 right-hand sides they would need n_up q^2
+    // 128 floats pairs)
+    if (!h->helm && h->d_Kdf &&
+        (e = cudaMalloc(&h->d_colpart, (size_t)nrhs * (h->n_up > 0 ? h->n_up : 1) * (P.q2 > 0 ? P.q2 : 1) *
                                            sizeof(float2))))
         return e;
     if ((e = cudaMalloc(&h->d_xs32, ns * sizeof(float)))) return e;
@@ -629,7 +633,8 @@ cudaError_t ensure_workspace(ibem_handle* h, int nrhs) {
         size_t n = (size_t)(P.N > P.nq ? P.N : P.nq);
         if ((e = cudaMalloc(&h->d_hsx, (size_t)nrhs * n * sizeof(double)))) return e;
         if ((e = cudaMalloc(&h->d_hsy, (size_t)nrhs * P.N * sizeof(double)))) return e;
-        if ((e = cudaMalloc(&h->d_xh4, (size_t)(nrhs / 2 + 1) * P.C * ((P.q2 + 1) & ~1) * sizeof(float4) + 32)))
+        // double-float moments of the stored coupling only (none when it is generated)
+        if (h->d_Kc && (e = cudaMalloc(&h->d_xh4, (size_t)(nrhs / 2 + 1) * P.C * ((P.q2 + 1) & ~1) * sizeof(float4) + 32)))
             return e;
     }
     h->ws_nrhs = nrhs;

@@ -758,12 +758,16 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
     const int R = nrhs, R2 = 2 * nrhs;
     const int T = 256;
     cudaError_t e;
-    helm_split_vec_kernel<<<nblk((int64_t)R * P.N, T), T, 0, st>>>(R, P.N, x, xsplit);
-    lift_kernel<<<nblk(R2 * P.E * P.nb, T), T, 0, st>>>(R2, P.E, P.p, P.ne1, h->d_ext, xsplit, P.N, h->d_xs);
-    h->launches += 2;
+    {
+        PhaseTimer pt(h, 0);
+        helm_split_vec_kernel<<<nblk((int64_t)R * P.N, T), T, 0, st>>>(R, P.N, x, xsplit);
+        lift_kernel<<<nblk(R2 * P.E * P.nb, T), T, 0, st>>>(R2, P.E, P.p, P.ne1, h->d_ext, xsplit, P.N, h->d_xs);
+        h->launches += 2;
+    }
     if (P.q > 0) {
         const int q2 = P.q2;
         const int64_t leaf_off = P.level_off[P.m];
+        PhaseTimer pt1(h, 1);
         leaf_moment_kernel<<<nblk(R2 * P.E * q2, T), T, 0, st>>>(R2, P.E, P.pp, P.q, h->d_M, h->d_xs, leaf_off, P.C,
                                                                   h->d_xh);
         h->launches++;
@@ -774,8 +778,10 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
             h->launches++;
         }
         if ((e = cudaMemsetAsync(h->d_yh, 0, (size_t)R2 * P.C * q2 * sizeof(double), st))) return e;
+        pt1.stop();
         unsigned nrows = (unsigned)h->far_rows.size();
         if (nrows > 0) {
+            PhaseTimer pt2(h, 2);
             if (precision == IBEM_FP32) {
                 int G = 256 / q2 > 0 ? 256 / q2 : 1;
                 int threads = ((G * q2 + 31) / 32) * 32;
@@ -821,6 +827,8 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
                 }
 #undef IBEM_HDF_LAUNCH
                 h->launches += 2;
+            } else if (P.prm.fp64_coupling != IBEM_COUPLING_NATIVE && gen_supported(h)) {
+                if ((e = launch_coupling_gen(h, R))) return e;
             } else {
                 int G = 256 / q2 > 0 ? 256 / q2 : 1;
                 int threads = ((G * q2 + 31) / 32) * 32;
@@ -830,6 +838,7 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
                 h->launches++;
             }
         }
+        PhaseTimer pt3(h, 3);
         for (int L = 0; L < P.m; ++L) {
             int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
             l2l_kernel<<<nblk(R2 * nL1 * q2, T), T, 0, st>>>(R2, nL1, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
@@ -843,6 +852,7 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
         if ((e = cudaMemsetAsync(h->d_ys, 0, (size_t)R2 * P.Nstar * sizeof(double), st))) return e;
     }
     int threads = ((P.nb * P.nb + 31) / 32) * 32;
+    PhaseTimer pt4(h, 4);
     if (precision == IBEM_FP32) {
         d2f_kernel<<<nblk(R2 * P.Nstar, T), T, 0, st>>>(h->d_xs, h->d_xs32, R2 * P.Nstar);
         helm_near_apply_kernel<float2, float><<<dim3((unsigned)P.E, R), threads, 2 * threads * sizeof(double), st>>>(
@@ -853,6 +863,8 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
             h->d_near_ptr, h->d_near_src, reinterpret_cast<const double2*>(h->d_near), P.nb, P.E, h->d_xs, h->d_ys);
         h->launches++;
     }
+    pt4.stop();
+    PhaseTimer pt5(h, 5);
     restrict_kernel<<<nblk(R2 * P.N, T), T, 0, st>>>(R2, P.N, P.p, P.ne1, h->d_ext, h->d_ys, P.E, ysplit);
     helm_join_vec_kernel<<<nblk((int64_t)R * P.N, T), T, 0, st>>>(R, P.N, ysplit, y);
     h->launches += 2;

@@ -576,6 +576,7 @@ ibem_status solver_pairs_impl(ibem_handle* h, const double* b, int nrhs, double 
         info->outer = total_outer;
         info->rel_residual = worst;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->steps = total_it;
     }
     return release(worst_s);
 }
@@ -637,12 +638,14 @@ ibem_status solver_residuals_impl(ibem_handle* h, const double* b, int nrhs, dou
         info->outer = total_outer;
         info->rel_residual = 0.0;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->steps = total_it;
     }
     return release(worst_s);
 }
 
 ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, double rtol, int maxit,
                        int precond, int precision, ibem_solve_info* info) {
+    if (nrhs > 1) return solve_block_impl(h, b, wout, nrhs, rtol, maxit, precond, precision, info);
     Plan& P = h->P;
     int64_t N = P.N;
     auto t0 = std::chrono::steady_clock::now();
@@ -700,6 +703,7 @@ ibem_status solve_impl(ibem_handle* h, const double* b, double* wout, int nrhs, 
         info->outer = total_outer;
         info->rel_residual = worst_res;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->steps = total_it;
     }
     return worst;
 }

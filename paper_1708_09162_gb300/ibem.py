@@ -68,7 +68,7 @@ class ibem_info(ctypes.Structure):
 
 class ibem_solve_info(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("outer", ctypes.c_int), ("rel_residual", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("steps", ctypes.c_int)]
 
 
 class ibem_profile_data(ctypes.Structure):
@@ -205,7 +205,7 @@ def nurbs_patches(specs):
     return arr
 
 
-IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE = 0, 1, 2
+IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERATE = 0, 1, 2, 3
 
 
 def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8,
