@@ -485,7 +485,8 @@ ibem_status ibem_matvec_host(ibem_handle* h, const double* x, double* y, int nrh
     if (nrhs == 0) return IBEM_OK;
     cudaError_t e;
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
-    size_t bytes = (size_t)nrhs * h->P.N * sizeof(double);
+    // [nrhs][ndof] values, complex (two doubles each) for Helmholtz
+    size_t bytes = (size_t)nrhs * h->P.N * (h->helm ? 2 : 1) * sizeof(double);
     double *dx = nullptr, *dy = nullptr;
     if ((e = cudaMallocAsync(&dx, bytes, h->stream))) return cuda_fail(h, e, "alloc x");
     if ((e = cudaMallocAsync(&dy, bytes, h->stream))) { cudaFreeAsync(dx, h->stream); return cuda_fail(h, e, "alloc y"); }

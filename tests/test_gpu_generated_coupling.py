@@ -81,3 +81,17 @@ def test_generated_coupling_bounded_wait():
     assert np.array_equal(_cmatvec(h, x), y_ok)
     assert ibem.ibem_device_status(h) == ibem.IBEM_DEVICE_OK
     ibem.ibem_destroy(h)
+
+
+def test_matvec_host_helmholtz_many_rhs():
+    # the host-buffer entry point with complex values: same result as the device one
+    import torch
+    ibem = lib()
+    h = _handle(2, 2, 8, 4.0, ibem.IBEM_COUPLING_GENERATE)
+    x = _x(ibem.ibem_get_info(h).ndof, 20, 9)
+    xh = torch.from_numpy(np.ascontiguousarray(np.stack([x.real, x.imag], -1))).pin_memory()
+    yh = torch.zeros_like(xh).pin_memory()
+    ibem.ibem_matvec_host(h, xh, yh, 20, 0)
+    y = yh.numpy()
+    assert np.array_equal(y[..., 0] + 1j * y[..., 1], _cmatvec(h, x))
+    ibem.ibem_destroy(h)
