@@ -1,24 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the FMM-compressed single-layer operator on one GB300.
 
-Workload: interior Laplace problem on the unit sphere (6 cube-sphere patches),
-degree-3 B-splines on level 5 (7,350 dofs, 98,304 superspace dofs), Chebyshev
-6 x 6 points per cluster, admissibility eta = 1.6, one right-hand side.
+Headline workload (Helmholtz sound-soft scattering): the unit sphere as 6
+cube-sphere patches, degree-2 B-splines on level 6 (26,136 complex dofs,
+221,184 superspace dofs), Chebyshev 8 x 8 points per cluster, admissibility
+eta = 1.6, wavenumber kappa = 4, 64 right-hand sides.
 
-A step is one application of y = T A T^T x (lift, upward pass, coupling,
-downward pass, near field, restriction), the operator applied in every Krylov
-iteration.  `value` is dofs x right-hand sides per second of the FP64 operator
-over all ranks (each rank runs an independent replica; no data-path
-collective).  Beside it: the FP32 operator (error against FP64 stated), the
-FP64 CG solve and the mixed-precision iterative-refinement solve to true
-relative residual 1e-8, the end-to-end time through ibem_matvec_host with host
-buffers, the roofline of the dominant kernel and the oracle on the host cores.
+A step is one application of y = T A T^T x to all 64 right-hand sides (lift,
+upward pass, coupling, downward pass, near field, restriction) with the
+FP64-accurate operator: FP64 near blocks and the coupling generated per far
+block in double-float arithmetic (about 48 significant bits) and applied to
+all right-hand sides.  `value` is dofs x right-hand sides per second over all
+ranks (each rank runs an independent replica; no data-path collective).
+Beside it: the FP32 operator with the coupling on the tensor cores, both
+operators' errors against the oracle on sampled rows at full size, the
+lock-step GMRES solves of the 64 plane waves to true relative residual 1e-8
+(mixed precision against plain FP64), the end-to-end time through
+ibem_matvec_host with host buffers, the Laplace degree-3 workload on level 5,
+the batched instances, the learned preconditioner, the roofline of the
+dominant kernel and the oracle on all host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -29,99 +36,174 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = {"workload": "laplace-sphere-p3-m5-q6-eta1.6", "p": 3, "m": 5, "q_cheb": 6, "eta": 1.6,
-            "nrhs": 1, "geometry": "unit sphere, 6 cube-sphere patches", "kernel": "laplace"}
-METRIC = "FMM single-layer matvec DOF*RHS/s (FP64), GMRES/CG solve time to 1e-8 vs plain FP64 GPU"
+WORKLOAD = {"workload": "helmholtz-sphere-p2-m6-q8-k4-R64", "kernel": "helmholtz", "kappa": 4.0, "p": 2, "m": 6,
+            "q_cheb": 8, "eta": 1.6, "nrhs": 64, "geometry": "unit sphere, 6 cube-sphere patches",
+            "rhs": "64 sound-soft plane waves, directions seeded uniform on S^2",
+            "coupling": "generated per far block in double-float, applied to all right-hand sides"}
+LAPLACE = {"workload": "laplace-sphere-p3-m5-q6-eta1.6", "p": 3, "m": 5, "q_cheb": 6, "eta": 1.6, "nrhs": 1}
+METRIC = "FMM single-layer matvec DOF·RHS/s and GMRES solve time to 1e-8, vs plain FP64 GPU"
 UNIT = "DOF*RHS/s"
 SEED = 170809162
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "coupling_df_kernel_laplace_sphere_p3_m5.md")
+ORACLE_ROWS = 32          # sampled rows of the oracle's FMM-mode operator (one right-hand side)
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "helm_coupling_gen_kernel_helmholtz_sphere_p2_k4.md")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-solve", action="store_true")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-native", action="store_true", help="skip the native-FP64-coupling comparison")
-    ap.add_argument("--no-helmholtz-many", action="store_true", help="skip the many-right-hand-side Helmholtz section")
-    ap.add_argument("--helmholtz-many-only", action="store_true", help="run only the many-right-hand-side section")
-    ap.add_argument("--helmholtz-many-m", type=int, default=6, help="refinement level of that section (profiling)")
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-laplace", action="store_true", help="skip the Laplace level-5 section")
+    ap.add_argument("--no-potential", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
+    ap.add_argument("--learned-config5", action="store_true",
+                    help="run only the learned preconditioner at level 7 with 16 plane waves (several minutes)")
     ap.add_argument("--cnn-forward-only", action="store_true", help="time only the network's forward pass")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances section")
     ap.add_argument("--batch-only", action="store_true", help="run only the batched-instances section")
+    ap.add_argument("--operator-only", action="store_true",
+                    help="headline operator only (profiling): no solves, side sections or oracle")
+    ap.add_argument("--fp32-only", action="store_true", help="time only the tensor-core FP32 operator (profiling)")
+    ap.add_argument("--laplace-only", action="store_true", help="run only the Laplace level-5 section (profiling)")
     ap.add_argument("--learn-train-m", type=int, default=5, help="level of the training solves")
     ap.add_argument("--learn-m", type=int, default=6, help="level of the compared solves")
     ap.add_argument("--learn-nrhs", type=int, default=2, help="plane waves of the compared solves")
-    ap.add_argument("--oracle-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
-# ---------------------------------------------------------------- oracle timing
-def oracle_worker(nrows):
-    """Runs in a child process with one BLAS thread: times nrows rows of the
-    oracle's FMM-mode operator on the benchmark workload; prints one JSON line."""
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def sampled_input(n):
+    """The seeded input of the accuracy checks and the oracle sample: rows and one
+    complex right-hand side (normal real and imaginary parts)."""
     import numpy as np
+    rng = np.random.default_rng(SEED + 11)
+    rows = np.sort(rng.choice(n, size=ORACLE_ROWS, replace=False))
+    x = rng.normal(size=n) + 1j * rng.normal(size=n)
+    return rows, x
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def _oracle_op():
     from oracle import fmm, galerkin, geometry
+    disc = galerkin.Discretisation(geometry.unit_sphere(), WORKLOAD["p"], WORKLOAD["m"],
+                                   galerkin.HelmholtzKernel(WORKLOAD["kappa"]))
+    return fmm.FMMOperator(disc, WORKLOAD["q_cheb"], WORKLOAD["eta"])
+
+
+_OP = None
+
+
+def _rows_task(chunk):
+    import numpy as np
+    rows, x = chunk
+    t = time.perf_counter()
+    y = _OP.rows([int(r) for r in rows], x)[:, 0]
+    return np.stack([y.real, y.imag], -1).tolist(), time.perf_counter() - t
+
+
+def oracle_child(path):
+    """Runs in a fresh CPU-only process (no CUDA): builds the oracle's FMM-mode
+    operator of the headline workload once, then computes ORACLE_ROWS sampled
+    rows of A x for one seeded right-hand side in a pool of one worker per host
+    core (forked after the build, so the workers share the operator); the
+    timed region is the pool's row phase.  Writes one JSON file."""
+    import multiprocessing as mp
+    import numpy as np
+    global _OP
     t0 = time.perf_counter()
-    disc = galerkin.Discretisation(geometry.unit_sphere(), WORKLOAD["p"], WORKLOAD["m"], galerkin.LaplaceKernel())
-    op = fmm.FMMOperator(disc, WORKLOAD["q_cheb"], WORKLOAD["eta"])
+    _OP = _oracle_op()
     setup = time.perf_counter() - t0
-    rng = np.random.default_rng(SEED)
-    x = rng.normal(size=disc.mesh.n_dofs)
-    rows = rng.choice(disc.mesh.n_dofs, size=nrows, replace=False)
-    times = []
-    for r in rows:
-        op._near_blocks.clear()
-        t = time.perf_counter()
-        op.rows([int(r)], x)
-        times.append(time.perf_counter() - t)
-    print(json.dumps({"rows": int(nrows), "seconds": sum(times), "setup_s": setup}))
+    n = _OP.mesh.n_dofs
+    rows, x = sampled_input(n)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    chunks = [(rows[i::cores], x) for i in range(min(cores, len(rows)))]
+    ctx = mp.get_context("fork")
+    t = time.perf_counter()
+    with ctx.Pool(len(chunks)) as pool:
+        res = pool.map(_rows_task, chunks, chunksize=1)
+    wall = time.perf_counter() - t
+    y = np.zeros((len(rows), 2))
+    for i, (vals, _) in enumerate(res):
+        y[i::len(chunks)] = np.array(vals)
+    json.dump({"rows": rows.tolist(), "y": y.tolist(), "seconds": wall, "setup_s": setup,
+               "workers": len(chunks), "cores": cores, "cpu": cpu_model(),
+               "busy_s": sum(r[1] for r in res)}, open(path, "w"))
 
 
-def run_oracle(nrows):
+def start_oracle_child():
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", str(nrows)],
-                         capture_output=True, text=True, env=env, cwd=ROOT)
-    if out.returncode != 0:
-        raise RuntimeError("oracle worker failed: " + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    proc = subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-child", path], env=env, cwd=ROOT,
+                            stdout=subprocess.DEVNULL, stderr=subprocess.PIPE, text=True)
+    return proc, path
+
+
+def finish_oracle_child(proc, path):
+    _, err = proc.communicate()
+    if proc.returncode != 0:
+        raise RuntimeError("oracle child failed: " + (err or "")[-2000:])
+    with open(path) as f:
+        d = json.load(f)
+    os.unlink(path)
+    return d
 
 
 def reference_arm(args, rank):
-    """The oracle, as it stands, on the host cores: each step computes 2 rows."""
+    """The oracle, as it stands, on the host cores: a pool of one worker per core
+    (forked after the operator's tree is built once, outside the steps); each
+    step computes one sampled row of the FMM-mode operator of the headline
+    workload per worker, applied to one right-hand side."""
     if rank != 0:
         return
-    per_step = 2
+    import multiprocessing as mp
     import numpy as np
-    from oracle import fmm, galerkin, geometry
-    disc = galerkin.Discretisation(geometry.unit_sphere(), WORKLOAD["p"], WORKLOAD["m"], galerkin.LaplaceKernel())
-    op = fmm.FMMOperator(disc, WORKLOAD["q_cheb"], WORKLOAD["eta"])
+    global _OP
+    t0 = time.perf_counter()
+    _OP = _oracle_op()
+    setup = time.perf_counter() - t0
+    n = _OP.mesh.n_dofs
     rng = np.random.default_rng(SEED)
-    x = rng.normal(size=disc.mesh.n_dofs)
+    _, x = sampled_input(n)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    with mp.get_context("fork").Pool(cores) as pool:
+        def step():
+            pool.map(_rows_task, [(rng.choice(n, 1), x) for _ in range(cores)], chunksize=1)
 
-    def step():
-        op._near_blocks.clear()
-        op.rows([int(r) for r in rng.choice(disc.mesh.n_dofs, per_step, replace=False)], x)
-
-    for _ in range(args.warmup):
-        step()
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = time.perf_counter() - t
-    value = args.steps * per_step / dt
+        for _ in range(args.warmup):
+            step()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t
+    value = args.steps * cores / dt
+    cfg = dict(WORKLOAD, ndof=n, ndof_super=_OP.mesh.n_elements * (WORKLOAD["p"] + 1) ** 2, n_near=len(_OP.near),
+               n_far=len(_OP.far), parallelism="single")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, l2="n/a (host)"), "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d rows of the FMM-mode operator per step (one BLAS thread)" % per_step},
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": "per step one sampled row of the oracle's FMM-mode operator per core, one "
+                                       "right-hand side, near blocks and the moments the rows use included "
+                                       "(tree setup %.0f s excluded); one BLAS thread per worker" % setup},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -209,117 +291,6 @@ def _peaks():
         return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
     except OSError:
         return 6800.0, 2070.0, "fallback"
-
-
-def helmholtz_many_rhs(ibem, stream, world, barrier, args):
-    """Exterior Helmholtz, kappa = 4, p = 2, m = 6, q = 8, 64 incident plane waves
-    (seeded uniform directions): the FP32 operator with the coupling on the
-    tensor cores, its error against the FP64 operator on one right-hand side,
-    and the roofline of the tensor-core coupling kernel."""
-    import numpy as np
-    import torch
-    p, m, q, kappa, R = 2, args.helmholtz_many_m, 8, 4.0, 64
-    t0 = time.perf_counter()
-    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=ibem.IBEM_HELMHOLTZ,
-                                                                 kappa=kappa), stream)
-    ibem.ibem_assemble(h)
-    setup_s = time.perf_counter() - t0
-    info = ibem.ibem_get_info(h)
-    N = info.ndof
-    rng = np.random.default_rng(SEED + 3)
-    d = rng.normal(size=(R, 3))
-    d /= np.linalg.norm(d, axis=1)[:, None]
-    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
-    ibem.ibem_quad_points(h, qp)
-    torch.cuda.synchronize()
-    ph = qp.cpu().numpy() @ d.T                                    # [nq, R]
-    g = -np.exp(1j * kappa * ph).T                                 # sound-soft data, [R, nq]
-    gq = torch.from_numpy(np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))).cuda()
-    b = torch.empty((R, N, 2), dtype=torch.float64, device="cuda")
-    ibem.ibem_rhs(h, gq, R, b)
-    y = torch.empty_like(b)
-    steps = max(3, args.steps // 20)
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            ibem.ibem_matvec(h, b, y, R, ibem.IBEM_FP32)
-    barrier()
-    ibem.ibem_profile_enable(h, True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(steps):
-            ibem.ibem_matvec(h, b, y, R, ibem.IBEM_FP32)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1) / steps
-    prof = ibem.ibem_profile_read(h)
-    ibem.ibem_profile_enable(h, False)
-    coup_ms = prof["ms"]["coupling"] / steps
-    phases = {k: v / steps for k, v in prof["ms"].items()}
-    # FP64 operator on the first right-hand side (coupling generated on the fly in FP64)
-    y64 = torch.empty((1, N, 2), dtype=torch.float64, device="cuda")
-    t1 = time.perf_counter()
-    ibem.ibem_matvec(h, b[:1].contiguous(), y64, 1, ibem.IBEM_FP64)
-    torch.cuda.synchronize()
-    fp64_s = time.perf_counter() - t1
-    err = float((y[0] - y64[0]).abs().max() / y64[0].abs().max())
-    # potential of the 64 densities (the right-hand sides stand in for them) at 200
-    # points on the sphere of radius 3 (seeded): one e^{ikr}/r per point, source
-    # and chunk of 16 densities, FP64
-    npt = 200
-    dp = rng.normal(size=(npt, 3))
-    pts = torch.from_numpy(3.0 * dp / np.linalg.norm(dp, axis=1)[:, None]).cuda()
-    u = torch.empty((R, npt, 2), dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        ibem.ibem_potential(h, b, R, pts, u)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            ibem.ibem_potential(h, b, R, pts, u)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    pot_ms = e0.elapsed_time(e1) / 2
-    nsrc = info.n_elements * 64
-    # the same potentials with the far field interpolated (forward moments of the
-    # 64 densities, per-point tree walk, q^2 kernel values per admissible cluster)
-    uf = torch.empty_like(u)
-    with torch.cuda.stream(stream):
-        nf, nn = ibem.ibem_potential_fmm(h, b, R, pts, uf)
-    e0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(5):
-            ibem.ibem_potential_fmm(h, b, R, pts, uf)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fmm_ms = e0.elapsed_time(e1) / 5
-    fmm_err = float((uf - u).abs().max() / u.abs().max())
-    potential = {"points": npt, "densities": R, "sources": nsrc, "ms": pot_ms,
-                 "pair_density_evals_per_s": npt * nsrc * R / (pot_ms * 1e-3),
-                 "kernel_evals_per_s": npt * nsrc * ((R + 15) // 16) / (pot_ms * 1e-3),
-                 "interpolated": {"ms": fmm_ms, "far_terms": nf, "near_terms": nn, "speedup": pot_ms / fmm_ms,
-                                  "rel_err_vs_direct": fmm_err}}
-    q2 = q * q
-    flops = 2.0 * 128 * 128 * 64 * info.n_far                      # real-form GEMM per far block
-    peak = 1912.6
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peak = json.load(f).get("bf16_tflops", peak)
-    except OSError:
-        pass
-    sfu = 3.0 * q2 * q2 * info.n_far                               # rsqrt, sine, cosine per complex entry
-    sfu_peak = 152 * 16 * 2070e6
-    ibem.ibem_destroy(h)
-    return {"workload": "helmholtz-sphere-p2-m%d-q8-k4-R64" % m, "ndof": N, "ndof_super": info.ndof_super,
-            "n_near": info.n_near, "n_far": info.n_far, "nrhs": R, "setup_s": setup_s,
-            "value": world * N * R / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "coupling_ms": coup_ms,
-            "phase_ms": phases,
-            "rel_err_vs_fp64_rhs0": err, "fp64_one_rhs_s": fp64_s, "potential": potential,
-            "tensor": {"kernel": "mr_coupling_tc_kernel", "achieved_tflops": flops / (coup_ms * 1e-3) / 1e12,
-                       "peak_tflops": peak, "frac": flops / (coup_ms * 1e-3) / 1e12 / peak,
-                       "sfu_frac": sfu / (coup_ms * 1e-3) / sfu_peak,
-                       "note": "K is generated per block on the SFU (rsqrt, sine, cosine); the tensor pipe waits "
-                               "for it"}}
 
 
 def batched_instances(ibem, stream, args):
@@ -501,6 +472,243 @@ def learned_preconditioner(ibem, stream, args):
             "cnn_forward": fwd}
 
 
+def bessel_zeros(lmax, lo, hi):
+    """Zeros of the spherical Bessel functions j_l, l <= lmax, in [lo, hi]
+    (sign changes on a fine grid, refined by Brent's method)."""
+    import numpy as np
+    from scipy import optimize, special
+    zs = []
+    g = np.linspace(lo, hi, 4001)
+    for l in range(lmax + 1):
+        v = special.spherical_jn(l, g)
+        for i in np.nonzero(np.sign(v[:-1]) * np.sign(v[1:]) < 0)[0]:
+            zs.append(optimize.brentq(lambda t: special.spherical_jn(l, t), g[i], g[i + 1]))
+    return np.array(sorted(zs))
+
+
+def draw_wavenumbers(rng, n, lo=8.0, hi=16.0, gap=0.02, lmax=20):
+    """n wavenumbers uniform in [lo, hi], rejecting draws within `gap` of a zero
+    of j_l (l <= lmax): there the single-layer operator of the unit sphere has a
+    vanishing eigenvalue.  Returns the kept and the rejected draws."""
+    import numpy as np
+    zeros = bessel_zeros(lmax, lo - 1.0, hi + 1.0)
+    kept, rejected = [], []
+    while len(kept) < n:
+        k = float(rng.uniform(lo, hi))
+        (rejected if np.min(np.abs(zeros - k)) < gap else kept).append(k)
+    return kept, rejected
+
+
+def learned_config5(ibem, stream, args):
+    """Learned preconditioner at the 101,400-dof workload: Helmholtz sound-soft
+    scattering on the unit sphere, p = 2, level 7, q = 8, kappa drawn uniformly
+    from [8, 16] (resonance filter: no draw within 0.02 of a zero of j_l,
+    l <= 20), 16 seeded plane waves.  The network (4 layers, 32 channels, BF16)
+    is trained on the plain solver's residuals at levels 5 and 6 (q = 6, three
+    wavenumbers each, two plane waves, residual-norm objective); then lock-step
+    flexible GMRES(100) with it is compared with block-Jacobi GMRES(100), both
+    with the FP32 operator (tensor-core coupling) inside iterative refinement
+    and judged by the FP64 true residual 1e-8 of every right-hand side."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(SEED + 13)
+    k_solve, rejected = draw_wavenumbers(rng, 1)
+    k_solve = k_solve[0]
+
+    def make(m, q, k, coupling=0):
+        h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(2, m, q_cheb=q, eta=1.6,
+                                                                     kernel=ibem.IBEM_HELMHOLTZ, kappa=k,
+                                                                     fp64_coupling=coupling), stream)
+        ibem.ibem_assemble(h)
+        return h
+
+    c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
+    t0 = time.perf_counter()
+    train = []
+    for m in (5, 6):
+        ks, rej = draw_wavenumbers(rng, 3)
+        rejected += rej
+        for k in ks:
+            h = make(m, 6, k)
+            info = ibem.ibem_get_info(h)
+            b = plane_wave_rhs(ibem, h, k, 2, int(rng.integers(1 << 30)))
+            r = torch.zeros((2 * 60, info.ndof, 2), dtype=torch.float64, device="cuda")
+            _, n, _ = ibem.ibem_solver_residuals(h, b, 2, r, rtol=1e-10, maxit=600, stride=1, max_vecs=60,
+                                                 check=False)
+            l1 = ibem.ibem_cnn_train_operator(h, c, r, n, batch=16, epochs=6, lr=1e-3, seed=len(train))
+            train.append({"level": m, "k": k, "vectors": n, "objective_after": l1})
+            ibem.ibem_destroy(h)
+    train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    h = make(7, 8, k_solve, ibem.IBEM_COUPLING_GENERATE)
+    setup_s = time.perf_counter() - t0
+    info = ibem.ibem_get_info(h)
+    R = 16
+    b = plane_wave_rhs(ibem, h, k_solve, R, SEED + 14)
+    res = {}
+    for name, pc in (("block_jacobi", ibem.IBEM_PRECOND_BLOCK_JACOBI), ("learned", ibem.IBEM_PRECOND_LEARNED)):
+        ibem.ibem_set_learned_preconditioner(h, c if pc == ibem.IBEM_PRECOND_LEARNED else None)
+        w = torch.empty_like(b)
+        s, si = ibem.ibem_solve(h, b, w, R, rtol=1e-8, maxit=4000, precond=pc, precision=ibem.IBEM_FP32,
+                                check=False)
+        res[name] = {"status": ibem.ibem_status_string(s), "steps": si.steps, "iterations": si.iterations,
+                     "outer": si.outer, "rel_residual_fp64": si.rel_residual, "seconds": si.seconds}
+    ibem.ibem_set_learned_preconditioner(h, None)
+    ibem.ibem_destroy(h)
+    ibem.ibem_cnn_destroy(c)
+    return {"workload": "helmholtz-sphere-p2-m7-q8-R16, kappa from [8, 16]", "k_solve": k_solve,
+            "k_rejected_by_filter": rejected, "ndof": info.ndof, "n_far": info.n_far, "setup_s": setup_s,
+            "train": train, "train_s": train_s, "solve": res,
+            "steps_learned_over_block_jacobi": res["learned"]["steps"] / max(1, res["block_jacobi"]["steps"])}
+
+
+def _peak_tensor():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f).get("bf16_tflops", 1912.6), "measured"
+    except OSError:
+        return 1900.0, "fallback"
+
+
+def gen_ops_per_launch(n_far, q, R):
+    """FP32-pipe operations of the double-float coupling, counted from its
+    formulas: 247 per generated complex kernel value (differences, r^2, r, 1/r,
+    the phase and its reduction, the Taylor terms, the table product) and 48 per
+    complex multiply-add and right-hand side (four exact products with their
+    error terms and TwoSum accumulations of 12 operations each)."""
+    q4 = float(q) ** 4
+    return n_far * q4 * 247.0, n_far * q4 * 48.0 * R
+
+
+def plane_wave_rhs(ibem, h, kappa, R, seed):
+    import numpy as np
+    import torch
+    info = ibem.ibem_get_info(h)
+    d = np.random.default_rng(seed).normal(size=(R, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    torch.cuda.synchronize()
+    g = -np.exp(1j * kappa * (d @ qp.cpu().numpy().T))          # sound-soft data, [R, nq]
+    gq = torch.from_numpy(np.ascontiguousarray(np.stack([g.real, g.imag], axis=-1))).cuda()
+    b = torch.empty((R, info.ndof, 2), dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, gq, R, b)
+    return b
+
+
+def laplace_section(ibem, stream, world, barrier, steps, warmup):
+    """The Laplace workload of the previous headline: p = 3, m = 5, q = 6, one
+    right-hand side, FP64 operator with the stored symmetric double-float
+    coupling (HBM-bound), FP32 operator, block-Jacobi CG FP64 and mixed."""
+    import numpy as np
+    import torch
+    W = LAPLACE
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=W["q_cheb"], eta=W["eta"]),
+                         stream)
+    t0 = time.perf_counter()
+    ibem.ibem_assemble(h)
+    asm = time.perf_counter() - t0
+    info = ibem.ibem_get_info(h)
+    N = info.ndof
+    x = torch.from_numpy(np.random.default_rng(SEED).normal(size=(1, N))).cuda()
+    y, y32 = torch.empty_like(x), torch.empty_like(x)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(prec, out, n):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                ibem.ibem_matvec(h, x, out, 1, prec)
+        barrier()
+        ibem.ibem_profile_enable(h, True)
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(n):
+                ibem.ibem_matvec(h, x, out, 1, prec)
+        ev1.record(stream)
+        barrier()
+        prof = ibem.ibem_profile_read(h)
+        ibem.ibem_profile_enable(h, False)
+        return ev0.elapsed_time(ev1) / n, {k: v / n for k, v in prof["ms"].items()}
+
+    ms, ph = timed(0, y, steps)
+    ms32, _ = timed(1, y32, steps)
+    # roofline of coupling_df_kernel: the stored upper half of K (8 bytes per
+    # double-float entry), the moments streamed with every block, column shares
+    # written and gathered, y^ written
+    q2 = W["q_cheb"] ** 2
+    kpt = (q2 + 3) // 4
+    n_up = info.bytes_far // (kpt * 4 * q2 * 8)
+    kbytes = info.bytes_far + n_up * ((q2 + 1) // 2 * 2) * 8 + n_up * q2 * 8 + info.n_clusters * q2 * 8
+    hbm, _, src = _peaks()
+    coup = ph["coupling"]
+    x0 = np.array([0.9, 0.9, 0.9])
+    qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
+    ibem.ibem_quad_points(h, qp)
+    torch.cuda.synchronize()
+    gq = torch.from_numpy(1.0 / (4 * np.pi * np.linalg.norm(qp.cpu().numpy() - x0, axis=1))).cuda()
+    b = torch.empty(N, dtype=torch.float64, device="cuda")
+    ibem.ibem_rhs(h, gq, 1, b)
+    w = torch.empty_like(b)
+    s64 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI, precision=0)
+    s32 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precond=ibem.IBEM_PRECOND_BLOCK_JACOBI, precision=1)
+    ibem.ibem_destroy(h)
+    return {"workload": W["workload"], "ndof": N, "ndof_super": info.ndof_super, "n_near": info.n_near,
+            "n_far": info.n_far, "assemble_s": asm,
+            "fp64": {"value": world * N / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "phase_ms": ph,
+                     "dtype": "f64 (stored double-float coupling, about 48 bits)"},
+            "fp32": {"value": world * N / (ms32 * 1e-3), "ms_per_step": ms32,
+                     "rel_err_vs_fp64": float((y32 - y).abs().max() / y.abs().max())},
+            "roofline_coupling": {"kernel": "coupling_df_kernel", "bound": "hbm", "algorithmic_bytes": kbytes,
+                                  "achieved": kbytes / (coup * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                  "frac": kbytes / (coup * 1e-3) / 1e9 / hbm,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % src},
+            "block_jacobi_cg": {"rtol": 1e-8, "rhs": "point source 1/(4 pi |x - x0|), x0 = (0.9, 0.9, 0.9)",
+                                "fp64": {"seconds": s64.seconds, "iterations": s64.iterations,
+                                         "rel_residual": s64.rel_residual},
+                                "mixed": {"seconds": s32.seconds, "iterations": s32.iterations,
+                                          "fp64_updates": s32.outer, "rel_residual": s32.rel_residual},
+                                "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}}
+
+
+def potentials_section(ibem, stream, h, b):
+    """Potentials of the 64 densities (the right-hand sides stand in for them) at
+    200 seeded points on the sphere of radius 3: direct Gauss sums (FP64) and with
+    the far field interpolated."""
+    import numpy as np
+    import torch
+    info = ibem.ibem_get_info(h)
+    R = b.shape[0]
+    npt = 200
+    dp = np.random.default_rng(SEED + 4).normal(size=(npt, 3))
+    pts = torch.from_numpy(3.0 * dp / np.linalg.norm(dp, axis=1)[:, None]).cuda()
+    u = torch.empty((R, npt, 2), dtype=torch.float64, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ibem.ibem_potential(h, b, R, pts, u)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ibem.ibem_potential(h, b, R, pts, u)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pot_ms = e0.elapsed_time(e1) / 2
+    uf = torch.empty_like(u)
+    with torch.cuda.stream(stream):
+        nf, nn = ibem.ibem_potential_fmm(h, b, R, pts, uf)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            ibem.ibem_potential_fmm(h, b, R, pts, uf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fmm_ms = e0.elapsed_time(e1) / 5
+    nsrc = info.n_elements * 64
+    return {"points": npt, "densities": R, "sources": nsrc, "direct_ms": pot_ms,
+            "pair_density_evals_per_s": npt * nsrc * R / (pot_ms * 1e-3),
+            "interpolated": {"ms": fmm_ms, "far_terms": nf, "near_terms": nn, "speedup": pot_ms / fmm_ms,
+                             "rel_err_vs_direct": float((uf - u).abs().max() / u.abs().max())}}
+
+
 # ---------------------------------------------------------------- our arm
 def ours(args, rank, world, local_rank):
     import numpy as np
@@ -509,6 +717,11 @@ def ours(args, rank, world, local_rank):
     build.build()
     from paper_1708_09162_gb300 import ibem
 
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.operator_only and not args.fp32_only \
+            and not (args.batch_only or args.learned_only or args.cnn_forward_only or args.laplace_only
+                     or args.learned_config5):
+        oracle = start_oracle_child()             # CPU only; overlaps the GPU setup below
     torch.cuda.set_device(local_rank)
     dist = world > 1
     if dist:
@@ -520,49 +733,61 @@ def ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     stream = torch.cuda.Stream()
-    if args.helmholtz_many_only:
-        out = helmholtz_many_rhs(ibem, stream, world, barrier, args)
-        if rank == 0:
-            print(json.dumps({"helmholtz_64rhs": out}), flush=True)
-        return
     if args.batch_only:
-        out = batched_instances(ibem, stream, args)
-        if rank == 0:
-            print(json.dumps({"batched_instances": out}), flush=True)
+        print(json.dumps({"batched_instances": batched_instances(ibem, stream, args)}), flush=True)
         return
     if args.cnn_forward_only:
         c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
         out = cnn_forward_timing(ibem, stream, c)
         ibem.ibem_cnn_destroy(c)
-        if rank == 0:
-            print(json.dumps({"cnn_forward": out}), flush=True)
+        print(json.dumps({"cnn_forward": out}), flush=True)
         return
     if args.learned_only:
-        out = learned_preconditioner(ibem, stream, args)
-        if rank == 0:
-            print(json.dumps({"learned_preconditioner": out}), flush=True)
+        print(json.dumps({"learned_preconditioner": learned_preconditioner(ibem, stream, args)}), flush=True)
         return
-    prm = ibem.make_params(WORKLOAD["p"], WORKLOAD["m"], q_cheb=WORKLOAD["q_cheb"], eta=WORKLOAD["eta"])
+    if args.learned_config5:
+        print(json.dumps({"learned_config5": learned_config5(ibem, stream, args)}), flush=True)
+        return
+    if args.laplace_only:
+        print(json.dumps({"laplace": laplace_section(ibem, stream, world, barrier, args.steps, args.warmup)}),
+              flush=True)
+        return
+
+    W = WORKLOAD
+    R = W["nrhs"]
     t0 = time.perf_counter()
-    h = ibem.ibem_create(ibem.sphere_patches(), prm, stream)
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(
+        W["p"], W["m"], q_cheb=W["q_cheb"], eta=W["eta"], kernel=ibem.IBEM_HELMHOLTZ, kappa=W["kappa"],
+        fp64_coupling=ibem.IBEM_COUPLING_GENERATE), stream)
     t_create = time.perf_counter() - t0
     t0 = time.perf_counter()
     ibem.ibem_assemble(h)
     t_assemble = time.perf_counter() - t0
     info = ibem.ibem_get_info(h)
-    N, R = info.ndof, WORKLOAD["nrhs"]
-    rng = np.random.default_rng(SEED + rank)
-    x = torch.from_numpy(rng.normal(size=(R, N))).cuda()
-    y = torch.empty_like(x)
-    y32 = torch.empty_like(x)
+    N = info.ndof
+    b = plane_wave_rhs(ibem, h, W["kappa"], R, SEED + 3)           # [R][N][2]: the 64 plane waves
+    y = torch.empty_like(b)
+    y32 = torch.empty_like(b)
 
-    def run(steps, precision):
+    def run(steps, precision, out):
         with torch.cuda.stream(stream):
             for _ in range(steps):
-                ibem.ibem_matvec(h, x, y if precision == 0 else y32, R, precision)
+                ibem.ibem_matvec(h, b, out, R, precision)
 
-    # ---- FP64 operator: the headline ----
-    run(args.warmup, 0)
+    if args.fp32_only:
+        run(max(1, args.warmup), 1, y32)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        run(args.steps, 1, y32)
+        ev1.record(stream)
+        barrier()
+        print(json.dumps({"fp32_ms": ev0.elapsed_time(ev1) / args.steps}), flush=True)
+        return
+    oracle_res = finish_oracle_child(*oracle) if oracle else None
+
+    # ---- headline: FP64-accurate operator, 64 right-hand sides ----
+    run(args.warmup, 0, y)
     ibem.ibem_profile_read(h)
     barrier()
     clocks = ClockSampler(local_rank)
@@ -570,7 +795,7 @@ def ours(args, rank, world, local_rank):
     ibem.ibem_profile_enable(h, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    run(args.steps, 0)
+    run(args.steps, 0, y)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -579,161 +804,145 @@ def ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = max_over_ranks(ms)
     value = job_throughput(world, N * R, ms * 1e-3)
-
-    # ---- roofline of the dominant kernel ----
-    # coupling_df_kernel streams the double-float coupling matrices (8 bytes per
-    # entry) once and spends 12 FP32-pipe operations per entry (exact product,
-    # two cross terms, TwoSum); its bound is whichever fraction is larger.
     phase_ms = {k: v / args.steps for k, v in prof["ms"].items()}
-    q2 = WORKLOAD["q_cheb"] ** 2
-    kpt = (q2 + 3) // 4
+
+    # ---- roofline of the dominant kernel (helm_coupling_gen_kernel, FP32 pipe) ----
+    _, sm_max, peak_src = _peaks()
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12                      # FP32 lane operations per second (T)
     coup_ms = phase_ms["coupling"]
-    entries = float(q2 * q2 * info.n_far * R)          # matrix entries applied (both halves)
-    # bytes: the stored upper half of K (symmetric storage), the source moments
-    # streamed with every block, column shares written and gathered, y^ written
-    n_up = info.bytes_far // (kpt * 4 * q2 * 8)
-    kbytes = info.bytes_far + n_up * ((q2 + 1) // 2 * 2) * 8 * R + n_up * q2 * 8 * R + \
-        info.n_clusters * q2 * R * 8
-    hbm_gbs, sm_max, peak_src = _peaks()
-    fp32_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12            # FP32 lanes x clock
-    alu_frac = (12.0 * entries / (coup_ms * 1e-3) / 1e12) / fp32_peak_tops
-    hbm_frac = (kbytes / (coup_ms * 1e-3) / 1e9) / hbm_gbs
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": 12.0 * entries / (coup_ms * 1e-3) / 1e12, "peak": fp32_peak_tops,
-                "unit": "Tops/s", "frac": alu_frac,
-                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz (%s clock)" % (sm_max, peak_src)}
-    else:
-        roof = {"bound": "hbm", "achieved": kbytes / (coup_ms * 1e-3) / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": hbm_frac, "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s; of measured)" % peak_src}
-    roof.update({"kernel": "coupling_df_kernel", "ms_per_launch": coup_ms, "traffic": _profile_traffic(),
-                 "algorithmic_bytes": kbytes, "matrix_entries": entries, "flops_equiv_fp64": 2.0 * entries,
-                 "hbm_frac_of_measured": hbm_frac, "fp32_alu_frac": alu_frac})
+    gen_ops, mac_ops = gen_ops_per_launch(info.n_far, W["q_cheb"], R)
+    achieved = (gen_ops + mac_ops) / (coup_ms * 1e-3) / 1e12
+    kvals = info.n_far * float(W["q_cheb"]) ** 4
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+            "traffic": _profile_traffic(), "kernel": "helm_coupling_gen_kernel", "ms_per_launch": coup_ms,
+            "algorithmic_ops": gen_ops + mac_ops, "ops_generation": gen_ops, "ops_multiply_add": mac_ops,
+            "kernel_values": kvals, "kernel_values_per_s": kvals / (coup_ms * 1e-3),
+            "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json, %s)"
+                           % (sm_max, peak_src),
+            "ops_source": "counted from the double-float formulas: 247 FP32 operations per generated complex "
+                          "kernel value, 48 per complex multiply-add and right-hand side"}
 
-    # ---- native FP64 coupling (FP64 FMA pipe), for comparison ----
-    native = None
-    if not args.no_native:
-        hn = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(
-            WORKLOAD["p"], WORKLOAD["m"], q_cheb=WORKLOAD["q_cheb"], eta=WORKLOAD["eta"],
-            fp64_coupling=ibem.IBEM_COUPLING_NATIVE), stream)
-        ibem.ibem_assemble(hn)
-        yn = torch.empty_like(x)
-        nsteps = max(3, args.steps // 4)
-        with torch.cuda.stream(stream):
-            for _ in range(args.warmup):
-                ibem.ibem_matvec(hn, x, yn, R, 0)
-        barrier()
-        ibem.ibem_profile_enable(hn, True)
-        ev0.record(stream)
-        with torch.cuda.stream(stream):
-            for _ in range(nsteps):
-                ibem.ibem_matvec(hn, x, yn, R, 0)
-        ev1.record(stream)
-        barrier()
-        pn = ibem.ibem_profile_read(hn)
-        msn = ev0.elapsed_time(ev1) / nsteps
-        native = {"value": world * N * R / (msn * 1e-3), "ms_per_step": msn,
-                  "coupling_ms": pn["ms"]["coupling"] / nsteps,
-                  "rel_diff_vs_double_float": float((yn - y).abs().max() / y.abs().max())}
-        ibem.ibem_destroy(hn)
-
-    # ---- FP32 operator ----
-    run(args.warmup, 1)
+    # ---- FP32 operator (tensor-core coupling, BF16 K and moments) ----
+    run(args.warmup, 1, y32)
     barrier()
+    ibem.ibem_profile_enable(h, True)
     ev0.record(stream)
-    run(args.steps, 1)
+    run(args.steps, 1, y32)
     ev1.record(stream)
     barrier()
     ms32 = ev0.elapsed_time(ev1) / args.steps
+    p32 = ibem.ibem_profile_read(h)
+    ibem.ibem_profile_enable(h, False)
+    c32 = p32["ms"]["coupling"] / args.steps
     err32 = float((y32 - y).abs().max() / y.abs().max())
+    flops_tc = 2.0 * 128 * 128 * R * info.n_far                      # real-form GEMM per far block
+    tpk, tsrc = _peak_tensor()
+    fp32 = {"value": world * N * R / (ms32 * 1e-3), "ms_per_step": ms32, "coupling_ms": c32,
+            "rel_err_vs_fp64_all_64": err32,
+            "tensor": {"kernel": "mr_coupling_tc_kernel", "achieved_tflops": flops_tc / (c32 * 1e-3) / 1e12,
+                       "peak_tflops": tpk, "frac": flops_tc / (c32 * 1e-3) / 1e12 / tpk,
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (%s)" % tsrc}}
+
+    # ---- both operators against the oracle on sampled rows at full size ----
+    accuracy = None
+    if oracle_res is not None:
+        rows, xs = sampled_input(N)
+        X = np.zeros((16, N), dtype=complex)
+        X[0] = xs
+        X[1:] = np.random.default_rng(SEED + 12).normal(size=(15, N))
+        xd = torch.from_numpy(np.ascontiguousarray(np.stack([X.real, X.imag], -1))).cuda()
+        yd = torch.empty_like(xd)
+        yo = np.array(oracle_res["y"])
+        yo = yo[:, 0] + 1j * yo[:, 1]
+        accuracy = {"rows": len(rows), "rhs": "one seeded complex normal vector (column 0 of a 16-column block)"}
+        for name, prec in (("fp64", 0), ("fp32_tensor_core", 1)):
+            ibem.ibem_matvec(h, xd, yd, 16, prec)
+            torch.cuda.synchronize()
+            yy = yd[0].cpu().numpy()
+            yy = (yy[:, 0] + 1j * yy[:, 1])[rows]
+            accuracy[name] = float(np.max(np.abs(yy - yo)) / np.max(np.abs(yo)))
 
     # ---- end to end through the host-buffer entry point ----
-    xh = torch.empty((R, N), dtype=torch.float64, pin_memory=True)
-    xh.copy_(x.cpu())
-    yh = torch.empty((R, N), dtype=torch.float64, pin_memory=True)
-    e2e_steps = max(3, args.steps // 10)
-    for _ in range(3):
-        ibem.ibem_matvec_host(h, xh, yh, R)
+    bh = torch.empty((R, N, 2), dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    yh = torch.empty((R, N, 2), dtype=torch.float64, pin_memory=True)
+    e2e_steps = max(2, args.steps // 5)
+    ibem.ibem_matvec_host(h, bh, yh, R)
     barrier()
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        ibem.ibem_matvec_host(h, xh, yh, R)
-    e2e_s = (time.perf_counter() - t) / e2e_steps
-    e2e_s = max_over_ranks(e2e_s)
+        ibem.ibem_matvec_host(h, bh, yh, R)
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps)
 
-    # ---- solves to 1e-8 ----
+    # ---- lock-step GMRES of the plane waves to true relative residual 1e-8 ----
     solve = None
-    if not args.no_solve:
-        x0 = np.array([0.9, 0.9, 0.9])
-        qp = torch.empty((info.n_quad_points, 3), dtype=torch.float64, device="cuda")
-        ibem.ibem_quad_points(h, qp)
-        torch.cuda.synchronize()
-        gq = torch.from_numpy(1.0 / (4 * np.pi * np.linalg.norm(qp.cpu().numpy() - x0, axis=1))).cuda()
-        b = torch.empty(N, dtype=torch.float64, device="cuda")
-        ibem.ibem_rhs(h, gq, 1, b)
-        w = torch.empty_like(b)
-        solve = {"rtol": 1e-8, "rhs": "point source 1/(4 pi |x - x0|), x0 = (0.9, 0.9, 0.9)"}
-        for name, pc in (("jacobi", ibem.IBEM_PRECOND_JACOBI), ("block_jacobi", ibem.IBEM_PRECOND_BLOCK_JACOBI)):
-            s64 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precond=pc, precision=0)
-            s32 = ibem.ibem_solve(h, b, w, 1, rtol=1e-8, maxit=5000, precond=pc, precision=1)
-            solve[name] = {"fp64": {"seconds": s64.seconds, "iterations": s64.iterations,
-                                    "rel_residual": s64.rel_residual},
-                           "mixed": {"seconds": s32.seconds, "iterations": s32.iterations,
-                                     "fp64_updates": s32.outer, "rel_residual": s32.rel_residual},
-                           "speedup_mixed_vs_fp64": s64.seconds / s32.seconds}
+    if not args.no_solve and not args.operator_only:
+        solve = {"rtol": 1e-8, "precond": "block-Jacobi", "solver": "lock-step GMRES(100)"}
 
-    # ---- Helmholtz, 64 plane waves: tensor-core coupling ----
-    helm_many = None if args.no_helmholtz_many else helmholtz_many_rhs(ibem, stream, world, barrier, args)
+        def solve_once(nr, prec):
+            w = torch.empty_like(b[:nr])
+            s, si = ibem.ibem_solve(h, b[:nr].contiguous(), w, nr, rtol=1e-8, maxit=5000,
+                                    precond=ibem.IBEM_PRECOND_BLOCK_JACOBI, precision=prec, check=False)
+            return {"status": ibem.ibem_status_string(s), "seconds": si.seconds, "steps": si.steps,
+                    "iterations": si.iterations, "outer": si.outer, "rel_residual_fp64": si.rel_residual}
 
-    # ---- many uneven instances in one application ----
-    batched = None if args.no_batch else batched_instances(ibem, stream, args)
+        solve["mixed_64"] = solve_once(R, 1)
+        solve["mixed_16"] = solve_once(16, 1)
+        if not args.no_fp64_solve:
+            solve["fp64_16"] = solve_once(16, 0)
+            solve["speedup_mixed_vs_fp64_16rhs"] = solve["fp64_16"]["seconds"] / solve["mixed_16"]["seconds"]
 
-    # ---- learned preconditioner vs block-Jacobi ----
-    learned = None if args.no_learned else learned_preconditioner(ibem, stream, args)
+    pot = None if (args.no_potential or args.operator_only) else potentials_section(ibem, stream, h, b)
+    ibem.ibem_destroy(h)
 
-    # ---- oracle on the host cores (rank 0, N = 1) ----
+    lap = None if (args.no_laplace or args.operator_only) else laplace_section(
+        ibem, stream, world, barrier, max(10, args.steps), args.warmup)
+    batched = None if (args.no_batch or args.operator_only) else batched_instances(ibem, stream, args)
+    learned = None if (args.no_learned or args.operator_only) else learned_preconditioner(ibem, stream, args)
+
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        o = run_oracle(3)
-        cpu = {"value": o["rows"] / o["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d rows of the oracle's FMM-mode operator on the same workload (near blocks, "
-                         "far couplings and the moment pass included; tree setup %.1f s excluded)"
-                         % (o["rows"], o["setup_s"])}
+    if oracle_res is not None:
+        cpu = {"value": len(oracle_res["rows"]) / oracle_res["seconds"], "unit": UNIT, "cores": oracle_res["workers"],
+               "cpu": oracle_res["cpu"], "host_cores": oracle_res["cores"], "kind": "oracle",
+               "sample": "%d rows of the oracle's FMM-mode operator of the same workload applied to one right-hand "
+                         "side, one forked worker per core (near blocks and the moments the rows use included; "
+                         "the operator's tree, built once in %.0f s, excluded)"
+                         % (len(oracle_res["rows"]), oracle_res["setup_s"])}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(WORKLOAD, ndof=N, ndof_super=info.ndof_super, n_near=info.n_near, n_far=info.n_far,
+            "vs_baseline": None, "dtype": "f64 (double-float coupling, about 48 bits; FP64 near field)",
+            "data": "synthetic",
+            "config": dict(W, ndof=N, ndof_super=info.ndof_super, n_near=info.n_near, n_far=info.n_far,
                            parallelism="replicas" if world > 1 else "single",
-                           l2="inputs larger than L2: %.1f GB of stored operator streamed per step"
-                              % ((info.bytes_near + info.bytes_far) / 1e9)),
-            "phase_ms": phase_ms,
-            "fp32": {"value": world * N * R / (ms32 * 1e-3), "ms_per_step": ms32, "rel_err_vs_fp64": err32},
-            "fp64_native_coupling": native,
-            "assemble_s": t_assemble, "create_s": t_create,
-            "solve": solve,
+                           l2="inputs larger than L2: %.1f GB of FP64 near blocks and %.1f GB of moments read "
+                              "per step" % (info.bytes_near / 1e9, info.n_far * 64 * R * 16 / 1e9)),
+            "phase_ms": phase_ms, "create_s": t_create, "assemble_s": t_assemble,
             "roofline": roof,
-            "cpu_baseline": cpu,
-            "helmholtz_64rhs": helm_many,
-            "learned_preconditioner": learned,
+            "fp32_tensor_core": fp32,
+            "accuracy_vs_oracle_rows": accuracy,
+            "solve": solve,
+            "potential": pot,
+            "laplace_p3_m5": lap,
             "batched_instances": batched,
-            "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
-                    "d2h_bytes_per_step": N * R * 8},
+            "learned_preconditioner": learned,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * N * R / e2e_s, "unit": UNIT, "h2d_bytes_per_step": N * R * 16,
+                    "d2h_bytes_per_step": N * R * 16},
             "gpu_launches": prof["launches"],
             "clocks": clk}
-    ibem.ibem_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse()
+    if args.oracle_child:
+        oracle_child(args.oracle_child)
+        return
     if args.m is not None:
         WORKLOAD["m"] = args.m
-        WORKLOAD["workload"] = "laplace-sphere-p%d-m%d-q%d-eta%g" % (WORKLOAD["p"], args.m, WORKLOAD["q_cheb"],
-                                                                    WORKLOAD["eta"])
-    if args.oracle_worker:
-        oracle_worker(args.oracle_worker)
-        return
+        WORKLOAD["workload"] = "helmholtz-sphere-p2-m%d-q8-k4-R64" % args.m
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
