@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-potential", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
+    ap.add_argument("--fmm-error-study", action="store_true",
+                    help="run only the FMM-against-dense error study of the Laplace level-5 workload")
     ap.add_argument("--learned-config5", action="store_true",
                     help="run only the learned preconditioner at level 7 with 16 plane waves (several minutes)")
     ap.add_argument("--cnn-forward-only", action="store_true", help="time only the network's forward pass")
@@ -562,6 +564,44 @@ def learned_config5(ibem, stream, args):
             "steps_learned_over_block_jacobi": res["learned"]["steps"] / max(1, res["block_jacobi"]["steps"])}
 
 
+def fmm_error_study(ibem, stream, args):
+    """FMM error of the Laplace degree-3 level-5 workload (q = 6, eta = 1.6)
+    against the dense Galerkin matrix of the same quadrature (every element
+    pair as near field), for both readings of the admissibility condition
+    (Def. 4.1): eta max(diam) < dist (the default) and max(diam) < eta dist.
+    Operator applied to one seeded vector and to the point-source right-hand
+    side; max-norm relative errors over all dofs."""
+    import numpy as np
+    import torch
+    W = LAPLACE
+    x = torch.from_numpy(np.random.default_rng(SEED + 21).normal(size=(1, 7350))).cuda()
+    out = {"workload": W["workload"]}
+    t0 = time.perf_counter()
+    hd = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=0), stream)
+    ibem.ibem_assemble(hd)
+    out["dense_setup_s"] = time.perf_counter() - t0
+    info = ibem.ibem_get_info(hd)
+    out["dense_near_pairs"] = info.n_near
+    yd = torch.empty_like(x)
+    ibem.ibem_matvec(hd, x, yd, 1, 0)
+    torch.cuda.synchronize()
+    ibem.ibem_destroy(hd)
+    for name, adm in (("eta_max_diam_lt_dist", ibem.IBEM_ADMISSIBLE_ETA_DIAM),
+                      ("max_diam_lt_eta_dist", ibem.IBEM_ADMISSIBLE_ETA_DIST)):
+        for q in (4, 6, 8):
+            h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=q, eta=W["eta"],
+                                                                         admissibility=adm), stream)
+            ibem.ibem_assemble(h)
+            inf = ibem.ibem_get_info(h)
+            y = torch.empty_like(x)
+            ibem.ibem_matvec(h, x, y, 1, 0)
+            torch.cuda.synchronize()
+            out["%s_q%d" % (name, q)] = {"n_near": inf.n_near, "n_far": inf.n_far,
+                                         "rel_err_vs_dense": float((y - yd).abs().max() / yd.abs().max())}
+            ibem.ibem_destroy(h)
+    return out
+
+
 def _peak_tensor():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -720,7 +760,7 @@ def ours(args, rank, world, local_rank):
     oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.operator_only and not args.fp32_only \
             and not (args.batch_only or args.learned_only or args.cnn_forward_only or args.laplace_only
-                     or args.learned_config5):
+                     or args.learned_config5 or args.fmm_error_study):
         oracle = start_oracle_child()             # CPU only; overlaps the GPU setup below
     torch.cuda.set_device(local_rank)
     dist = world > 1
@@ -747,6 +787,9 @@ def ours(args, rank, world, local_rank):
         return
     if args.learned_config5:
         print(json.dumps({"learned_config5": learned_config5(ibem, stream, args)}), flush=True)
+        return
+    if args.fmm_error_study:
+        print(json.dumps({"fmm_error_study": fmm_error_study(ibem, stream, args)}), flush=True)
         return
     if args.laplace_only:
         print(json.dumps({"laplace": laplace_section(ibem, stream, world, barrier, args.steps, args.warmup)}),

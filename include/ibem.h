@@ -114,7 +114,14 @@ typedef struct {
     int gauss_singular;  /* Gauss points per variable, Duffy rules (1..12, default 8) */
     int fp64_coupling;   /* storage and arithmetic of the FP64 operator's coupling:
                             IBEM_COUPLING_DF (0, default) or IBEM_COUPLING_NATIVE (1) */
+    int admissibility;   /* reading of Def. 4.1 (printed as max diam < mu dist with
+                            0 < mu < 1, while the workloads give eta = 1.6):
+                            IBEM_ADMISSIBLE_ETA_DIAM (0, default): admissible iff
+                            eta * max(diam) < dist (eta = 1/mu);
+                            IBEM_ADMISSIBLE_ETA_DIST (1): iff max(diam) < eta * dist */
 } ibem_params;
+
+enum { IBEM_ADMISSIBLE_ETA_DIAM = 0, IBEM_ADMISSIBLE_ETA_DIST = 1 };
 
 /* FP64 coupling variants.  GB300 executes FP64 FMA at 1/64 of the FP32 rate, so
  * by default the coupling matrices are stored as unevaluated float pairs
@@ -335,6 +342,23 @@ ibem_status ibem_batch_offsets(const ibem_batch* b, int64_t* offsets);
 ibem_status ibem_batch_matvec(ibem_batch* b, const double* x_dev, double* y_dev);
 /* kernel launches in one application, and the autotuned coupling CTA size. */
 ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads);
+/* Solve A x = b for every instance and right-hand side of the batch (Sec. 4
+ * item 3, for many uneven problems at once): lock-step restarted GMRES(100)
+ * over all columns of the concatenated arrays (layout of ibem_batch_offsets),
+ * each column with its own Krylov space and stopping test, every step one
+ * application of the batched FP32 operator; Laplace columns run the same
+ * GMRES (real).  Outer loop: the residual b - A x with each instance's FP64
+ * operator when every handle has one (the inner cycles then stop at
+ * max(rtol |b|, 1e-3 |r|): iterative refinement to rtol in FP64), otherwise
+ * with the batched FP32 operator (relative tolerances much below 1e-6 are then
+ * out of reach).  precond: IBEM_PRECOND_NONE, JACOBI or BLOCK_JACOBI (each
+ * instance's own).  maxit bounds the lock-step operator applications.
+ * info->rel_residual is the largest relative residual of a column.  During
+ * the call the instances' work runs on the batch stream; the handles must not
+ * be used elsewhere meanwhile.  Synchronises; IBEM_ERR_NOCONV if maxit is
+ * reached. */
+ibem_status ibem_batch_solve(ibem_batch* b, const double* b_dev, double* x_dev, double rtol, int maxit, int precond,
+                             ibem_solve_info* info);
 ibem_status ibem_batch_destroy(ibem_batch* b);
 
 /* Host-only: build the block cluster tree without a GPU and return its lists.

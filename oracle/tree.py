@@ -52,12 +52,17 @@ class ClusterGeometry:
             self._cache[cl] = bounding_ball(self.patches[patch], level, ix, iy)
         return self._cache[cl]
 
-    def admissible(self, s, t, eta):
+    def admissible(self, s, t, eta, reading="eta_diam"):
+        """reading "eta_diam": eta max(diam) < dist (eta = 1/mu, the default);
+        "eta_dist": max(diam) < eta dist (the other way to fit eta = 1.6 into
+        the printed max diam < mu dist)."""
         cs, rs = self.ball(s)
         ct, rt = self.ball(t)
         d = np.sqrt(np.sum((cs - ct) ** 2)) - rs - rt
         dist = d if d > 0.0 else 0.0
         diam = 2.0 * (rs if rs > rt else rt)
+        if reading == "eta_dist":
+            return diam < eta * dist
         return eta * diam < dist
 
 
@@ -66,7 +71,7 @@ def children(cl):
     return [(patch, level + 1, 2 * ix + dx, 2 * iy + dy) for dy in (0, 1) for dx in (0, 1)]
 
 
-def block_cluster_tree(patches, m, eta, cg=None):
+def block_cluster_tree(patches, m, eta, cg=None, reading="eta_diam"):
     """Return (near, far): lists of (sigma, tau) cluster pairs."""
     cg = cg or ClusterGeometry(patches)
     near, far = [], []
@@ -74,7 +79,7 @@ def block_cluster_tree(patches, m, eta, cg=None):
              for i in range(len(patches)) for j in range(len(patches))]
     while stack:
         s, t = stack.pop()
-        if cg.admissible(s, t, eta):
+        if cg.admissible(s, t, eta, reading):
             far.append((s, t))
         elif s[1] == m:
             near.append((s, t))

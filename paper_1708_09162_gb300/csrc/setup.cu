@@ -221,6 +221,8 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.m < 0 || q.m > 10) return "m must be in 0..10";
     if (q.q_cheb != 0 && (q.q_cheb < 2 || q.q_cheb > IBEM_MAX_Q)) return "q_cheb must be 0 or 2..12";
     if (q.q_cheb != 0 && !(q.eta > 0.0)) return "eta must be > 0";
+    if (q.admissibility != IBEM_ADMISSIBLE_ETA_DIAM && q.admissibility != IBEM_ADMISSIBLE_ETA_DIST)
+        return "admissibility must be IBEM_ADMISSIBLE_ETA_DIAM or IBEM_ADMISSIBLE_ETA_DIST";
     if (q.gauss_regular < 1 || q.gauss_regular > IBEM_MAX_GAUSS) return "gauss_regular must be in 1..40";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
@@ -338,7 +340,7 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
         if (compress) {
             double dist = ball_dist(bs, bt);
             double diam = 2.0 * (bs.r > bt.r ? bs.r : bt.r);
-            adm = eta * diam < dist;
+            adm = q.admissibility == IBEM_ADMISSIBLE_ETA_DIST ? diam < eta * dist : eta * diam < dist;
         }
         if (adm) {
             far.push_back({(int32_t)st.first, (int32_t)st.second});

@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "gmres_column.h"
 #include "ibem_internal.cuh"
 
 namespace ibem {
@@ -294,14 +295,10 @@ ibem_status gmres_cycle(Ctx& c, int Ra, const double* r, double* d, const std::v
     if (nact == 0) return IBEM_OK;
     if (c.upload(scale, c.d_red) != cudaSuccess) return IBEM_ERR_CUDA;
     bscale_kernel<<<nb_((int64_t)Ra * M, 256), 256, 0, st>>>(r, c.d_red, M, Ra, V);
-    // per column: Hessenberg (rotated), rotations, g
-    std::vector<std::vector<double>> H(Ra, std::vector<double>((size_t)(m + 1) * m * 2, 0.0));
-    std::vector<std::vector<double>> g(Ra, std::vector<double>(2 * (m + 1), 0.0));
-    std::vector<std::vector<double>> cs(Ra, std::vector<double>(m)), sr(Ra, std::vector<double>(m)),
-        si(Ra, std::vector<double>(m));
-    for (int q = 0; q < Ra; ++q) g[q][0] = beta[q];
+    std::vector<GmresColumn> col(Ra);
+    for (int q = 0; q < Ra; ++q) col[q].start(m, beta[q]);
     int j = 0;
-    std::vector<double> hb;
+    std::vector<double> hb, hq;
     for (; j < m && nact > 0 && *steps < max_steps; ++j) {
         double* Vj = V + (size_t)j * Ra * M;
         double* zj = flex ? Z + (size_t)j * Ra * M : tmp;
@@ -331,47 +328,18 @@ ibem_status gmres_cycle(Ctx& c, int Ra, const double* r, double* d, const std::v
         for (int q = 0; q < Ra; ++q) {
             scale[q] = 0.0;
             if (!active[q]) continue;
-            auto Hr = [&](int i, int k) -> double& { return H[q][2 * ((size_t)i * m + k)]; };
-            auto Hi = [&](int i, int k) -> double& { return H[q][2 * ((size_t)i * m + k) + 1]; };
+            hq.assign(2 * (j + 1), 0.0);
             for (int i = 0; i <= j; ++i) {
-                Hr(i, j) = hb[2 * ((size_t)i * Ra + q)] + hb[(size_t)2 * (j + 1) * Ra + 2 * ((size_t)i * Ra + q)];
-                Hi(i, j) = hb[2 * ((size_t)i * Ra + q) + 1] +
-                           hb[(size_t)2 * (j + 1) * Ra + 2 * ((size_t)i * Ra + q) + 1];
+                hq[2 * i] = hb[2 * ((size_t)i * Ra + q)] + hb[(size_t)2 * (j + 1) * Ra + 2 * ((size_t)i * Ra + q)];
+                hq[2 * i + 1] = hb[2 * ((size_t)i * Ra + q) + 1] +
+                                hb[(size_t)2 * (j + 1) * Ra + 2 * ((size_t)i * Ra + q) + 1];
             }
             const double hnq = std::sqrt(hb[(size_t)4 * (j + 1) * Ra + q]);
             if (!std::isfinite(hnq)) return IBEM_ERR_BREAKDOWN;
-            Hr(j + 1, j) = hnq;
-            Hi(j + 1, j) = 0.0;
-            for (int i = 0; i < j; ++i) {
-                const double ar = Hr(i, j), ai = Hi(i, j), br = Hr(i + 1, j), bi = Hi(i + 1, j);
-                Hr(i, j) = cs[q][i] * ar + (sr[q][i] * br - si[q][i] * bi);
-                Hi(i, j) = cs[q][i] * ai + (sr[q][i] * bi + si[q][i] * br);
-                Hr(i + 1, j) = -(sr[q][i] * ar + si[q][i] * ai) + cs[q][i] * br;
-                Hi(i + 1, j) = -(sr[q][i] * ai - si[q][i] * ar) + cs[q][i] * bi;
-            }
-            const double ar = Hr(j, j), ai = Hi(j, j), bb = hnq;
-            const double na = std::sqrt(ar * ar + ai * ai), den = std::sqrt(na * na + bb * bb);
-            if (den == 0.0) return IBEM_ERR_BREAKDOWN;
-            if (na == 0.0) {
-                cs[q][j] = 0.0; sr[q][j] = 1.0; si[q][j] = 0.0;
-            } else {
-                cs[q][j] = na / den;
-                sr[q][j] = (ar / na) * bb / den;
-                si[q][j] = (ai / na) * bb / den;
-            }
-            Hr(j, j) = cs[q][j] * ar + sr[q][j] * bb;
-            Hi(j, j) = cs[q][j] * ai + si[q][j] * bb;
-            Hr(j + 1, j) = 0.0;
-            Hi(j + 1, j) = 0.0;
-            const double gr = g[q][2 * j], gi = g[q][2 * j + 1];
-            g[q][2 * j] = cs[q][j] * gr;
-            g[q][2 * j + 1] = cs[q][j] * gi;
-            g[q][2 * (j + 1)] = -(sr[q][j] * gr + si[q][j] * gi);
-            g[q][2 * (j + 1) + 1] = -(sr[q][j] * gi - si[q][j] * gr);
+            const double res = col[q].add(j, hq.data(), hnq);
+            if (res < 0.0) return IBEM_ERR_BREAKDOWN;
             kr[q] = j + 1;
             ++its[q];
-            const double res = std::hypot(g[q][2 * (j + 1)], g[q][2 * (j + 1) + 1]);
-            if (!std::isfinite(res)) return IBEM_ERR_BREAKDOWN;
             if (res <= tol[q] || hnq == 0.0) {
                 active[q] = 0;
                 --nact;
@@ -386,23 +354,10 @@ ibem_status gmres_cycle(Ctx& c, int Ra, const double* r, double* d, const std::v
     // back substitution per column, y [K][Ra][2] (zero beyond each column's k)
     const int K = j;
     if (K == 0) return IBEM_OK;
-    std::vector<double> y((size_t)2 * K * Ra, 0.0);
+    std::vector<double> y((size_t)2 * K * Ra, 0.0), yy;
     for (int q = 0; q < Ra; ++q) {
-        const int k = kr[q];
-        auto Hr = [&](int i, int kk) { return H[q][2 * ((size_t)i * m + kk)]; };
-        auto Hi = [&](int i, int kk) { return H[q][2 * ((size_t)i * m + kk) + 1]; };
-        std::vector<double> yy(2 * k, 0.0);
-        for (int i = k - 1; i >= 0; --i) {
-            double s_r = g[q][2 * i], s_i = g[q][2 * i + 1];
-            for (int l = i + 1; l < k; ++l) {
-                s_r -= Hr(i, l) * yy[2 * l] - Hi(i, l) * yy[2 * l + 1];
-                s_i -= Hr(i, l) * yy[2 * l + 1] + Hi(i, l) * yy[2 * l];
-            }
-            const double dr = Hr(i, i), di = Hi(i, i), den = dr * dr + di * di;
-            yy[2 * i] = (s_r * dr + s_i * di) / den;
-            yy[2 * i + 1] = (s_i * dr - s_r * di) / den;
-        }
-        for (int i = 0; i < k; ++i) {
+        col[q].solve(yy);
+        for (int i = 0; i < col[q].k; ++i) {
             y[2 * ((size_t)i * Ra + q)] = yy[2 * i];
             y[2 * ((size_t)i * Ra + q) + 1] = yy[2 * i + 1];
         }

@@ -32,6 +32,7 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_profile_read", "ibem_set_wait_limit", "ibem_device_status", "ibem_potential_noalloc",
             "ibem_potential_fmm",
             "ibem_batch_create", "ibem_batch_offsets", "ibem_batch_matvec", "ibem_batch_info", "ibem_batch_destroy",
+            "ibem_batch_solve",
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
             "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
@@ -56,7 +57,7 @@ class ibem_patch(ctypes.Structure):
 class ibem_params(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("kappa", ctypes.c_double), ("p", ctypes.c_int), ("m", ctypes.c_int),
                 ("q_cheb", ctypes.c_int), ("eta", ctypes.c_double), ("gauss_regular", ctypes.c_int),
-                ("gauss_singular", ctypes.c_int), ("fp64_coupling", ctypes.c_int)]
+                ("gauss_singular", ctypes.c_int), ("fp64_coupling", ctypes.c_int), ("admissibility", ctypes.c_int)]
 
 
 class ibem_info(ctypes.Structure):
@@ -106,6 +107,7 @@ def _load():
         "ibem_batch_matvec": (I32, [P, P, P]),
         "ibem_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "ibem_batch_destroy": (I32, [P]),
+        "ibem_batch_solve": (I32, [P, P, P, ctypes.c_double, I32, I32, ctypes.POINTER(ibem_solve_info)]),
         "ibem_device_status": (I32, [P, ctypes.POINTER(I32)]),
         "ibem_cnn_create": (I32, [I32, ctypes.c_ulonglong, P, ctypes.POINTER(P)]),
         "ibem_cnn_destroy": (I32, [P]),
@@ -208,9 +210,13 @@ def nurbs_patches(specs):
 IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERATE = 0, 1, 2, 3
 
 
+IBEM_ADMISSIBLE_ETA_DIAM, IBEM_ADMISSIBLE_ETA_DIST = 0, 1
+
+
 def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8,
-                fp64_coupling=IBEM_COUPLING_DF):
-    return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular, fp64_coupling)
+                fp64_coupling=IBEM_COUPLING_DF, admissibility=IBEM_ADMISSIBLE_ETA_DIAM):
+    return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular, fp64_coupling,
+                       admissibility)
 
 
 # ---- entry points --------------------------------------------------------------------
@@ -344,6 +350,17 @@ def ibem_batch_info(b):
 
 def ibem_batch_destroy(b):
     _check(_lib.ibem_batch_destroy(b))
+
+
+def ibem_batch_solve(b, rhs, x, rtol=1e-8, maxit=2000, precond=IBEM_PRECOND_JACOBI, check=True):
+    """Concatenated right-hand sides and solutions (float64 CUDA, ibem_batch_offsets
+    layout); returns info, or (status, info) with check=False."""
+    info = ibem_solve_info()
+    s = _lib.ibem_batch_solve(b, _dptr(rhs), _dptr(x), rtol, maxit, precond, ctypes.byref(info))
+    if check:
+        _check(s)
+        return info
+    return s, info
 
 
 def ibem_last_error(h=None):

@@ -67,3 +67,44 @@ def test_coupling_none_refuses_fp64():
     assert ei.value.status == "IBEM_ERR_STATE"
     ibem.ibem_matvec(h, x, y, 1, 1)        # FP32 operator still available
     ibem.ibem_destroy(h)
+
+
+def test_batch_solve_against_single_instance_solves():
+    # every instance of the uneven batch solved in lock step through the batched
+    # operator (FP64 residual refinement), against each instance's own solve
+    import torch
+    ibem = lib()
+    handles = []
+    for kern, kappa, p, m, q, R, rad, cen in SPECS:
+        h = ibem.ibem_create(ibem.sphere_patches(rad, cen), ibem.make_params(p, m, q_cheb=q, eta=1.6, kernel=kern,
+                                                                             kappa=kappa))
+        ibem.ibem_assemble(h)
+        handles.append(h)
+    nrhs = [s[5] for s in SPECS]
+    b = ibem.ibem_batch_create(handles, nrhs)
+    off = ibem.ibem_batch_offsets(b, len(handles))
+    rng = np.random.default_rng(7)
+    rhs = torch.from_numpy(rng.normal(size=off[-1])).cuda()
+    rhs[off[2]:off[3]] = 0.0                                   # an instance with a zero right-hand side
+    x = torch.full_like(rhs, np.nan)
+    for precond in (ibem.IBEM_PRECOND_JACOBI, ibem.IBEM_PRECOND_BLOCK_JACOBI):
+        info = ibem.ibem_batch_solve(b, rhs, x, rtol=1e-9, maxit=3000, precond=precond)
+        assert info.rel_residual <= 1e-9 and info.outer >= 2, (info.rel_residual, info.outer)
+        assert torch.all(x[off[2]:off[3]] == 0.0)
+        for i, (h, spec) in enumerate(zip(handles, SPECS)):
+            if i == 2:
+                continue
+            R = spec[5]
+            bi = rhs[off[i]:off[i + 1]].contiguous()
+            xi = torch.empty_like(bi)
+            ibem.ibem_solve(h, bi, xi, R, rtol=1e-11, maxit=3000, precond=precond)
+            xb = x[off[i]:off[i + 1]]
+            assert rel_err(xb.cpu().numpy(), xi.cpu().numpy()) < 1e-6, (i, rel_err(xb.cpu().numpy(), xi.cpu().numpy()))
+            # residual of the batch solution with the instance's FP64 operator
+            y = torch.empty_like(bi)
+            ibem.ibem_matvec(h, xb.contiguous(), y, R, 0)
+            res = (y - bi).reshape(R, -1).norm(dim=1) / bi.reshape(R, -1).norm(dim=1)
+            assert float(res.max()) <= 1.0001e-9, (i, float(res.max()))
+    ibem.ibem_batch_destroy(b)
+    for h in handles:
+        ibem.ibem_destroy(h)

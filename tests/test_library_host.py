@@ -28,10 +28,10 @@ def test_exports_every_declared_symbol(ibem):
         assert hasattr(lib, name), name
 
 
-def _oracle_lists(patches_py, p, m, eta):
+def _oracle_lists(patches_py, p, m, eta, reading="eta_diam"):
     from oracle import galerkin, tree
     disc = galerkin.Discretisation(patches_py, p, m, galerkin.LaplaceKernel())
-    near, far = tree.block_cluster_tree(patches_py, m, eta)
+    near, far = tree.block_cluster_tree(patches_py, m, eta, reading=reading)
     cls_code = {"identical": 0, "edge": 1, "vertex": 2, "nearsing": 3, "regular": 4}
     rows = []
     for s, t in near:
@@ -48,6 +48,18 @@ def test_block_tree_equals_oracle_sphere(ibem, sphere, p, m):
     onear, ofar = _oracle_lists(sphere, p, m, 1.6)
     assert sorted(map(tuple, near.tolist())) == onear
     assert sorted(map(tuple, far.tolist())) == ofar
+
+
+def test_block_tree_alternative_admissibility_reading(ibem, sphere):
+    # Def. 4.1 read as max(diam) < eta dist: many more far blocks, lists equal
+    # the oracle's with the same reading
+    prm = ibem.make_params(1, 3, q_cheb=6, eta=1.6, admissibility=ibem.IBEM_ADMISSIBLE_ETA_DIST)
+    near, far = ibem.ibem_block_tree(ibem.sphere_patches(), prm)
+    onear, ofar = _oracle_lists(sphere, 1, 3, 1.6, reading="eta_dist")
+    assert sorted(map(tuple, near.tolist())) == onear
+    assert sorted(map(tuple, far.tolist())) == ofar
+    near0, _ = ibem.ibem_block_tree(ibem.sphere_patches(), ibem.make_params(1, 3, q_cheb=6, eta=1.6))
+    assert len(near) < len(near0)
 
 
 def test_block_tree_equals_oracle_perturbed_sphere(ibem):
