@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-potential", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner section")
     ap.add_argument("--learned-only", action="store_true", help="run only the learned-preconditioner section")
+    ap.add_argument("--config4", action="store_true",
+                    help="run only the 256-instance batched workload (several minutes of setup)")
     ap.add_argument("--fmm-error-study", action="store_true",
                     help="run only the FMM-against-dense error study of the Laplace level-5 workload")
     ap.add_argument("--learned-config5", action="store_true",
@@ -354,7 +356,8 @@ def batched_instances(ibem, stream, args):
     return {"instances": len(handles), "dof_rhs_per_apply": dofs, "setup_s": setup_s,
             "batched_ms": batched_ms, "one_by_one_ms": single_ms, "speedup": single_ms / batched_ms,
             "value": dofs / (batched_ms * 1e-3), "unit": UNIT, "rel_diff_batched_vs_one_by_one": diff,
-            "launches_per_apply": info["launches_per_apply"], "coupling_threads": info["coupling_threads"]}
+            "launches_per_apply": info["launches_per_apply"], "coupling_threads": info["coupling_threads"],
+            "coupling_rhs_tile": info["coupling_rhs_tile"]}
 
 
 def cnn_forward_timing(ibem, stream, c):
@@ -505,12 +508,14 @@ def learned_config5(ibem, stream, args):
     """Learned preconditioner at the 101,400-dof workload: Helmholtz sound-soft
     scattering on the unit sphere, p = 2, level 7, q = 8, kappa drawn uniformly
     from [8, 16] (resonance filter: no draw within 0.02 of a zero of j_l,
-    l <= 20), 16 seeded plane waves.  The network (4 layers, 32 channels, BF16)
-    is trained on the plain solver's residuals at levels 5 and 6 (q = 6, three
-    wavenumbers each, two plane waves, residual-norm objective); then lock-step
-    flexible GMRES(100) with it is compared with block-Jacobi GMRES(100), both
-    with the FP32 operator (tensor-core coupling) inside iterative refinement
-    and judged by the FP64 true residual 1e-8 of every right-hand side."""
+    l <= 20), 16 seeded plane waves.  Two networks (4 layers, 32 channels, BF16)
+    are trained on the plain solver's residuals at levels 5 and 6 (q = 6, three
+    wavenumbers each, two plane waves, residual-norm objective): one on the fine
+    coefficient images, one on the coarse grid with f = 2^(m - 4) (the level-4
+    grid at every level).  Lock-step flexible GMRES(100) with each is compared
+    with block-Jacobi GMRES(100), all with the FP32 operator (tensor-core
+    coupling) inside iterative refinement and judged by the FP64 true residual
+    1e-8 of every right-hand side."""
     import numpy as np
     import torch
     rng = np.random.default_rng(SEED + 13)
@@ -524,7 +529,8 @@ def learned_config5(ibem, stream, args):
         ibem.ibem_assemble(h)
         return h
 
-    c = ibem.ibem_cnn_create(32, seed=SEED, stream=stream)
+    nets = {"fine": ibem.ibem_cnn_create(32, seed=SEED, stream=stream),
+            "coarse": ibem.ibem_cnn_create(32, seed=SEED, stream=stream)}
     t0 = time.perf_counter()
     train = []
     for m in (5, 6):
@@ -537,8 +543,12 @@ def learned_config5(ibem, stream, args):
             r = torch.zeros((2 * 60, info.ndof, 2), dtype=torch.float64, device="cuda")
             _, n, _ = ibem.ibem_solver_residuals(h, b, 2, r, rtol=1e-10, maxit=600, stride=1, max_vecs=60,
                                                  check=False)
-            l1 = ibem.ibem_cnn_train_operator(h, c, r, n, batch=16, epochs=6, lr=1e-3, seed=len(train))
-            train.append({"level": m, "k": k, "vectors": n, "objective_after": l1})
+            rec = {"level": m, "k": k, "vectors": n}
+            for name, c in nets.items():
+                ibem.ibem_cnn_set_coarsening(c, 2 ** (m - 4) if name == "coarse" else 1)
+                rec["objective_after_" + name] = ibem.ibem_cnn_train_operator(h, c, r, n, batch=16, epochs=6,
+                                                                              lr=1e-3, seed=len(train))
+            train.append(rec)
             ibem.ibem_destroy(h)
     train_s = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -547,9 +557,12 @@ def learned_config5(ibem, stream, args):
     info = ibem.ibem_get_info(h)
     R = 16
     b = plane_wave_rhs(ibem, h, k_solve, R, SEED + 14)
+    ibem.ibem_cnn_set_coarsening(nets["coarse"], 2 ** (7 - 4))
     res = {}
-    for name, pc in (("block_jacobi", ibem.IBEM_PRECOND_BLOCK_JACOBI), ("learned", ibem.IBEM_PRECOND_LEARNED)):
-        ibem.ibem_set_learned_preconditioner(h, c if pc == ibem.IBEM_PRECOND_LEARNED else None)
+    for name, pc, c in (("block_jacobi", ibem.IBEM_PRECOND_BLOCK_JACOBI, None),
+                        ("learned_fine", ibem.IBEM_PRECOND_LEARNED, nets["fine"]),
+                        ("learned_coarse", ibem.IBEM_PRECOND_LEARNED, nets["coarse"])):
+        ibem.ibem_set_learned_preconditioner(h, c)
         w = torch.empty_like(b)
         s, si = ibem.ibem_solve(h, b, w, R, rtol=1e-8, maxit=4000, precond=pc, precision=ibem.IBEM_FP32,
                                 check=False)
@@ -557,49 +570,13 @@ def learned_config5(ibem, stream, args):
                      "outer": si.outer, "rel_residual_fp64": si.rel_residual, "seconds": si.seconds}
     ibem.ibem_set_learned_preconditioner(h, None)
     ibem.ibem_destroy(h)
-    ibem.ibem_cnn_destroy(c)
+    for c in nets.values():
+        ibem.ibem_cnn_destroy(c)
+    bjs = max(1, res["block_jacobi"]["steps"])
     return {"workload": "helmholtz-sphere-p2-m7-q8-R16, kappa from [8, 16]", "k_solve": k_solve,
             "k_rejected_by_filter": rejected, "ndof": info.ndof, "n_far": info.n_far, "setup_s": setup_s,
             "train": train, "train_s": train_s, "solve": res,
-            "steps_learned_over_block_jacobi": res["learned"]["steps"] / max(1, res["block_jacobi"]["steps"])}
-
-
-def fmm_error_study(ibem, stream, args):
-    """FMM error of the Laplace degree-3 level-5 workload (q = 6, eta = 1.6)
-    against the dense Galerkin matrix of the same quadrature (every element
-    pair as near field), for both readings of the admissibility condition
-    (Def. 4.1): eta max(diam) < dist (the default) and max(diam) < eta dist.
-    Operator applied to one seeded vector and to the point-source right-hand
-    side; max-norm relative errors over all dofs."""
-    import numpy as np
-    import torch
-    W = LAPLACE
-    x = torch.from_numpy(np.random.default_rng(SEED + 21).normal(size=(1, 7350))).cuda()
-    out = {"workload": W["workload"]}
-    t0 = time.perf_counter()
-    hd = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=0), stream)
-    ibem.ibem_assemble(hd)
-    out["dense_setup_s"] = time.perf_counter() - t0
-    info = ibem.ibem_get_info(hd)
-    out["dense_near_pairs"] = info.n_near
-    yd = torch.empty_like(x)
-    ibem.ibem_matvec(hd, x, yd, 1, 0)
-    torch.cuda.synchronize()
-    ibem.ibem_destroy(hd)
-    for name, adm in (("eta_max_diam_lt_dist", ibem.IBEM_ADMISSIBLE_ETA_DIAM),
-                      ("max_diam_lt_eta_dist", ibem.IBEM_ADMISSIBLE_ETA_DIST)):
-        for q in (4, 6, 8):
-            h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=q, eta=W["eta"],
-                                                                         admissibility=adm), stream)
-            ibem.ibem_assemble(h)
-            inf = ibem.ibem_get_info(h)
-            y = torch.empty_like(x)
-            ibem.ibem_matvec(h, x, y, 1, 0)
-            torch.cuda.synchronize()
-            out["%s_q%d" % (name, q)] = {"n_near": inf.n_near, "n_far": inf.n_far,
-                                         "rel_err_vs_dense": float((y - yd).abs().max() / yd.abs().max())}
-            ibem.ibem_destroy(h)
-    return out
+            "steps_over_block_jacobi": {k: v["steps"] / bjs for k, v in res.items()}}
 
 
 def _peak_tensor():
@@ -760,7 +737,7 @@ def ours(args, rank, world, local_rank):
     oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.operator_only and not args.fp32_only \
             and not (args.batch_only or args.learned_only or args.cnn_forward_only or args.laplace_only
-                     or args.learned_config5 or args.fmm_error_study):
+                     or args.learned_config5 or args.fmm_error_study or args.config4):
         oracle = start_oracle_child()             # CPU only; overlaps the GPU setup below
     torch.cuda.set_device(local_rank)
     dist = world > 1
@@ -790,6 +767,9 @@ def ours(args, rank, world, local_rank):
         return
     if args.fmm_error_study:
         print(json.dumps({"fmm_error_study": fmm_error_study(ibem, stream, args)}), flush=True)
+        return
+    if args.config4:
+        print(json.dumps({"config4": config4_section(ibem, stream, args)}), flush=True)
         return
     if args.laplace_only:
         print(json.dumps({"laplace": laplace_section(ibem, stream, world, barrier, args.steps, args.warmup)}),

@@ -131,7 +131,8 @@ enum { IBEM_ADMISSIBLE_ETA_DIAM = 0, IBEM_ADMISSIBLE_ETA_DIST = 1 };
  * generates the coupling on the fly in FP64 (also chosen automatically when the
  * stored complex matrices would exceed half of the free device memory).  All
  * variants reproduce the FP64 oracle to 1e-12. */
-enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, IBEM_COUPLING_GENERATE = 3 };
+enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, IBEM_COUPLING_GENERATE = 3,
+       IBEM_COUPLING_FP32_ONLY = 4 };
 /* IBEM_COUPLING_NONE stores no FP64 coupling matrices (memory for large
  * batches): the FP32 operator is available; the FP64 operator of a Laplace
  * handle then returns IBEM_ERR_STATE, Helmholtz generates it on the fly.
@@ -143,7 +144,12 @@ enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, I
  * stored matrices would not fit, for q <= 8 and a phase kappa |x - y| below
  * 90 on every far block;
  * otherwise the generation runs in native FP64 per right-hand side.  A Laplace
- * handle treats GENERATE like IBEM_COUPLING_DF. */
+ * handle treats GENERATE like IBEM_COUPLING_DF.
+ * IBEM_COUPLING_FP32_ONLY (memory for large batches): the FP64 near blocks are
+ * released at the end of ibem_assemble, after the FP32 copy, the Jacobi
+ * diagonal and the block-Jacobi inverses are formed from them, and no FP64
+ * coupling is stored; only the FP32 operator is available (the FP64 operator,
+ * ibem_solve and the training entry points return IBEM_ERR_STATE). */
 
 typedef struct {
     int64_t ndof;          /* dim S_{p,m} = n (2^m + p)^2                          */
@@ -340,8 +346,11 @@ ibem_status ibem_batch_offsets(const ibem_batch* b, int64_t* offsets);
 /* y = A x for every instance (FP32 operator, FP64 in and out), enqueued on the
  * batch stream as one graph launch (captured on first use for this (x, y) pair). */
 ibem_status ibem_batch_matvec(ibem_batch* b, const double* x_dev, double* y_dev);
-/* kernel launches in one application, and the autotuned coupling CTA size. */
-ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads);
+/* kernel launches in one application and the autotuned shape of the coupling
+ * kernel: CTA size and right-hand sides per work item (4, 8 or 16).  Any
+ * output may be null. */
+ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads,
+                            int* coupling_rhs_tile);
 /* Solve A x = b for every instance and right-hand side of the batch (Sec. 4
  * item 3, for many uneven problems at once): lock-step restarted GMRES(100)
  * over all columns of the concatenated arrays (layout of ibem_batch_offsets),
@@ -444,6 +453,16 @@ ibem_status ibem_cnn_device_status(ibem_cnn* cnn, int* status);
 
 /* Kernel launches of the network since the last call (then reset). */
 ibem_status ibem_cnn_launches(ibem_cnn* cnn, int64_t* launches);
+
+/* Coarse-grid variant of the preconditioner (factor f, 1..64; 1 = the fine
+ * grid, the default): the network sees each patch image averaged over blocks
+ * of f x f pixels (ragged blocks at the far edge average the pixels they hold)
+ * and its correction is spread back over the blocks (piecewise constant):
+ * z = s + sigma P net(R(s / sigma)); with f = 2^(m - l) it always sees the
+ * level-l grid of a level-m discretisation.  Applies to the preconditioner and
+ * to the residual-norm objective (ibem_cnn_operator_gradients,
+ * ibem_cnn_train_operator), whose gradient passes through P^T (block sums). */
+ibem_status ibem_cnn_set_coarsening(ibem_cnn* cnn, int factor);
 
 /* Attach (or with NULL detach) a network as the learned preconditioner of a
  * Helmholtz handle.  The handle does not own it. */

@@ -25,11 +25,22 @@ net(x_j) and the complex linear A, dL / d(real, imag of z_j) is
 A^H (A z_j - r_j) / nb, and dL / d(net output of x_j) is sigma_j times that,
 in the real / imaginary channels.
 
+Coarse-grid variant (coarsening factor f >= 1; f = 1 is the above): the
+network sees each patch image averaged over blocks of f x f pixels (ragged
+blocks at the far edge average the pixels they hold), R, and its output is
+spread back over the blocks, P (piecewise constant):
+    z = s + sigma * P net(R(s / sigma)).
+The receptive field of the four 3 x 3 layers then spans 9 f pixels, so the
+network can act on the smooth, patch-wide part of the error that block-Jacobi
+leaves; with f = 2^(m - l) it always sees the level-l grid.  The gradient with
+respect to the network output is P^T of the fine one (block sums).
+
 Pinned by: the block groups cover every dof once and follow the anchor
 elements, a network whose last layer is zero gives block-Jacobi exactly, z is
 homogeneous of degree one in v, a training pair rebuilds e from its input and
 target, and the gradient of the residual-norm objective against central
-differences (tests/test_oracle_cnn.py).
+differences, with f = 1 and f = 2 on ragged images; R P is the identity and P
+is the adjoint of the block sum (tests/test_oracle_cnn.py).
 """
 import numpy as np
 
@@ -78,13 +89,51 @@ def rms(s):
     return np.linalg.norm(s) / np.sqrt(2.0 * s.shape[0])
 
 
-def learned_apply(v, bj, params, C, n1):
+def coarse_size(n1, f):
+    return -(-n1 // f)
+
+
+def restrict(img, f):
+    """Mean over f x f pixel blocks: [B, c, n1, n1] -> [B, c, nc, nc]."""
+    if f == 1:
+        return img
+    B, c, n1, _ = img.shape
+    nc = coarse_size(n1, f)
+    out = np.zeros((B, c, nc, nc))
+    for Y in range(nc):
+        for X in range(nc):
+            blk = img[:, :, Y * f:(Y + 1) * f, X * f:(X + 1) * f]
+            out[:, :, Y, X] = blk.mean(axis=(2, 3))
+    return out
+
+
+def prolong(img, f, n1):
+    """Piecewise constant: fine pixel (y, x) takes coarse pixel (y // f, x // f)."""
+    if f == 1:
+        return img
+    idx = np.arange(n1) // f
+    return img[:, :, idx][:, :, :, idx]
+
+
+def prolong_adjoint(img, f, nc):
+    """P^T: sums over the f x f blocks."""
+    if f == 1:
+        return img
+    B, c, n1, _ = img.shape
+    out = np.zeros((B, c, nc, nc))
+    for Y in range(nc):
+        for X in range(nc):
+            out[:, :, Y, X] = img[:, :, Y * f:(Y + 1) * f, X * f:(X + 1) * f].sum(axis=(2, 3))
+    return out
+
+
+def learned_apply(v, bj, params, C, n1, f=1):
     s = bj(v)
     sigma = rms(s)
     if sigma == 0.0:
         return s
-    out = cnn.forward(params, cnn.vector_to_images(s / sigma, n1), C)
-    return s + sigma * cnn.images_to_vector(out)
+    out = cnn.forward(params, restrict(cnn.vector_to_images(s / sigma, n1), f), C)
+    return s + sigma * cnn.images_to_vector(prolong(out, f, n1))
 
 
 def training_pair(r, e, bj, n1):
@@ -94,21 +143,22 @@ def training_pair(r, e, bj, n1):
     return cnn.vector_to_images(s / sigma, n1), cnn.vector_to_images((e - s) / sigma, n1)
 
 
-def operator_loss_and_grad(params, rs, apply_A, apply_AH, bj, C, n1):
-    """L = 1/(2 nb) sum_j |A (s_j + sigma_j net(s_j / sigma_j)) - r_j|^2 and
+def operator_loss_and_grad(params, rs, apply_A, apply_AH, bj, C, n1, f=1):
+    """L = 1/(2 nb) sum_j |A (s_j + sigma_j P net(R(s_j / sigma_j))) - r_j|^2 and
     dL/dparams for residuals rs [nb, N] (complex)."""
     nb = rs.shape[0]
     ss = [bj(r) for r in rs]
     sig = [rms(s) for s in ss]
-    X = np.concatenate([cnn.vector_to_images(s / g, n1) for s, g in zip(ss, sig)])
+    X = np.concatenate([restrict(cnn.vector_to_images(s / g, n1), f) for s, g in zip(ss, sig)])
     out, acts, pres = cnn.forward(params, X, C, keep=True)
     npatch = X.shape[0] // nb
+    nc = coarse_size(n1, f)
     loss = 0.0
     gout = np.zeros_like(out)
     for j in range(nb):
         sl = slice(j * npatch, (j + 1) * npatch)
-        z = ss[j] + sig[j] * cnn.images_to_vector(out[sl])
+        z = ss[j] + sig[j] * cnn.images_to_vector(prolong(out[sl], f, n1))
         res = apply_A(z) - rs[j]
         loss += 0.5 * np.vdot(res, res).real / nb
-        gout[sl] = sig[j] * cnn.vector_to_images(apply_AH(res) / nb, n1)
+        gout[sl] = sig[j] * prolong_adjoint(cnn.vector_to_images(apply_AH(res) / nb, n1), f, nc)
     return loss, cnn.backward(params, acts, pres, gout, C)

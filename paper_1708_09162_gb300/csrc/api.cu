@@ -119,9 +119,19 @@ ibem_status check_ready(ibem_handle* h) {
 
 cudaError_t set_device(ibem_handle* h) { return cudaSetDevice(h->device); }
 
+// Errors of the patch description and the mesh topology (IBEM_ERR_GEOMETRY)
+// against errors of the parameters (IBEM_ERR_ARG), by the text build_plan returns.
+ibem_status plan_error_status(const std::string& msg) {
+    if (msg.rfind("null", 0) == 0) return IBEM_ERR_ARG;
+    for (const char* key : {"NURBS", "knot", "sphere", "patch", "degenerate", "touching"})
+        if (msg.find(key) != std::string::npos) return IBEM_ERR_GEOMETRY;
+    return IBEM_ERR_ARG;
+}
+
 // the FP64 operator needs stored coupling matrices for Laplace (Helmholtz can
 // generate them on the fly)
 bool fp64_available(const ibem_handle* h) {
+    if (h->P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY) return false;
     return h->helm || h->P.n_far == 0 || h->d_K || h->d_Kdf;
 }
 
@@ -155,7 +165,7 @@ ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_pa
     } catch (const std::bad_alloc&) {
         return fail(nullptr, IBEM_ERR_OOM, "host allocation failed");
     }
-    if (!msg.empty()) return fail(nullptr, msg.find("degenerate") != std::string::npos ? IBEM_ERR_GEOMETRY : IBEM_ERR_ARG, msg);
+    if (!msg.empty()) return fail(nullptr, plan_error_status(msg), msg);
     *n_near = P.n_near;
     *n_far = P.n_far;
     if (near) {
@@ -198,7 +208,7 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
     }
     if (!msg.empty()) {
         delete h;
-        return fail(nullptr, msg.find("degenerate") != std::string::npos ? IBEM_ERR_GEOMETRY : IBEM_ERR_ARG, msg);
+        return fail(nullptr, plan_error_status(msg), msg);
     }
     Plan& P = h->P;
     h->helm = params->kernel == IBEM_HELMHOLTZ;
@@ -403,16 +413,19 @@ ibem_status ibem_assemble(ibem_handle* h) {
     if (!h->d_near) {
         size_t nn = (size_t)(P.n_near > 0 ? P.n_near : 1) * P.nb * P.nb * (h->helm ? 2 : 1);
         if ((e = cudaMalloc(&h->d_near, nn * sizeof(double)))) return cuda_fail(h, e, "alloc near blocks");
-        if ((e = cudaMalloc(&h->d_near32, nn * sizeof(float)))) return cuda_fail(h, e, "alloc near blocks fp32");
+        if (!h->d_near32 && (e = cudaMalloc(&h->d_near32, nn * sizeof(float))))
+            return cuda_fail(h, e, "alloc near blocks fp32");
         if (P.n_far > 0 && h->helm) {
             // stored complex coupling (16 B per entry) if it fits in half of the free memory
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             size_t free_b = 0, total_b = 0;
             cudaMemGetInfo(&free_b, &total_b);
             h->far_on_the_fly = P.prm.fp64_coupling != IBEM_COUPLING_DF || nk * sizeof(float4) > free_b / 2;
+            if (P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY) h->far_on_the_fly = true;
             if (!h->far_on_the_fly)
                 if ((e = cudaMalloc(&h->d_Kc, nk * sizeof(float4)))) return cuda_fail(h, e, "alloc coupling matrices");
-        } else if (P.n_far > 0 && P.prm.fp64_coupling != IBEM_COUPLING_NONE) {   // Laplace (GENERATE: as DF)
+        } else if (P.n_far > 0 && P.prm.fp64_coupling != IBEM_COUPLING_NONE &&
+                   P.prm.fp64_coupling != IBEM_COUPLING_FP32_ONLY) {   // Laplace (GENERATE: as DF)
             size_t nk = (size_t)P.n_far * h->kpt * 4 * P.q2;
             if (P.prm.fp64_coupling == IBEM_COUPLING_NATIVE) {
                 if ((e = cudaMalloc(&h->d_K, nk * sizeof(double)))) return cuda_fail(h, e, "alloc coupling matrices");
@@ -438,6 +451,12 @@ ibem_status ibem_assemble(ibem_handle* h) {
     }
     if (!h->helm && h->d_Kdf && !h->up_rows.empty())
         if ((e = tune_coupling_df(h))) return cuda_fail(h, e, "coupling autotune");
+    if (P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY && h->d_near) {
+        // the FP32 copy, the diagonal and the block-Jacobi inverses are formed
+        if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");
+        cudaFree(h->d_near);
+        h->d_near = nullptr;
+    }
     h->assembled = true;
     return IBEM_OK;
 }

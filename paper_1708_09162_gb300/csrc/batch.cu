@@ -139,9 +139,10 @@ __global__ void b_m2m_kernel(const BatchInst* __restrict__ B, int n, const int64
 // Thread t = g * q2 + a (g < G = blockDim / q2) sums target point a against the
 // blocks g, g + G, ... of the row; partial sums meet in shared memory.
 // Right-hand sides per coupling work item: every kernel value generated for a
-// far block serves up to BC_RB right-hand sides of the instance.
-constexpr int BC_RB = 8;
+// far block serves up to RB right-hand sides of the instance (the tile shape
+// chosen with the CTA size by the autotuner: RB in 4, 8, 16).
 
+template <int BC_RB>
 __global__ void b_coupling_kernel(const BatchInst* __restrict__ B, int n, const int64_t* __restrict__ pre,
                                   int64_t total, int* __restrict__ counter) {
     extern __shared__ float red[];   // [BC_RB][blockDim][2]
@@ -359,8 +360,16 @@ cudaError_t batch_enqueue(ibem_batch* b, const double* x, double* y, int couplin
         ++launches;
     }
     if (total(B::ST_COUPLE) > 0) {
-        b_coupling_kernel<<<b->couple_ctas, coupling_threads, 2 * BC_RB * coupling_threads * sizeof(float), st>>>(
-            b->d_inst, b->n, b->d_pre[B::ST_COUPLE], total(B::ST_COUPLE), b->d_counter);
+        const size_t sm = 2 * (size_t)b->couple_rb * coupling_threads * sizeof(float);
+        if (b->couple_rb == 4)
+            b_coupling_kernel<4><<<b->couple_ctas, coupling_threads, sm, st>>>(
+                b->d_inst, b->n, b->d_pre[B::ST_COUPLE], total(B::ST_COUPLE), b->d_counter);
+        else if (b->couple_rb == 16)
+            b_coupling_kernel<16><<<b->couple_ctas, coupling_threads, sm, st>>>(
+                b->d_inst, b->n, b->d_pre[B::ST_COUPLE], total(B::ST_COUPLE), b->d_counter);
+        else
+            b_coupling_kernel<8><<<b->couple_ctas, coupling_threads, sm, st>>>(
+                b->d_inst, b->n, b->d_pre[B::ST_COUPLE], total(B::ST_COUPLE), b->d_counter);
         ++launches;
     }
     for (int kk = 1; kk <= b->max_m; ++kk) {
@@ -479,7 +488,7 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
         cnt[ibem_batch::ST_BACK] = R * I.E * I.nb;
         cnt[ibem_batch::ST_NEAR] = 0;
         cnt[ibem_batch::ST_RESTRICT] = R * I.N;
-        cnt[ibem_batch::ST_COUPLE] = ((R + BC_RB - 1) / BC_RB) * (int64_t)handles[i]->far_rows.size();
+        cnt[ibem_batch::ST_COUPLE] = ((R + 7) / 8) * (int64_t)handles[i]->far_rows.size();   // RB = 8 until tuned
         for (int kk = 1; kk <= b->max_m; ++kk) {
             if (I.m >= kk) {
                 const int L = I.m - kk;
@@ -503,10 +512,36 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
     }
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    // autotune the CTA size of the persistent coupling kernel on scratch inputs
+    // coupling work list (items of RB right-hand sides) for every candidate tile
+    auto couple_list = [&](int rb) {
+        std::vector<int64_t> pre(n + 1, 0);
+        for (int i = 0; i < n; ++i)
+            pre[i + 1] = pre[i] + (int64_t)((b->inst[i].R + rb - 1) / rb) * (int64_t)handles[i]->far_rows.size();
+        return pre;
+    };
+    auto use_tile = [&](int rb) {
+        b->couple_rb = rb;
+        b->pre[ibem_batch::ST_COUPLE] = couple_list(rb);
+        cudaMemcpyAsync(b->d_pre[ibem_batch::ST_COUPLE], b->pre[ibem_batch::ST_COUPLE].data(), (n + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, b->stream);
+    };
+    auto resident = [&](int rb, int threads) {
+        const size_t smb = 2 * (size_t)rb * threads * sizeof(float);
+        int per_sm = 0;
+        if (rb == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel<4>, threads, smb);
+        else if (rb == 16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel<16>, threads, smb);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel<8>, threads, smb);
+        return sms * per_sm;   // 0: this shape cannot be launched (registers or shared memory)
+    };
+    cudaFuncSetAttribute(b_coupling_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 4 * 512 * 4);
+    cudaFuncSetAttribute(b_coupling_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 8 * 512 * 4);
+    cudaFuncSetAttribute(b_coupling_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 16 * 512 * 4);
+    // autotune the tile (right-hand sides per work item) and the CTA size of the
+    // persistent coupling kernel on scratch inputs
     double* xs_tmp = nullptr;
     double* ys_tmp = nullptr;
     const int64_t tot = b->offsets[n];
+    int best_rb = 8;
     if (cudaMallocAsync(&xs_tmp, tot * sizeof(double), b->stream) == cudaSuccess &&
         cudaMallocAsync(&ys_tmp, tot * sizeof(double), b->stream) == cudaSuccess) {
         cudaMemsetAsync(xs_tmp, 0, tot * sizeof(double), b->stream);
@@ -514,21 +549,25 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
-        for (int threads : {128, 256, 512}) {
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel, threads,
-                                                          2 * BC_RB * threads * sizeof(float));
-            b->couple_ctas = sms * std::max(1, per_sm);
-            batch_enqueue(b, xs_tmp, ys_tmp, threads);
-            cudaEventRecord(e0, b->stream);
-            batch_enqueue(b, xs_tmp, ys_tmp, threads);
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                b->couple_threads = threads;
+        for (int rb : {4, 8, 16}) {
+            use_tile(rb);
+            for (int threads : {128, 256, 512}) {
+                b->couple_ctas = resident(rb, threads);
+                if (b->couple_ctas == 0) continue;
+                // a shape whose launch fails takes no time: never a candidate
+                if (batch_enqueue(b, xs_tmp, ys_tmp, threads) != cudaSuccess) continue;
+                cudaEventRecord(e0, b->stream);
+                if (batch_enqueue(b, xs_tmp, ys_tmp, threads) != cudaSuccess) continue;
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                b->tune_ms.push_back(ms);
+                if (ms < best) {
+                    best = ms;
+                    b->couple_threads = threads;
+                    best_rb = rb;
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -536,10 +575,12 @@ ibem_status ibem_batch_create(ibem_handle* const* handles, int n, const int* nrh
         cudaFreeAsync(xs_tmp, b->stream);
         cudaFreeAsync(ys_tmp, b->stream);
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b_coupling_kernel, b->couple_threads,
-                                                  2 * BC_RB * b->couple_threads * sizeof(float));
-    b->couple_ctas = sms * std::max(1, per_sm);
+    use_tile(best_rb);
+    b->couple_ctas = resident(best_rb, b->couple_threads);
+    if (b->couple_ctas == 0) {
+        ibem_batch_destroy(b);
+        return IBEM_ERR_CUDA;
+    }
     if (cudaStreamSynchronize(b->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         ibem_batch_destroy(b);
         return IBEM_ERR_CUDA;
@@ -574,10 +615,12 @@ ibem_status ibem_batch_matvec(ibem_batch* b, const double* x_dev, double* y_dev)
     return IBEM_OK;
 }
 
-ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads) {
+ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* coupling_threads,
+                            int* coupling_rhs_tile) {
     if (!b) return IBEM_ERR_ARG;
     if (launches_per_apply) *launches_per_apply = b->launches;
     if (coupling_threads) *coupling_threads = b->couple_threads;
+    if (coupling_rhs_tile) *coupling_rhs_tile = b->couple_rb;
     return IBEM_OK;
 }
 

@@ -47,6 +47,8 @@ struct ibem_batch {
     size_t yh_begin = 0, yh_floats = 0;      // contiguous y^ region (cleared per application)
     int* d_counter = nullptr;
     int couple_threads = 256;
+    int couple_rb = 8;                       // right-hand sides per coupling work item (autotuned)
+    std::vector<float> tune_ms;              // autotuner timings, tiles x CTA sizes
     int couple_ctas = 0;
     int launches = 0;
     bool own_stream = false;

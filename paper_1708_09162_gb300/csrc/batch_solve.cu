@@ -289,6 +289,8 @@ extern "C" ibem_status ibem_batch_solve(ibem_batch* b, const double* b_dev, doub
     const unsigned gT = sblk(T, 256), gE = sblk(K.nent, 256);
     std::vector<double> nb, rn;
     if (K.norms(b_dev, nb) != cudaSuccess) return IBEM_ERR_CUDA;
+    for (double v : nb)
+        if (!std::isfinite(v)) return IBEM_ERR_BREAKDOWN;   // NaN or Inf in the right-hand sides
     cudaMemsetAsync(x_dev, 0, T * sizeof(double), st);
     cudaMemcpyAsync(r, b_dev, T * sizeof(double), cudaMemcpyDeviceToDevice, st);
     const double delta = K.fp64 ? 1e-3 : 0.0;

@@ -64,6 +64,9 @@ struct ibem_cnn {
     size_t wtc_bytes = 0;
     int* d_status = nullptr;     // device-side wait status of the tensor-core layers
     double* d_red = nullptr;     // [0] loss, [1] |s|^2, [2] loss sum of an epoch
+    int coarse = 1;              // coarsening factor f of the preconditioner's images (1: the fine grid)
+    float* d_cimg = nullptr;     // coarse images of the preconditioner
+    size_t cimg_floats = 0;
     cudaStream_t stream = nullptr;
     int64_t launches = 0;
 };
@@ -556,6 +559,24 @@ __global__ void gather_kernel(int nb, int H, int W, const TrainItem* __restrict_
     btgt[d0 + HW] = it.s * re + it.c * im;
 }
 
+// Coarse grid of the preconditioner (factor f): the mean over blocks of f x f
+// pixels (ragged blocks at the far edge average the pixels they hold), and the
+// block sums (the adjoint of the piecewise-constant prolongation, for the
+// gradient).  Images [n_ch][n1][n1] -> [n_ch][nc][nc], nc = ceil(n1 / f).
+__global__ void restrict_images_kernel(int64_t n_ch, int n1, int f, int nc, const float* __restrict__ in,
+                                       float* __restrict__ out, int mean) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n_ch * nc * nc) return;
+    const int X = (int)(idx % nc), Y = (int)((idx / nc) % nc);
+    const int64_t ch = idx / ((int64_t)nc * nc);
+    const float* src = in + ch * n1 * n1;
+    const int y1 = min(n1, (Y + 1) * f), x1 = min(n1, (X + 1) * f);
+    float acc = 0.0f;
+    for (int y = Y * f; y < y1; ++y)
+        for (int x = X * f; x < x1; ++x) acc += src[(int64_t)y * n1 + x];
+    out[idx] = mean ? acc / (float)((y1 - Y * f) * (x1 - X * f)) : acc;
+}
+
 // Preconditioner glue.  img[patch][2][n1][n1] = s / sigma with
 // sigma^2 = |s|^2 / (2N) (zero image if s = 0).
 __global__ void pack_images_kernel(int64_t N, int n1, const double* __restrict__ s, const double* __restrict__ ss,
@@ -569,17 +590,19 @@ __global__ void pack_images_kernel(int64_t N, int n1, const double* __restrict__
     img[(patch * 2 + 1) * per + pix] = (float)(s[2 * dof + 1] * inv);
 }
 
-// z += sigma * out
+// z += sigma * out, out on the coarse grid (f, nc; f = 1: the fine grid),
+// spread piecewise constant
 template <typename T>
-__global__ void unpack_add_kernel(int64_t N, int n1, const T* __restrict__ img, const double* __restrict__ ss,
-                                  double* __restrict__ z) {
+__global__ void unpack_add_kernel(int64_t N, int n1, int f, int nc, const T* __restrict__ img,
+                                  const double* __restrict__ ss, double* __restrict__ z) {
     int64_t dof = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (dof >= N) return;
-    const int64_t per = (int64_t)n1 * n1;
+    const int64_t per = (int64_t)n1 * n1, cper = (int64_t)nc * nc;
     const int64_t patch = dof / per, pix = dof % per;
+    const int64_t cpix = (pix / n1 / f) * nc + (pix % n1) / f;
     const double sig = sqrt(ss[0] / (2.0 * N));
-    z[2 * dof] += sig * (double)ld_act(img, (patch * 2) * per + pix);
-    z[2 * dof + 1] += sig * (double)ld_act(img, (patch * 2 + 1) * per + pix);
+    z[2 * dof] += sig * (double)ld_act(img, (patch * 2) * cper + cpix);
+    z[2 * dof + 1] += sig * (double)ld_act(img, (patch * 2 + 1) * cper + cpix);
 }
 
 __global__ void sumsq_kernel(int64_t n, const double* __restrict__ v, double* __restrict__ out) {
@@ -860,19 +883,21 @@ __global__ void batch_pack_kernel(int nb, int64_t N, int n1, const double* __res
     img[o + per] = (float)(s[idx * 2 + 1] * inv);
 }
 
-// z_j = s_j + sigma_j out_j
+// z_j = s_j + sigma_j P out_j (out on the coarse grid f, nc; piecewise constant P)
 template <typename T>
-__global__ void batch_unpack_kernel(int nb, int64_t N, int n1, const T* __restrict__ out, const double* __restrict__ ss,
-                                    const double* __restrict__ s, double* __restrict__ z) {
+__global__ void batch_unpack_kernel(int nb, int64_t N, int n1, int f, int nc, const T* __restrict__ out,
+                                    const double* __restrict__ ss, const double* __restrict__ s,
+                                    double* __restrict__ z) {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)nb * N) return;
     const int j = (int)(idx / N);
-    const int64_t dof = idx % N, per = (int64_t)n1 * n1, npatch = N / per;
+    const int64_t dof = idx % N, per = (int64_t)n1 * n1, npatch = N / per, cper = (int64_t)nc * nc;
     const int64_t patch = dof / per, pix = dof % per;
+    const int64_t cpix = (pix / n1 / f) * nc + (pix % n1) / f;
     const double sig = sqrt(ss[j] / (2.0 * N));
-    const int64_t o = ((int64_t)j * npatch + patch) * 2 * per + pix;
+    const int64_t o = ((int64_t)j * npatch + patch) * 2 * cper + cpix;
     z[idx * 2] = s[idx * 2] + sig * (double)ld_act(out, o);
-    z[idx * 2 + 1] = s[idx * 2 + 1] + sig * (double)ld_act(out, o + per);
+    z[idx * 2 + 1] = s[idx * 2 + 1] + sig * (double)ld_act(out, o + cper);
 }
 
 // gimg = (sigma_j / nb) (Re, Im) g_j
@@ -896,12 +921,13 @@ namespace {
 struct OpScratch {
     double *R, *S, *Z, *Y, *G, *ss, *part;
     float *img, *gimg;
+    float *cimg, *cgimg;   // the same on the coarse grid (coarsening factor > 1)
 };
 
 cudaError_t op_scratch(ibem_cnn* c, int nb, int64_t N, int64_t img_per_vec, OpScratch* o) {
     const size_t vec = (size_t)2 * N;
     const size_t nd = 5 * (size_t)nb * vec + 2 * (size_t)nb;
-    const size_t nf = 2 * (size_t)nb * img_per_vec;
+    const size_t nf = 4 * (size_t)nb * img_per_vec;
     cudaError_t e;
     if ((e = grow(&c->d_opvec, &c->opvec_bytes, nd * sizeof(double)))) return e;
     if ((e = grow(&c->d_opimg, &c->opimg_bytes, nf * sizeof(float)))) return e;
@@ -915,6 +941,8 @@ cudaError_t op_scratch(ibem_cnn* c, int nb, int64_t N, int64_t img_per_vec, OpSc
     o->part = o->ss + nb;
     o->img = reinterpret_cast<float*>(c->d_opimg);
     o->gimg = o->img + (size_t)nb * img_per_vec;
+    o->cimg = o->gimg + (size_t)nb * img_per_vec;
+    o->cgimg = o->cimg + (size_t)nb * img_per_vec;
     return cudaSuccess;
 }
 
@@ -928,13 +956,17 @@ cudaError_t op_batch(ibem_handle* h, ibem_cnn* c, const OpScratch& o, int nb, in
     const int n1 = P.n1, npatch = P.npatch;
     cudaStream_t st = c->stream;
     cudaError_t e;
+    const int f = c->coarse, nc = (n1 + f - 1) / f;
+    const int64_t nch = (int64_t)nb * npatch * 2;
     for (int j = 0; j < nb; ++j) apply_block_jacobi(h, o.R + (size_t)j * vec, o.S + (size_t)j * vec);
     vec_sumsq_kernel<<<nb, 256, 0, st>>>(vec, o.S, o.ss);
     batch_pack_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(nb, N, n1, o.S, o.ss, o.img);
-    c->launches += nb + 2;
-    if ((e = forward<T>(c, o.img, nb * npatch, n1, n1, bf))) return e;
+    if (f > 1)
+        restrict_images_kernel<<<cblk(nch * nc * nc, 256), 256, 0, st>>>(nch, n1, f, nc, o.img, o.cimg, 1);
+    c->launches += nb + 2 + (f > 1 ? 1 : 0);
+    if ((e = forward<T>(c, f > 1 ? o.cimg : o.img, nb * npatch, nc, nc, bf))) return e;
     batch_unpack_kernel<T><<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(
-        nb, N, n1, reinterpret_cast<const T*>(c->d_act) + c->L * c->act_slot, o.ss, o.S, o.Z);
+        nb, N, n1, f, nc, reinterpret_cast<const T*>(c->d_act) + c->L * c->act_slot, o.ss, o.S, o.Z);
     if ((e = apply_operator(h, o.Z, o.Y, nb, op_prec))) return e;
     residual_sumsq_kernel<<<nb, 256, 0, st>>>(vec, o.R, o.Y, o.part);
     op_loss_kernel<<<1, 32, 0, st>>>(nb, o.part, c->d_red);
@@ -945,8 +977,10 @@ cudaError_t op_batch(ibem_handle* h, ibem_cnn* c, const OpScratch& o, int nb, in
     if ((e = apply_operator(h, o.Y, o.G, nb, op_prec))) return e;
     conj_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>((int64_t)nb * N, o.G);
     batch_grad_images_kernel<<<cblk((int64_t)nb * N, 256), 256, 0, st>>>(nb, N, n1, o.G, o.ss, o.gimg);
-    c->launches += 3;
-    if ((e = backward<T>(c, nullptr, nb * npatch, n1, n1, bf, o.gimg))) return e;
+    if (f > 1)   // gradient of the coarse output: P^T, the block sums
+        restrict_images_kernel<<<cblk(nch * nc * nc, 256), 256, 0, st>>>(nch, n1, f, nc, o.gimg, o.cgimg, 0);
+    c->launches += 3 + (f > 1 ? 1 : 0);
+    if ((e = backward<T>(c, nullptr, nb * npatch, nc, nc, bf, f > 1 ? o.cgimg : o.gimg))) return e;
     return cudaGetLastError();
 }
 
@@ -973,16 +1007,28 @@ cudaError_t cnn_precondition(ibem_handle* h, ibem_cnn* c, const double* v, doubl
         return e;
     }
     c->img_floats = ib / sizeof(float);
+    const int f = c->coarse, nc = (n1 + f - 1) / f;
+    if (f > 1) {
+        size_t cb = c->cimg_floats * sizeof(float);
+        if ((e = grow(reinterpret_cast<void**>(&c->d_cimg), &cb, (size_t)B * 2 * nc * nc * sizeof(float)))) {
+            c->stream = keep;
+            return e;
+        }
+        c->cimg_floats = cb / sizeof(float);
+    }
     apply_block_jacobi(h, v, z);
     sumsq_kernel<<<1, 1024, 0, h->stream>>>(2 * P.N, z, c->d_red + 1);
     pack_images_kernel<<<cblk(P.N, 256), 256, 0, h->stream>>>(P.N, n1, z, c->d_red + 1, c->d_img);
-    e = forward_infer(c, c->d_img, B, n1, n1, h->d_status, h->wait_limit);
+    if (f > 1)
+        restrict_images_kernel<<<cblk((int64_t)B * 2 * nc * nc, 256), 256, 0, h->stream>>>((int64_t)B * 2, n1, f, nc,
+                                                                                           c->d_img, c->d_cimg, 1);
+    e = forward_infer(c, f > 1 ? c->d_cimg : c->d_img, B, nc, nc, h->d_status, h->wait_limit);
     if (!e) {
         unpack_add_kernel<__nv_bfloat16><<<cblk(P.N, 256), 256, 0, h->stream>>>(
-            P.N, n1, reinterpret_cast<const __nv_bfloat16*>(c->d_act) + c->L * c->act_slot, c->d_red + 1, z);
+            P.N, n1, f, nc, reinterpret_cast<const __nv_bfloat16*>(c->d_act) + c->L * c->act_slot, c->d_red + 1, z);
         e = cudaGetLastError();
     }
-    h->launches += 4 + 1 + c->L;
+    h->launches += 4 + 1 + c->L + (f > 1 ? 1 : 0);
     c->stream = keep;
     return e;
 }
@@ -1039,6 +1085,12 @@ ibem_status ibem_cnn_create(int channels, unsigned long long seed, void* cuda_st
     return IBEM_OK;
 }
 
+ibem_status ibem_cnn_set_coarsening(ibem_cnn* c, int factor) {
+    if (!c || factor < 1 || factor > 64) return IBEM_ERR_ARG;
+    c->coarse = factor;
+    return IBEM_OK;
+}
+
 ibem_status ibem_cnn_destroy(ibem_cnn* c) {
     if (!c) return IBEM_OK;
     cudaStreamSynchronize(c->stream);
@@ -1051,6 +1103,7 @@ ibem_status ibem_cnn_destroy(ibem_cnn* c) {
     cudaFree(c->d_gbuf);
     cudaFree(c->d_part);
     cudaFree(c->d_img);
+    cudaFree(c->d_cimg);
     cudaFree(c->d_items);
     cudaFree(c->d_opvec);
     cudaFree(c->d_opimg);
@@ -1201,6 +1254,7 @@ ibem_status ibem_cnn_operator_gradients(ibem_handle* h, ibem_cnn* c, const doubl
     if (!r_dev || n < 1 || n > 256 || (precision != IBEM_FP32 && precision != IBEM_BF16) ||
         (op_precision != IBEM_FP64 && op_precision != IBEM_FP32))
         return IBEM_ERR_ARG;
+    if (op_precision == IBEM_FP64 && h->P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY) return IBEM_ERR_STATE;
     Plan& P = h->P;
     cudaStream_t keep = c->stream;
     c->stream = h->stream;
@@ -1228,6 +1282,7 @@ ibem_status ibem_cnn_train_operator(ibem_handle* h, ibem_cnn* c, const double* r
     if (!r_dev || n < 1 || batch < 1 || batch > 256 || epochs < 1 || !(lr > 0.0f) ||
         (augment & ~IBEM_AUGMENT_PHASE) || (op_precision != IBEM_FP64 && op_precision != IBEM_FP32))
         return IBEM_ERR_ARG;
+    if (op_precision == IBEM_FP64 && h->P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY) return IBEM_ERR_STATE;
     Plan& P = h->P;
     const int nb_max = std::min(batch, n);
     cudaStream_t keep = c->stream;

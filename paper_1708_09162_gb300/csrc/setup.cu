@@ -226,8 +226,9 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.gauss_regular < 1 || q.gauss_regular > IBEM_MAX_GAUSS) return "gauss_regular must be in 1..40";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
-        q.fp64_coupling != IBEM_COUPLING_NONE && q.fp64_coupling != IBEM_COUPLING_GENERATE)
-        return "fp64_coupling must be IBEM_COUPLING_DF, NATIVE, NONE or GENERATE";
+        q.fp64_coupling != IBEM_COUPLING_NONE && q.fp64_coupling != IBEM_COUPLING_GENERATE &&
+        q.fp64_coupling != IBEM_COUPLING_FP32_ONLY)
+        return "fp64_coupling must be IBEM_COUPLING_DF, NATIVE, NONE, GENERATE or FP32_ONLY";
     P.prm = q;
     P.npatch = npatch;
     P.p = q.p;

@@ -478,6 +478,7 @@ ibem_status solve_block_impl(ibem_handle* h, const double* b, double* x, int R, 
     std::vector<double> tol_final(R);
     for (int r = 0; r < R; ++r) {
         nb[r] = std::sqrt(nb[r]);
+        if (!std::isfinite(nb[r])) return IBEM_ERR_BREAKDOWN;   // NaN or Inf in the right-hand side
         tol_final[r] = rtol * nb[r];
         if (nb[r] > 0.0) act.push_back(r);
     }

@@ -36,7 +36,7 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
             "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
-            "ibem_cnn_train_operator", "ibem_cnn_device_status")
+            "ibem_cnn_train_operator", "ibem_cnn_device_status", "ibem_cnn_set_coarsening")
 
 
 class IbemError(RuntimeError):
@@ -105,7 +105,7 @@ def _load():
         "ibem_batch_create": (I32, [ctypes.POINTER(P), I32, ctypes.POINTER(I32), P, ctypes.POINTER(P)]),
         "ibem_batch_offsets": (I32, [P, ctypes.POINTER(I64)]),
         "ibem_batch_matvec": (I32, [P, P, P]),
-        "ibem_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "ibem_batch_info": (I32, [P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)]),
         "ibem_batch_destroy": (I32, [P]),
         "ibem_batch_solve": (I32, [P, P, P, ctypes.c_double, I32, I32, ctypes.POINTER(ibem_solve_info)]),
         "ibem_device_status": (I32, [P, ctypes.POINTER(I32)]),
@@ -119,6 +119,7 @@ def _load():
                                  ctypes.POINTER(ctypes.c_double)]),
         "ibem_cnn_launches": (I32, [P, ctypes.POINTER(I64)]),
         "ibem_cnn_device_status": (I32, [P, ctypes.POINTER(I32)]),
+        "ibem_cnn_set_coarsening": (I32, [P, I32]),
         "ibem_set_learned_preconditioner": (I32, [P, P]),
         "ibem_learned_apply": (I32, [P, P, P]),
         "ibem_solver_pairs": (I32, [P, P, I32, ctypes.c_double, I32, I32, I32, P, P, ctypes.POINTER(I32),
@@ -207,7 +208,7 @@ def nurbs_patches(specs):
     return arr
 
 
-IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERATE = 0, 1, 2, 3
+IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERATE, IBEM_COUPLING_FP32_ONLY = 0, 1, 2, 3, 4
 
 
 IBEM_ADMISSIBLE_ETA_DIAM, IBEM_ADMISSIBLE_ETA_DIST = 0, 1
@@ -343,9 +344,9 @@ def ibem_batch_matvec(b, x, y):
 
 
 def ibem_batch_info(b):
-    l, t = ctypes.c_int(), ctypes.c_int()
-    _check(_lib.ibem_batch_info(b, ctypes.byref(l), ctypes.byref(t)))
-    return {"launches_per_apply": l.value, "coupling_threads": t.value}
+    l, t, rb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.ibem_batch_info(b, ctypes.byref(l), ctypes.byref(t), ctypes.byref(rb)))
+    return {"launches_per_apply": l.value, "coupling_threads": t.value, "coupling_rhs_tile": rb.value}
 
 
 def ibem_batch_destroy(b):
@@ -434,6 +435,10 @@ def ibem_cnn_launches(c):
     n = ctypes.c_int64()
     _check(_lib.ibem_cnn_launches(c, ctypes.byref(n)))
     return n.value
+
+
+def ibem_cnn_set_coarsening(c, factor):
+    _check(_lib.ibem_cnn_set_coarsening(c, factor))
 
 
 def ibem_set_learned_preconditioner(h, c):

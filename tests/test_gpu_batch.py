@@ -41,6 +41,7 @@ def test_batched_uneven_instances():
     info = ibem.ibem_batch_info(b)
     assert info["launches_per_apply"] <= 2 * max(s[3] for s in SPECS) + 8
     assert info["coupling_threads"] in (128, 256, 512)
+    assert info["coupling_rhs_tile"] in (4, 8, 16)
     for i, (h, spec) in enumerate(zip(handles, SPECS)):
         R = spec[5]
         xi = x[off[i]:off[i + 1]].contiguous()

@@ -372,3 +372,72 @@ def test_learned_preconditioner_against_block_jacobi():
     ibem.ibem_set_learned_preconditioner(h, None)
     ibem.ibem_cnn_destroy(c)
     ibem.ibem_destroy(h)
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_coarse_learned_apply_against_oracle(helm_m2, f):
+    # coarse-grid variant: n1 = 6 patch images averaged over 2 x 2 (nc = 3) and
+    # over 4 x 4 blocks (nc = 2, ragged), correction spread back
+    import torch
+    from oracle import learned
+    op, _, bj = helm_m2
+    ibem = lib()
+    h = _helm_handle(ibem, 2, 2, 6, 3.0)
+    C = 32
+    c = ibem.ibem_cnn_create(C, seed=2)
+    ibem.ibem_cnn_set_coarsening(c, f)
+    ibem.ibem_set_learned_preconditioner(h, c)
+    n1 = op.mesh.n1
+    rng = np.random.default_rng(18 + f)
+    v = rng.normal(size=op.mesh.n_dofs) + 1j * rng.normal(size=op.mesh.n_dofs)
+    vd = _cplx_dev(v)
+    zd = torch.empty_like(vd)
+    p = _params64(ibem, c)
+    p0 = p.copy()
+    p0[-(2 * C * 9 + 2):] = 0.0
+    ibem.ibem_cnn_params(c, p0)
+    ibem.ibem_learned_apply(h, vd, zd)
+    torch.cuda.synchronize()
+    s = bj(v)
+    assert np.max(np.abs(_cplx_host(zd) - s)) < 1e-12 * np.max(np.abs(s))
+    p[-2:] = [0.05, -0.03]
+    ibem.ibem_cnn_params(c, p)
+    ibem.ibem_learned_apply(h, vd, zd)
+    torch.cuda.synchronize()
+    z0 = learned.learned_apply(v, bj, p.astype(np.float32).astype(np.float64), C, n1, f)
+    z1 = learned.learned_apply(v, bj, p.astype(np.float32).astype(np.float64), C, n1, 1)
+    z = _cplx_host(zd)
+    assert _rel(z - s, z0 - s) < 2e-2
+    assert _rel(z0 - s, z1 - s) > 0.1          # the coarse correction is a different one
+    ibem.ibem_set_learned_preconditioner(h, None)
+    ibem.ibem_cnn_destroy(c)
+    ibem.ibem_destroy(h)
+
+
+@pytest.mark.parametrize("f", [2, 4])
+def test_coarse_operator_objective_gradients_against_oracle(helm_m2, f):
+    import torch
+    from oracle import cnn, learned
+    op, _, bj = helm_m2
+    ibem = lib()
+    h = _helm_handle(ibem, 2, 2, 6, 3.0)
+    N, n1, C = op.mesh.n_dofs, op.mesh.n1, 8
+    A = op.matvec(np.eye(N, dtype=np.complex128))
+    rng = np.random.default_rng(33 + f)
+    rs = rng.normal(size=(3, N)) + 1j * rng.normal(size=(3, N))
+    rs /= np.linalg.norm(rs, axis=1)[:, None]
+    c = ibem.ibem_cnn_create(C, seed=4)
+    ibem.ibem_cnn_set_coarsening(c, f)
+    p = _params64(ibem, c)
+    rd = torch.from_numpy(np.ascontiguousarray(np.stack([rs.real, rs.imag], -1))).cuda()
+    loss, g = ibem.ibem_cnn_operator_gradients(h, c, rd, 3, ibem.IBEM_FP32, ibem.IBEM_FP64)
+    loss0, g0 = learned.operator_loss_and_grad(p, rs, lambda z: A @ z, lambda z: A.conj().T @ z, bj, C, n1, f)
+    assert loss == pytest.approx(loss0, rel=1e-6)
+    off = 0
+    for ci, co in cnn.layer_channels(C):
+        for n in (co * ci * 9, co):
+            sl = slice(off, off + n)
+            assert _rel(g[sl], g0[sl]) < 1e-4
+            off += n
+    ibem.ibem_cnn_destroy(c)
+    ibem.ibem_destroy(h)

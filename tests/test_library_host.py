@@ -160,3 +160,31 @@ def test_block_tree_partitions_every_element_pair(ibem):
             # identical pairs are near and classed as such
             diag = near[(near[:, 0] == near[:, 3]) & (near[:, 1] == near[:, 4]) & (near[:, 2] == near[:, 5])]
             assert len(diag) == E and np.all(diag[:, 6] == 0)
+
+
+def test_corrupt_geometry_rejected_on_the_host(ibem):
+    # failure detection without a GPU: corrupt patch descriptions and parameters
+    # are refused by the host-side validation with IBEM_ERR_GEOMETRY / ARG
+    from oracle import geometry
+    a = geometry.quarter_cylinder(1.0, 1.5)
+
+    def tree(spec, **kw):
+        return ibem.ibem_block_tree(ibem.nurbs_patches([spec]), ibem.make_params(1, 1, **kw))
+
+    good = (2, 1, a.knots_u, a.knots_v, a.ctrl, a.weights)
+    tree(good)
+    cases = [
+        ((2, 1, a.knots_u[::-1], a.knots_v, a.ctrl, a.weights), "non-decreasing"),
+        ((2, 1, 0.5 * np.asarray(a.knots_u), a.knots_v, a.ctrl, a.weights), "from 0 to 1"),
+        ((2, 1, a.knots_u, a.knots_v, np.zeros_like(a.ctrl), a.weights), "degenerate"),
+        ((2, 1, a.knots_u, a.knots_v, np.where(np.arange(a.ctrl.size).reshape(a.ctrl.shape) == 4, np.nan, a.ctrl),
+          a.weights), "degenerate"),
+    ]
+    for spec, text in cases:
+        with pytest.raises(ibem.IbemError) as ei:
+            tree(spec)
+        assert ei.value.status == "IBEM_ERR_GEOMETRY" and text in str(ei.value), str(ei.value)
+    for kw, text in (({"kernel": 1, "kappa": float("nan")}, "kappa"), ({"q_cheb": 4, "eta": float("nan")}, "eta")):
+        with pytest.raises(ibem.IbemError) as ei:
+            tree(good, **kw)
+        assert ei.value.status == "IBEM_ERR_ARG" and text in str(ei.value)

@@ -201,3 +201,48 @@ def test_operator_loss_gradient_matches_central_differences():
         d = rng.normal(size=params.shape)
         fd = (f(params + eps * d)[0] - f(params - eps * d)[0]) / (2 * eps)
         assert fd == pytest.approx(g @ d, rel=1e-6)
+
+
+def test_coarse_grid_restriction_and_prolongation():
+    # ragged blocks (n1 = 7, f = 3 and 2): R P = identity on coarse images, P is
+    # the adjoint of the block sum, f = 1 changes nothing
+    rng = np.random.default_rng(17)
+    for n1, f in ((7, 3), (7, 2), (6, 2)):
+        nc = learned.coarse_size(n1, f)
+        c = rng.normal(size=(2, 2, nc, nc))
+        assert np.allclose(learned.restrict(learned.prolong(c, f, n1), f), c, rtol=0, atol=1e-14)
+        y = rng.normal(size=(2, 2, n1, n1))
+        assert np.isclose(np.sum(learned.prolong(c, f, n1) * y), np.sum(c * learned.prolong_adjoint(y, f, nc)))
+        # mean of a block: a constant image stays constant, a single pixel is divided by the block size
+        one = np.zeros((1, 1, n1, n1))
+        one[0, 0, 0, 0] = 1.0
+        assert learned.restrict(one, f)[0, 0, 0, 0] == pytest.approx(1.0 / (f * f))
+    x = rng.normal(size=(1, 2, 5, 5))
+    assert learned.restrict(x, 1) is x and learned.prolong(x, 1, 5) is x
+
+
+def test_coarse_operator_loss_gradient_matches_central_differences():
+    # the residual-norm objective of the coarse-grid variant (f = 2 on ragged
+    # 5 x 5 patch images): loss = direct evaluation, gradient = differences
+    rng = np.random.default_rng(19)
+    n1, npatch, C, f = 5, 2, 3, 2
+    N = npatch * n1 * n1
+    A = np.eye(N) * 2 + 0.3 * (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N)))
+    bj = learned.BlockJacobi(A, [np.arange(0, N // 2), np.arange(N // 2, N)])
+    rs = rng.normal(size=(3, N)) + 1j * rng.normal(size=(3, N))
+    rs /= np.linalg.norm(rs, axis=1)[:, None]
+    params = rng.normal(0.0, 0.3, cnn.n_params(C))
+    fn = lambda p: learned.operator_loss_and_grad(p, rs, lambda z: A @ z, lambda z: A.conj().T @ z, bj, C, n1, f)
+    loss, g = fn(params)
+    z0 = [learned.learned_apply(r, bj, params, C, n1, f) for r in rs]
+    assert loss == pytest.approx(sum(np.linalg.norm(A @ z - r) ** 2 for z, r in zip(z0, rs)) / 6.0, rel=1e-12)
+    eps = 1e-6
+    for _ in range(3):
+        d = rng.normal(size=params.shape)
+        fd = (fn(params + eps * d)[0] - fn(params - eps * d)[0]) / (2 * eps)
+        assert fd == pytest.approx(g @ d, rel=1e-6)
+    # the zero last layer still gives block-Jacobi
+    p0 = params.copy()
+    p0[-(2 * C * 9 + 2):] = 0.0
+    v = rs[0]
+    assert np.allclose(learned.learned_apply(v, bj, p0, C, n1, f), bj(v), rtol=0, atol=1e-14)
