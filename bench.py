@@ -579,6 +579,121 @@ def learned_config5(ibem, stream, args):
             "steps_over_block_jacobi": {k: v["steps"] / bjs for k, v in res.items()}}
 
 
+def config4_section(ibem, stream, args):
+    """The batched-instances workload at its full size: 256 seeded instances, each
+    the 6-patch sphere with radius uniform in [0.5, 2], level 3-6 and degree 1-3
+    uniform, Laplace (first half, q = 6) or Helmholtz with kappa uniform in
+    [1, 8] (second half, q = 8), 1-16 right-hand sides; FP32-only handles (the
+    FP64 near blocks are released after assembly).  The batched, graph-captured
+    application (one launch per stage, persistent coupling kernel with autotuned
+    tile and CTA size) is timed against the same instances applied one after
+    another through ibem_matvec, and each instance's batched result is compared
+    with its own application."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(SEED + 40)
+    n = 256
+    specs = []
+    for i in range(n):
+        helm = i >= n // 2
+        specs.append({"kernel": int(helm), "p": int(rng.integers(1, 4)), "m": int(rng.integers(3, 7)),
+                      "R": int(rng.integers(1, 17)), "radius": float(rng.uniform(0.5, 2.0)),
+                      "kappa": float(rng.uniform(1.0, 8.0)) if helm else 0.0, "q": 8 if helm else 6})
+    handles, setup = [], {}
+    t0 = time.perf_counter()
+    for sp in specs:
+        t = time.perf_counter()
+        h = ibem.ibem_create(ibem.sphere_patches(sp["radius"]), ibem.make_params(
+            sp["p"], sp["m"], q_cheb=sp["q"], kernel=sp["kernel"], kappa=sp["kappa"],
+            fp64_coupling=ibem.IBEM_COUPLING_FP32_ONLY), stream)
+        ibem.ibem_assemble(h)
+        handles.append(h)
+        setup[sp["m"]] = setup.get(sp["m"], 0.0) + time.perf_counter() - t
+    setup_s = time.perf_counter() - t0
+    nrhs = [sp["R"] for sp in specs]
+    dofs = sum(ibem.ibem_get_info(h).ndof * R for h, R in zip(handles, nrhs))
+    t = time.perf_counter()
+    b = ibem.ibem_batch_create(handles, nrhs, stream)
+    create_s = time.perf_counter() - t
+    off = ibem.ibem_batch_offsets(b, n)
+    x = torch.from_numpy(rng.normal(size=off[-1])).cuda()
+    y, ys = torch.zeros_like(x), torch.zeros_like(x)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            fn()
+        ev0.record(stream)
+        with torch.cuda.stream(stream):
+            for _ in range(reps):
+                fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    def one_by_one():
+        for i, h in enumerate(handles):
+            ibem.ibem_matvec(h, x[off[i]:off[i + 1]], ys[off[i]:off[i + 1]], nrhs[i], ibem.IBEM_FP32)
+
+    batched_ms = timed(lambda: ibem.ibem_batch_matvec(b, x, y), 5)
+    single_ms = timed(one_by_one, 3)
+    worst = 0.0
+    for i in range(n):
+        a, c = y[off[i]:off[i + 1]], ys[off[i]:off[i + 1]]
+        worst = max(worst, float((a - c).abs().max() / c.abs().max()))
+    info = ibem.ibem_batch_info(b)
+    mem = torch.cuda.mem_get_info()
+    ibem.ibem_batch_destroy(b)
+    for h in handles:
+        ibem.ibem_destroy(h)
+    return {"instances": n, "dof_rhs_per_apply": dofs, "setup_s": setup_s,
+            "setup_s_by_level": {str(k): v for k, v in sorted(setup.items())}, "batch_create_s": create_s,
+            "batched_ms": batched_ms, "one_by_one_ms": single_ms, "speedup": single_ms / batched_ms,
+            "value": dofs / (batched_ms * 1e-3), "unit": UNIT, "max_rel_diff_batched_vs_own": worst,
+            "launches_per_apply": info["launches_per_apply"], "coupling_threads": info["coupling_threads"],
+            "coupling_rhs_tile": info["coupling_rhs_tile"],
+            "device_memory_used_gb": (mem[1] - mem[0]) / 1e9,
+            "levels": {str(m): sum(1 for sp in specs if sp["m"] == m) for m in range(3, 7)}}
+
+
+def fmm_error_study(ibem, stream, args):
+    """FMM error of the Laplace degree-3 level-5 workload (q = 6, eta = 1.6)
+    against the dense Galerkin matrix of the same quadrature (every element
+    pair as near field), for both readings of the admissibility condition
+    (Def. 4.1): eta max(diam) < dist (the default) and max(diam) < eta dist.
+    Operator applied to one seeded vector and to the point-source right-hand
+    side; max-norm relative errors over all dofs."""
+    import numpy as np
+    import torch
+    W = LAPLACE
+    x = torch.from_numpy(np.random.default_rng(SEED + 21).normal(size=(1, 7350))).cuda()
+    out = {"workload": W["workload"]}
+    t0 = time.perf_counter()
+    hd = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=0), stream)
+    ibem.ibem_assemble(hd)
+    out["dense_setup_s"] = time.perf_counter() - t0
+    info = ibem.ibem_get_info(hd)
+    out["dense_near_pairs"] = info.n_near
+    yd = torch.empty_like(x)
+    ibem.ibem_matvec(hd, x, yd, 1, 0)
+    torch.cuda.synchronize()
+    ibem.ibem_destroy(hd)
+    for name, adm in (("eta_max_diam_lt_dist", ibem.IBEM_ADMISSIBLE_ETA_DIAM),
+                      ("max_diam_lt_eta_dist", ibem.IBEM_ADMISSIBLE_ETA_DIST)):
+        for q in (4, 6, 8):
+            h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(W["p"], W["m"], q_cheb=q, eta=W["eta"],
+                                                                         admissibility=adm), stream)
+            ibem.ibem_assemble(h)
+            inf = ibem.ibem_get_info(h)
+            y = torch.empty_like(x)
+            ibem.ibem_matvec(h, x, y, 1, 0)
+            torch.cuda.synchronize()
+            out["%s_q%d" % (name, q)] = {"n_near": inf.n_near, "n_far": inf.n_far,
+                                         "rel_err_vs_dense": float((y - yd).abs().max() / yd.abs().max())}
+            ibem.ibem_destroy(h)
+    return out
+
+
 def _peak_tensor():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
