@@ -119,9 +119,28 @@ typedef struct {
                             IBEM_ADMISSIBLE_ETA_DIAM (0, default): admissible iff
                             eta * max(diam) < dist (eta = 1/mu);
                             IBEM_ADMISSIBLE_ETA_DIST (1): iff max(diam) < eta * dist */
+    int fp32_coupling;   /* coupling of the FP32 operator with 16..256 right-hand
+                            sides (tensor cores): IBEM_FP32_COUPLING_GENERATE (0,
+                            default) generates K per application; IBEM_FP32_
+                            COUPLING_STORE (1) stores it in BF16 at assembly when it
+                            fits in half of the free device memory (Helmholtz,
+                            q = 8: 16 KB per far block) and streams it */
+    int gauss_grading;   /* Gauss order raised towards the singularity (Sec. 4
+                            item 4: logarithmically, up to 40), 0..16; 0 = off.
+                            A non-touching near pair whose bounding balls give
+                            rho = dist / max(diam) takes
+                              n = min(40, gauss_regular + gauss_grading * k),
+                            k the least integer >= 0 with 2^k rho >= 3/4 (rho = 0:
+                            n = 40): gauss_grading more points per direction for
+                            every halving of the relative distance.  Subdivided
+                            pairs use n on each sub-square pair.  Touching pairs
+                            keep their Duffy rules (gauss_singular).  Pairs whose
+                            n differs from gauss_regular are formed by the
+                            streaming kernel with their own rule. */
 } ibem_params;
 
 enum { IBEM_ADMISSIBLE_ETA_DIAM = 0, IBEM_ADMISSIBLE_ETA_DIST = 1 };
+enum { IBEM_FP32_COUPLING_GENERATE = 0, IBEM_FP32_COUPLING_STORE = 1 };
 
 /* FP64 coupling variants.  GB300 executes FP64 FMA at 1/64 of the FP32 rate, so
  * by default the coupling matrices are stored as unevaluated float pairs
@@ -163,6 +182,8 @@ typedef struct {
     int64_t bytes_near;    /* device bytes of the stored FP64 near blocks           */
     int64_t bytes_far;     /* device bytes of the stored FP64 coupling matrices     */
     int assembled;         /* 1 after ibem_assemble                                 */
+    int max_gauss_order;   /* largest Gauss order of a non-touching near pair       */
+    int64_t n_near_graded; /* near pairs whose order differs from gauss_regular     */
 } ibem_info;
 
 typedef struct {
@@ -380,6 +401,13 @@ ibem_status ibem_batch_destroy(ibem_batch* b);
  * of the target cluster then of the source cluster.  Lists are sorted. */
 ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_params* params,
                             int64_t* n_near, int32_t* near, int64_t* n_far, int32_t* far);
+
+/* Host-only: the Gauss order per direction of every near pair, in the order of
+ * ibem_block_tree's near list: gauss_singular for touching pairs, the graded
+ * order (see gauss_grading) for the others.  order: [n_near] int32, or null to
+ * get the count only.  Errors as ibem_block_tree. */
+ibem_status ibem_near_orders(const ibem_patch* patches, int npatch, const ibem_params* params, int64_t* n_near,
+                             int32_t* order);
 
 /* ---------------------------------------------------------------------------
  * Learned right preconditioner.  The paper has no counterpart (it preconditions

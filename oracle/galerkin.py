@@ -15,6 +15,15 @@ patch maps and multiplied by both surface measures - is what ``LocalKernel``
 objects evaluate, so a test can substitute another kernel (for example one that
 is polynomial in the parameters).
 
+Graded orders (Sec. 4 item 4: the order rises logarithmically towards the
+singularity, up to 40; the rule is a reading): with grading > 0 a
+non-touching pair takes graded_order(n_regular, grading, dist, diam) points per
+direction (per sub-square pair when it is subdivided), dist and diam from the
+elements' bounding balls as in the classification.  Pinned by the separated
+flat squares of tests/test_oracle_grading.py (inclusion-exclusion over
+rectangle self-interactions) and by the order being n_regular + grading per
+halving of dist / diam below 3/4.
+
 Pinned by: V 1 = 1 (Laplace) and V 1 = sin(k) e^{ik} / k (Helmholtz) on the unit
 sphere, the Rayleigh quotients of Y_l against 1 / (2l + 1), the l = 1
 densities 3 z (Laplace) and z / (i k j_1(k) h_1(k)) (Helmholtz), symmetry and
@@ -25,6 +34,24 @@ import numpy as np
 from . import singular
 from .mesh import Mesh
 from .tree import bounding_ball
+
+
+MAX_GAUSS = 40
+
+
+def graded_order(n_regular, grading, dist, diam):
+    """Gauss order of a non-touching pair (Sec. 4 item 4: raised logarithmically
+    towards the singularity, up to 40; reading): n_regular + grading * k with k
+    the number of halvings of the ratio dist / diam below 3/4, i.e. the least
+    k >= 0 with 2^k dist >= 3/4 diam; capped at 40, and 40 for dist = 0."""
+    if grading == 0:
+        return n_regular
+    if not dist > 0.0:
+        return MAX_GAUSS
+    k = 0
+    while dist * 2.0 ** k < 0.75 * diam and n_regular + grading * k < MAX_GAUSS:
+        k += 1
+    return min(n_regular + grading * k, MAX_GAUSS)
 
 
 class LaplaceKernel:
@@ -55,11 +82,12 @@ def fundamental_solution(kernel, X, Y):
 
 
 class Discretisation:
-    def __init__(self, patches, p, m, kernel, n_regular=8, n_singular=8):
+    def __init__(self, patches, p, m, kernel, n_regular=8, n_singular=8, grading=0):
         self.mesh = Mesh(patches, p, m)
         self.kernel = kernel
         self.n_regular = n_regular
         self.n_singular = n_singular
+        self.grading = grading
         me = self.mesh
         self.corners = [me.element_corners(e) for e in range(me.n_elements)]
         self.balls = []
@@ -78,10 +106,11 @@ class Discretisation:
             self._rules[name] = fn(self.n_singular)
         return self._rules[name]
 
-    def _product_points(self, e, kind):
+    def _product_points(self, e, kind, n=None):
+        n = self.n_regular if n is None else n
         cache = self._regular_cache if kind == "regular" else self._nearsing_cache
-        if e not in cache:
-            st, w = singular.regular_rule(self.n_regular)
+        if (e, n) not in cache:
+            st, w = singular.regular_rule(n)
             if kind == "nearsing":
                 subs = [(0.0, 0.0), (0.5, 0.0), (0.0, 0.5), (0.5, 0.5)]
                 st = np.concatenate([np.stack((ox + 0.5 * st[:, 0], oy + 0.5 * st[:, 1]), axis=1)
@@ -91,8 +120,8 @@ class Discretisation:
             patch, _, _ = me.element(e)
             uv = me.to_patch(e, st)
             F, k = me.geometry(patch, uv)
-            cache[e] = (uv, F, k, w * me.h ** 2, me.local_basis(e, uv), patch)
-        return cache[e]
+            cache[(e, n)] = (uv, F, k, w * me.h ** 2, me.local_basis(e, uv), patch)
+        return cache[(e, n)]
 
     # ---- classification ----------------------------------------------------
     def pair_class(self, eA, eB):
@@ -115,14 +144,26 @@ class Discretisation:
             return "nearsing", 0, 0
         return "regular", 0, 0
 
+    def pair_order(self, eA, eB):
+        """Gauss points per direction of the pair: n_singular for touching pairs,
+        else graded_order of the bounding-ball distance ratio."""
+        cls, _, _ = self.pair_class(eA, eB)
+        if cls in ("identical", "edge", "vertex"):
+            return self.n_singular
+        (cA, rA), (cB, rB) = self.balls[eA], self.balls[eB]
+        diam = 2.0 * (rA if rA > rB else rB)
+        d = np.sqrt(np.sum((cA - cB) ** 2)) - rA - rB
+        return graded_order(self.n_regular, self.grading, d if d > 0.0 else 0.0, diam)
+
     # ---- element-pair block --------------------------------------------------
     def pair_block(self, eA, eB):
         """(p+1)^2 x (p+1)^2 block: rows = B-splines on eA, cols = on eB."""
         cls, ka, kb = self.pair_class(eA, eB)
         me = self.mesh
         if cls in ("regular", "nearsing"):
-            uvA, FA, kAv, wA, bA, pA = self._product_points(eA, cls)
-            uvB, FB, kBv, wB, bB, pB = self._product_points(eB, cls)
+            n = self.pair_order(eA, eB)
+            uvA, FA, kAv, wA, bA, pA = self._product_points(eA, cls, n)
+            uvB, FB, kBv, wB, bB, pB = self._product_points(eB, cls, n)
             K = self.kernel(FA[:, None, :], kAv[:, None], uvA[:, None, :], pA,
                             FB[None, :, :], kBv[None, :], uvB[None, :, :], pB)
             return bA.T @ ((wA[:, None] * K * wB[None, :]) @ bB)

@@ -19,13 +19,15 @@ common vertex (canonical form: vertex at x^ = y^ = 0): the 4-cube is cut into
 After each map |F(x^) - F(y^)| = xi |G| with G smooth and non-zero, so the
 integrand is smooth and every piece uses an 8-point Gauss rule per variable.
 
-Pair classes (reading; the paper's log-graded orders are not used):
+Pair classes (reading):
 * same element -> identical;
 * two physical corners in common -> common edge; one -> common vertex
   (corners match when |P - Q| <= 1e-10 * max diam);
 * otherwise dist < 0.5 * max diam (bounding balls) -> both elements split 2 x 2,
   8 x 8 Gauss on each sub-square pair ("near-singular");
 * otherwise 8 x 8 Gauss on each element ("regular").
+The orders of the last two classes may be graded by the distance ratio of the
+pair (``galerkin.graded_order``); the touching classes keep their rules.
 
 Canonical orientation: the eight symmetries of the square are listed in
 ``DIHEDRAL`` in a fixed order; for a touching pair (A, B) the first (k_A, k_B)

@@ -101,7 +101,7 @@ void free_handle(ibem_handle* h) {
                     h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
                     h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv, h->d_up_ptr, h->d_up_src,
                     h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr, h->d_Mf, h->d_Sf,
-                    h->d_gen_pts, h->d_gen_trig, h->d_gen_x};
+                    h->d_gen_pts, h->d_gen_trig, h->d_gen_x, h->d_Kbf, h->d_graded_pairs, h->d_graded_tab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -190,6 +190,22 @@ ibem_status ibem_block_tree(const ibem_patch* patches, int npatch, const ibem_pa
                 o[4] = a; o[5] = b; o[6] = x; o[7] = y;
             }
     }
+    return IBEM_OK;
+}
+
+ibem_status ibem_near_orders(const ibem_patch* patches, int npatch, const ibem_params* params, int64_t* n_near,
+                             int32_t* order) {
+    if (!n_near) return fail(nullptr, IBEM_ERR_ARG, "n_near must be non-null");
+    Plan P;
+    std::string msg;
+    try {
+        msg = build_plan(patches, npatch, params, P);
+    } catch (const std::bad_alloc&) {
+        return fail(nullptr, IBEM_ERR_OOM, "host allocation failed");
+    }
+    if (!msg.empty()) return fail(nullptr, plan_error_status(msg), msg);
+    *n_near = P.n_near;
+    if (order) std::copy(P.near_order.begin(), P.near_order.end(), order);
     return IBEM_OK;
 }
 
@@ -292,17 +308,57 @@ ibem_status ibem_create(const ibem_patch* patches, int npatch, const ibem_params
     // near and far lists
     std::vector<int32_t> ntgt(P.n_near);
     std::vector<std::vector<int32_t>> bycls(5);
+    std::vector<std::vector<int32_t>> bygrade(2 * (IBEM_MAX_GAUSS + 1));   // [subdiv][order]
     for (int64_t t = 0; t < P.E; ++t)
         for (int64_t k = P.near_ptr[t]; k < P.near_ptr[t + 1]; ++k) {
             ntgt[k] = (int32_t)t;
-            bycls[P.near_cls[k]].push_back((int32_t)k);
+            const int c = P.near_cls[k];
+            if ((c == CLS_REGULAR || c == CLS_SUBDIV) && P.near_order[k] != P.Q)
+                bygrade[(c == CLS_SUBDIV) * (IBEM_MAX_GAUSS + 1) + P.near_order[k]].push_back((int32_t)k);
+            else
+                bycls[c].push_back((int32_t)k);
         }
+    // graded groups: pairs, Gauss rule and Bernstein products at that order
+    {
+        std::vector<int32_t> gp;
+        std::vector<double> tab;
+        for (int sd = 0; sd < 2; ++sd)
+            for (int n = 1; n <= IBEM_MAX_GAUSS; ++n) {
+                const auto& lst = bygrade[sd * (IBEM_MAX_GAUSS + 1) + n];
+                if (lst.empty()) continue;
+                ibem_handle::GradedGroup gr{sd ? CLS_SUBDIV : CLS_REGULAR, n, (int64_t)gp.size(),
+                                            (int64_t)lst.size(), tab.size()};
+                gp.insert(gp.end(), lst.begin(), lst.end());
+                std::vector<double> nx, nw;
+                gauss_legendre(n, nx, nw);
+                tab.insert(tab.end(), nx.begin(), nx.end());
+                tab.insert(tab.end(), nw.begin(), nw.end());
+                const int nn = n * n, nsub = sd ? 4 : 1;
+                for (int sub = 0; sub < nsub; ++sub)
+                    for (int g = 0; g < nn; ++g) {
+                        double su = nx[g % n], sv = nx[g / n];
+                        if (sd) { su = 0.5 * (sub & 1) + 0.5 * su; sv = 0.5 * (sub >> 1) + 0.5 * sv; }
+                        bernstein(P.p, su, bu);
+                        bernstein(P.p, sv, bv);
+                        for (int iv = 0; iv < pp; ++iv)
+                            for (int iu = 0; iu < pp; ++iu) tab.push_back(bu[iu] * bv[iv]);
+                    }
+                h->graded.push_back(gr);
+            }
+        if (!gp.empty()) {
+            TRY(upload(&h->d_graded_pairs, gp, st), "upload graded pairs");
+            TRY(upload(&h->d_graded_tab, tab, st), "upload graded rules");
+        }
+    }
     TRY(upload(&h->d_near_ptr, P.near_ptr, st), "upload near ptr");
     TRY(upload(&h->d_near_src, P.near_src, st), "upload near src");
     TRY(upload(&h->d_near_tgt, ntgt, st), "upload near tgt");
     TRY(upload(&h->d_near_cls, P.near_cls, st), "upload near cls");
     TRY(upload(&h->d_near_orient, P.near_orient, st), "upload near orient");
-    for (int c = 0; c < 5; ++c) TRY(upload(&h->d_pairs_by_cls[c], bycls[c], st), "upload class lists");
+    for (int c = 0; c < 5; ++c) {
+        h->n_list[c] = (int64_t)bycls[c].size();
+        TRY(upload(&h->d_pairs_by_cls[c], bycls[c], st), "upload class lists");
+    }
     std::vector<int32_t> ftgt(P.n_far);
     for (int64_t c = 0; c < P.C; ++c) {
         if (P.far_ptr[c + 1] > P.far_ptr[c]) h->far_rows.push_back((int32_t)c);
@@ -402,6 +458,8 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     int64_t stored = (!h->helm && P.prm.fp64_coupling == IBEM_COUPLING_DF) ? h->n_up : P.n_far;
     info->bytes_far = h->far_on_the_fly ? 0 : stored * (int64_t)h->kpt * 4 * P.q2 * (h->helm ? 16 : 8);
     info->assembled = h->assembled ? 1 : 0;
+    info->max_gauss_order = P.max_order;
+    info->n_near_graded = P.n_graded;
     return IBEM_OK;
 }
 
@@ -451,6 +509,18 @@ ibem_status ibem_assemble(ibem_handle* h) {
     }
     if (!h->helm && h->d_Kdf && !h->up_rows.empty())
         if ((e = tune_coupling_df(h))) return cuda_fail(h, e, "coupling autotune");
+    if (P.prm.fp32_coupling == IBEM_FP32_COUPLING_STORE && mr_store_possible(h) && !h->d_Kbf) {
+        // BF16 coupling of the tensor-core path (16 KB per far block) if it fits in
+        // half of the free memory; otherwise the path keeps generating it
+        const size_t kb = (size_t)P.n_far * 128 * 64 * 2;
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        if (kb <= free_b / 2) {
+            if ((e = cudaMalloc(&h->d_Kbf, kb))) return cuda_fail(h, e, "alloc BF16 coupling");
+            if ((e = mr_store_coupling(h))) return cuda_fail(h, e, "BF16 coupling");
+            if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "BF16 coupling sync");
+        }
+    }
     if (P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY && h->d_near) {
         // the FP32 copy, the diagonal and the block-Jacobi inverses are formed
         if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "assemble sync");

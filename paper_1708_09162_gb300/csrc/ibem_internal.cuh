@@ -243,6 +243,9 @@ struct Plan {
     // near field: CSR by target element (sources ascending)
     std::vector<int64_t> near_ptr;
     std::vector<int32_t> near_src, near_cls, near_orient;
+    std::vector<int32_t> near_order;   // Gauss order per direction of every near pair
+    int max_order = 0;                 // largest order of a non-touching near pair
+    int64_t n_graded = 0;              // non-touching pairs with order != Q
     // far field: CSR by target cluster id (sources ascending)
     std::vector<int64_t> far_ptr;
     std::vector<int32_t> far_src;
@@ -302,6 +305,18 @@ struct ibem_handle {
     int32_t* d_near_cls = nullptr;
     int32_t* d_near_orient = nullptr;
     int32_t* d_pairs_by_cls[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int64_t n_list[5] = {0, 0, 0, 0, 0};   // lengths of d_pairs_by_cls (graded pairs excluded)
+    // graded near pairs (order != Q): one group per (class, order), its pairs
+    // contiguous in d_graded_pairs, its rule (nodes, weights) and Bernstein
+    // table ([1 or 4][n^2][nb]) at tab_off in d_graded_tab
+    struct GradedGroup {
+        int cls, order;
+        int64_t off, count;
+        size_t tab_off;
+    };
+    std::vector<GradedGroup> graded;
+    int32_t* d_graded_pairs = nullptr;
+    double* d_graded_tab = nullptr;
     double* d_near = nullptr;       // [n_near][nb][nb] (complex: [..][2])
     float* d_near32 = nullptr;
 
@@ -359,6 +374,7 @@ struct ibem_handle {
     // many-right-hand-side FP32 path (tensor-core coupling): one work area
     void* d_mr = nullptr;
     size_t mr_bytes = 0;
+    void* d_Kbf = nullptr;          // stored BF16 coupling blocks [n_far][128][64] (IBEM_FP32_COUPLING_STORE)
 
     // block-Jacobi preconditioner: blocks of dofs, inverse blocks
     int64_t* d_bj_ptr = nullptr;
@@ -433,6 +449,8 @@ __global__ void helm_split_vec_kernel(int R, int64_t n, const double* __restrict
 // subdivided pairs, used where the shared-matrix form needs more than
 // IBEM_MAX_SMEM_BYTES (near_shared_bytes) of shared memory
 cudaError_t launch_near_stream(ibem_handle* h, int cls, bool cplx, double kappa, double* blocks);
+// the graded pairs (orders != Q), one streaming launch per (class, order) group
+cudaError_t launch_near_graded(ibem_handle* h, bool cplx, double kappa, double* blocks);
 size_t near_shared_bytes(int Q, int nb, bool cplx, bool subdiv);
 // potential_fmm.cu
 cudaError_t launch_potential_fmm(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
@@ -454,6 +472,9 @@ ibem_status solve_block_impl(ibem_handle* h, const double* b, double* x, int R, 
 cudaError_t ensure_workspace(ibem_handle* h, int nrhs);
 cudaError_t build_block_jacobi(ibem_handle* h, std::string* err);
 bool mr_supported(const ibem_handle* h, int nrhs);
+// stored BF16 coupling of the tensor-core path (kernels_mrhs.cu)
+bool mr_store_possible(const ibem_handle* h);
+cudaError_t mr_store_coupling(ibem_handle* h);
 cudaError_t apply_operator_mrhs(ibem_handle* h, const double* x, double* y, int nrhs);
 void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
 // Helmholtz coupling generated in double-float for many right-hand sides (kernels_gen.cu).

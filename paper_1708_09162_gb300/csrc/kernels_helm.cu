@@ -708,28 +708,29 @@ cudaError_t helm_launch_near_assembly(ibem_handle* h) {
     if ((e = cudaMemcpyToSymbolAsync(c_hgw, gw.data(), P.Q * sizeof(double), 0, cudaMemcpyHostToDevice, h->stream))) return e;
     double2* blocks = reinterpret_cast<double2*>(h->d_near);
     for (int cls : {CLS_REGULAR, CLS_SUBDIV}) {
-        if (P.n_cls[cls] > 0 && near_shared_bytes(P.Q, nb, true, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
+        if (h->n_list[cls] > 0 && near_shared_bytes(P.Q, nb, true, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
             (e = launch_near_stream(h, cls, true, kappa, h->d_near)))
             return e;
     }
-    if (P.n_cls[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, true, false) <= IBEM_MAX_SMEM_BYTES) {
+    if ((e = launch_near_graded(h, true, kappa, h->d_near))) return e;
+    if (h->n_list[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, true, false) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(8 * QQ + 2 * QQ * QQ + 2 * QQ * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(helm_near_regular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        helm_near_regular_kernel<<<(unsigned)P.n_cls[CLS_REGULAR], 128, sm, h->stream>>>(
+        helm_near_regular_kernel<<<(unsigned)h->n_list[CLS_REGULAR], 128, sm, h->stream>>>(
             h->d_pairs_by_cls[CLS_REGULAR], h->d_near_tgt, h->d_near_src, h->d_qgeo, h->d_phi, QQ, nb, kappa, blocks);
     }
-    if (P.n_cls[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, true, true) <= IBEM_MAX_SMEM_BYTES) {
+    if (h->n_list[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, true, true) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(32 * QQ + 2 * QQ * QQ + 2 * QQ * nb + 2 * nb * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(helm_near_subdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        helm_near_subdiv_kernel<<<(unsigned)P.n_cls[CLS_SUBDIV], 128, sm, h->stream>>>(
+        helm_near_subdiv_kernel<<<(unsigned)h->n_list[CLS_SUBDIV], 128, sm, h->stream>>>(
             g, h->d_pairs_by_cls[CLS_SUBDIV], h->d_near_tgt, h->d_near_src, h->d_phi_sub, P.Q, nb, P.ne1, kappa, blocks);
     }
     for (int c = 0; c < 3; ++c) {
-        if (P.n_cls[c] == 0) continue;
+        if (h->n_list[c] == 0) continue;
         const int CH = 128;
         size_t sm = (size_t)3 * nb * CH * sizeof(double);
         if ((e = cudaFuncSetAttribute(helm_near_singular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        helm_near_singular_kernel<<<(unsigned)P.n_cls[c], CH, sm, h->stream>>>(
+        helm_near_singular_kernel<<<(unsigned)h->n_list[c], CH, sm, h->stream>>>(
             g, h->d_pairs_by_cls[c], h->d_near_tgt, h->d_near_src, h->d_near_orient, h->d_rule[c], h->rule_n[c], P.p,
             P.ne1, kappa, blocks);
     }

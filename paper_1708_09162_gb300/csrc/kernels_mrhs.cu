@@ -21,6 +21,8 @@
 // K, SBO = (KAP / 8) * 128 bytes along M or N.  All waits are bounded.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "ibem_internal.cuh"
 
 namespace ibem {
@@ -465,6 +467,211 @@ __global__ void __launch_bounds__(544) mr_coupling_tc_kernel(
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
+// ---- stored BF16 coupling (IBEM_FP32_COUPLING_STORE, Helmholtz, q = 8) ----------------------
+// Each far block is generated once at assembly, with the same FP32 formula as the
+// generating kernel above, and kept as one 128 x 64 BF16 tile: rows a < 64 hold
+// Re K[a][.], rows 64 + a hold Im K[a][.] (no-swizzle K-major layout, 16 KB).  An
+// application packs the moments per cluster as [N = 2 RQ][64] BF16 (rows n < RQ
+// the real parts of right-hand side n, rows RQ + n the imaginary parts), and one
+// M = 128, N = 2 RQ MMA group per far block accumulates
+// D = [Re K; Im K] [Re x^ | Im x^] in TMEM; the epilogue forms
+// Re y^ = D[a][n] - D[64 + a][RQ + n], Im y^ = D[a][RQ + n] + D[64 + a][n].
+// The kernel streams K (16 KB per block) and the moments by cp.async.bulk into
+// a ring of NST stages: lane 0 of warp 0 issues the copies, lane 0 of warp 1
+// the MMAs; all waits are bounded.
+constexpr int ST_Q2 = 64;            // q = 8
+constexpr int ST_NST = 4;            // ring stages
+constexpr int ST_ABYTES = 128 * ST_Q2 * 2;
+
+__device__ inline int st_tile_off(int m, int k) {   // element offset in a [rows][64] canonical tile
+    return ((m >> 3) * 8 + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
+}
+
+__global__ void mr_store_kernel(int64_t n_far, const int32_t* __restrict__ ftgt, const int32_t* __restrict__ fsrc,
+                                const float4* __restrict__ geo, float kappa, __nv_bfloat16* __restrict__ K) {
+    const int64_t blk = blockIdx.x;
+    if (blk >= n_far) return;
+    const float4* X = geo + (int64_t)ftgt[blk] * ST_Q2;
+    const float4* Y = geo + (int64_t)fsrc[blk] * ST_Q2;
+    __nv_bfloat16* T = K + blk * (128 * ST_Q2);
+    for (int e = threadIdx.x; e < ST_Q2 * ST_Q2; e += blockDim.x) {
+        const int a = e / ST_Q2, b = e % ST_Q2;
+        const float4 x = X[a], y = Y[b];
+        const float d0 = x.x - y.x, d1 = x.y - y.y, d2 = x.z - y.z;
+        const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        const float rinv = rsqrtf(r2);
+        const float w = (x.w * 0.07957747154594767f) * y.w * rinv;
+        float ph = kappa * (r2 * rinv);
+        ph = fmaf(-6.283185307179586f, rintf(ph * 0.15915494309189535f), ph);
+        float sn, cs;
+        __sincosf(ph, &sn, &cs);
+        T[st_tile_off(a, b)] = __float2bfloat16(w * cs);
+        T[st_tile_off(ST_Q2 + a, b)] = __float2bfloat16(w * sn);
+    }
+}
+
+// moments x^ [C][64][R] (float2) -> per (chunk, cluster) [2 RQ][64] BF16 tiles
+__global__ void mr_bpack_stored_kernel(int R, int RQ, int nch, int64_t C, const float2* __restrict__ xh,
+                                       __nv_bfloat16* __restrict__ xb) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int N = 2 * RQ;
+    if (idx >= (int64_t)nch * C * N * ST_Q2) return;
+    const int k = (int)(idx % ST_Q2);
+    int64_t rem = idx / ST_Q2;
+    const int n = (int)(rem % N);
+    rem /= N;
+    const int64_t c = rem % C;
+    const int ch = (int)(rem / C);
+    const int r = ch * 64 + (n < RQ ? n : n - RQ);   // RQ <= 64
+    float v = 0.0f;
+    if (r < R) {
+        const float2 x = xh[(c * ST_Q2 + k) * R + r];
+        v = n < RQ ? x.x : x.y;
+    }
+    xb[((int64_t)ch * C + c) * N * ST_Q2 + st_tile_off(n, k)] = __float2bfloat16(v);
+}
+
+__global__ void __launch_bounds__(128) mr_coupling_stored_kernel(
+    const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
+    const __nv_bfloat16* __restrict__ Kst, const __nv_bfloat16* __restrict__ xb, int R, int RQ, int64_t C,
+    int tcols, float2* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);          // [ST_NST]
+    uint64_t* empty = full + ST_NST;                              // [ST_NST]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 128);
+    int* flag = reinterpret_cast<int*>(smem + 136);
+    int* counts = reinterpret_cast<int*>(smem + 144);             // blocks copied, blocks consumed
+    const int N = 2 * RQ;
+    const unsigned bbytes = (unsigned)N * ST_Q2 * 2;
+    const size_t sbytes = ST_ABYTES + (size_t)bbytes;
+    unsigned char* tiles = smem + 1024;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int sigma = rows[blockIdx.x];
+    const int chunk = blockIdx.y;
+    const int64_t b0 = fptr[sigma];
+    const int n = (int)(fptr[sigma + 1] - b0);
+    const __nv_bfloat16* xc = xb + (int64_t)chunk * C * N * ST_Q2;
+    if (t == 0) {
+        for (int i = 0; i < ST_NST; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&full[i])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm(&empty[i])) : "memory");
+        }
+        *flag = 0;
+        counts[0] = counts[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tsm(tslot)), "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    int copied = 0, consumed = 0;
+    volatile int* vflag = flag;
+    bool failed = false;
+    if (t == 0) {
+        // producer: block i into stage i % ST_NST once the MMAs of block i - ST_NST are done
+        for (int i = 0; i < n; ++i) {
+            const int st = i % ST_NST;
+            if (*vflag) { failed = true; break; }
+            if (i >= ST_NST && !tc_wait(&empty[st], (unsigned)((i / ST_NST - 1) & 1), wait_limit)) {
+                atomicOr(flag, 1);
+                failed = true;
+                break;
+            }
+            unsigned char* dst = tiles + st * sbytes;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tsm(&full[st])),
+                         "r"((unsigned)ST_ABYTES + bbytes)
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tsm(dst)),
+                         "l"(Kst + (b0 + i) * (int64_t)(128 * ST_Q2)), "r"((unsigned)ST_ABYTES), "r"(tsm(&full[st]))
+                         : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             tsm(dst + ST_ABYTES)),
+                         "l"(xc + (int64_t)fsrc[b0 + i] * N * ST_Q2), "r"(bbytes), "r"(tsm(&full[st]))
+                         : "memory");
+            copied = i + 1;
+        }
+        counts[0] = copied;
+    } else if (t == 32) {
+        // MMA issuer
+        for (int i = 0; i < n; ++i) {
+            const int st = i % ST_NST;
+            if (*vflag) { failed = true; break; }
+            if (!tc_wait(&full[st], (unsigned)((i / ST_NST) & 1), wait_limit)) {
+                atomicOr(flag, 1);
+                failed = true;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* src = tiles + st * sbytes;
+            for (int kk = 0; kk < ST_Q2 / 16; ++kk) {
+                const uint64_t ad = umma_desc(tsm(src) + kk * 256, 128, 8 * 128);
+                const uint64_t bd = umma_desc(tsm(src + ST_ABYTES) + kk * 256, 128, 8 * 128);
+                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             tsm(&empty[st]))
+                         : "memory");
+            consumed = i + 1;
+        }
+        counts[1] = consumed;
+    }
+    if (__syncthreads_or(failed)) failed = true;
+    // the last committed MMA group completes the accumulator
+    bool ok = !failed;
+    if (n > 0 && ok) ok = tc_wait(&empty[(n - 1) % ST_NST], (unsigned)(((n - 1) / ST_NST) & 1), wait_limit);
+    if (failed && t == 0) {
+        // copies issued but not consumed land before the CTA leaves (bounded waits)
+        for (int i = counts[1]; i < counts[0]; ++i) tc_wait(&full[i % ST_NST], (unsigned)((i / ST_NST) & 1), 1LL << 20);
+        // MMAs committed but not waited for finish too
+        if (counts[1] > 0) tc_wait(&empty[(counts[1] - 1) % ST_NST], (unsigned)(((counts[1] - 1) / ST_NST) & 1), 1LL << 20);
+    }
+    if (__syncthreads_or(!ok)) {
+        if (t == 0) atomicOr(status, 1);
+    } else if (n > 0) {
+        // accumulator rows to shared memory (the ring is free), then combine
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float* S = reinterpret_cast<float*>(tiles);              // [128][N]
+        const int row = 32 * warp + lane;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int j = 0; j < 16; ++j) S[row * N + c0 + j] = __uint_as_float(v[j]);
+        }
+        __syncthreads();
+        const int r0 = chunk * 64;
+        const int rc = R - r0 < 64 ? R - r0 : 64;
+        for (int e = t; e < ST_Q2 * rc; e += blockDim.x) {
+            const int a = e / rc, j = e % rc;
+            const float yr = S[a * N + j] - S[(ST_Q2 + a) * N + RQ + j];
+            const float yi = S[a * N + RQ + j] + S[(ST_Q2 + a) * N + j];
+            yh[((int64_t)sigma * ST_Q2 + a) * R + r0 + j] = make_float2(yr, yi);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
 // ---- L2L, back-projection, near field, restriction ---------------------------------------
 template <bool CPLX>
 __global__ void mr_back_kernel(int R, int64_t E, int pp, int q, const float* __restrict__ M,
@@ -633,7 +840,12 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
     const int KAP = ((CPLX ? 2 * q2 : q2) + 15) & ~15;
     // work space (grown on demand)
     const size_t need_t = (size_t)R * P.N, need_s = (size_t)R * P.Nstar, need_h = (size_t)R * P.C * (q2 > 0 ? q2 : 1);
-    const size_t need_b = (size_t)P.C * RP * (KAP > 0 ? KAP : 16);
+    // moments as BF16 tiles: generated coupling [C][RP][KAP]; stored coupling
+    // [nch][C][2 RQ][64] with chunks of 64 right-hand sides
+    const bool stored = CPLX && h->d_Kbf != nullptr;
+    const int RQ = ((R < 64 ? R : 64) + 7) & ~7, nch = (R + 63) / 64;
+    size_t need_b = (size_t)P.C * RP * (KAP > 0 ? KAP : 16);
+    if (stored) need_b = std::max(need_b, (size_t)nch * P.C * 2 * RQ * ST_Q2);
     const size_t bytes = sizeof(T) * (need_t + 2 * need_s + 2 * need_h) + 2 * need_b + 1024;
     if (bytes > h->mr_bytes) {
         cudaFree(h->d_mr);
@@ -672,7 +884,21 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
         }
         if ((e = cudaMemsetAsync(yh, 0, need_h * sizeof(T), st))) return e;
         const unsigned nrows = (unsigned)h->far_rows.size();
-        if (nrows > 0) {
+        if (nrows > 0 && stored) {
+            PhaseTimer pt(h, 2);
+            mr_bpack_stored_kernel<<<nblk((int64_t)nch * P.C * 2 * RQ * ST_Q2, T_), T_, 0, st>>>(
+                R, RQ, nch, P.C, reinterpret_cast<const float2*>(xh), xb);
+            int tcols = 32;
+            while (tcols < 2 * RQ) tcols <<= 1;
+            const size_t sm = 1024 + (size_t)ST_NST * (ST_ABYTES + (size_t)2 * RQ * ST_Q2 * 2);
+            if ((e = cudaFuncSetAttribute(mr_coupling_stored_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)))
+                return e;
+            mr_coupling_stored_kernel<<<dim3(nrows, nch), 128, sm, st>>>(
+                h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const __nv_bfloat16*>(h->d_Kbf), xb, R,
+                RQ, P.C, tcols, reinterpret_cast<float2*>(yh), h->wait_limit, h->d_status);
+            h->launches += 2;
+        } else if (nrows > 0) {
             PhaseTimer pt(h, 2);
             mr_bpack_kernel<CPLX><<<nblk((int64_t)P.C * RP * KAP, T_), T_, 0, st>>>(R, RP, KAP, P.C, q2, xh, xb);
             int tcols = 32;
@@ -717,6 +943,17 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
         mr_restrict_kernel<CPLX><<<nblk((int64_t)R * P.N, T_), T_, 0, st>>>(R, P.N, P.p, P.ne1, h->d_ext, ys, y);
     }
     h->launches += 2;
+    return cudaGetLastError();
+}
+
+bool mr_store_possible(const ibem_handle* h) { return h->helm && h->P.q2 == ST_Q2 && h->P.n_far > 0; }
+
+cudaError_t mr_store_coupling(ibem_handle* h) {
+    const Plan& P = h->P;
+    mr_store_kernel<<<(unsigned)P.n_far, 256, 0, h->stream>>>(P.n_far, h->d_far_tgt, h->d_far_src,
+                                                              reinterpret_cast<const float4*>(h->d_igeo32),
+                                                              (float)P.prm.kappa,
+                                                              reinterpret_cast<__nv_bfloat16*>(h->d_Kbf));
     return cudaGetLastError();
 }
 

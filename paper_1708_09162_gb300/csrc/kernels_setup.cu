@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int
                                                            const int32_t* __restrict__ src,
                                                            const double* __restrict__ qgeo,
                                                            const double* __restrict__ phi, int Q, int ne1,
-                                                           bool subdiv, double kappa, double* __restrict__ blocks) {
+                                                           bool subdiv, double kappa, const double* __restrict__ rule,
+                                                           double* __restrict__ blocks) {
     extern __shared__ double sm[];
     constexpr int CW = CPLX ? 2 : 1;
     constexpr int NE = (NB * NB + NS_T - 1) / NS_T;     // block entries per thread
@@ -225,25 +226,30 @@ __global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int
 #pragma unroll
         for (int c = 0; c < CW; ++c) acc[i][c] = 0.0;
     const int nsub = subdiv ? 4 : 1;
+    // rule given (a graded order): nodes rule[0..Q), weights rule[Q..2Q), and the
+    // geometry evaluated here; otherwise the module rule and the qgeo table
+    const double* gx = rule ? rule : c_gx;
+    const double* gw = rule ? rule + Q : c_gw;
+    const double sc = subdiv ? 0.5 : 1.0;
     for (int sa = 0; sa < nsub; ++sa)
         for (int sb = 0; sb < nsub; ++sb) {
             __syncthreads();   // the previous pass is done with XA, XB and H
             for (int i = threadIdx.x; i < 2 * QQ; i += NS_T) {
                 const int which = i / QQ, gq = i % QQ;
                 double* o = (which ? XB : XA) + 4 * gq;
-                if (!subdiv) {
+                if (!subdiv && !rule) {
                     const double* in = qgeo + 4 * (QQ * (which ? s : t) + gq);
                     o[0] = in[0]; o[1] = in[1]; o[2] = in[2]; o[3] = in[3];
                 } else {
                     const int sub = which ? sb : sa;
                     int patch, ix, iy;
                     dev_element_of(which ? s : t, ne1, &patch, &ix, &iy);
-                    const double su = 0.5 * (sub & 1) + 0.5 * c_gx[gq % Q];
-                    const double sv = 0.5 * (sub >> 1) + 0.5 * c_gx[gq / Q];
+                    const double su = sc * (sub & 1) + sc * gx[gq % Q];
+                    const double sv = sc * (sub >> 1) + sc * gx[gq / Q];
                     double F[3], Fu[3], Fv[3];
                     eval_patch(g, patch, (ix + su) * h, (iy + sv) * h, F, Fu, Fv);
                     o[0] = F[0]; o[1] = F[1]; o[2] = F[2];
-                    o[3] = 0.25 * c_gw[gq % Q] * c_gw[gq / Q] * surface_measure(Fu, Fv) * h * h;
+                    o[3] = sc * sc * gw[gq % Q] * gw[gq / Q] * surface_measure(Fu, Fv) * h * h;
                 }
             }
             __syncthreads();
@@ -319,7 +325,7 @@ cudaError_t launch_near_stream_t(ibem_handle* h, int cls, double kappa, double* 
     const int QQ = P.Q * P.Q;
     const size_t sm = (size_t)(8 * QQ + (CPLX ? 2 : 1) * NS_T * P.nb) * sizeof(double);
     const double* phi = subdiv ? h->d_phi_sub : h->d_phi;
-    const unsigned n = (unsigned)P.n_cls[cls];
+    const unsigned n = (unsigned)h->n_list[cls];
     cudaError_t e;
 #define IBEM_NS_CASE(NB_)                                                                                      \
     case NB_:                                                                                                  \
@@ -328,7 +334,7 @@ cudaError_t launch_near_stream_t(ibem_handle* h, int cls, double kappa, double* 
             return e;                                                                                          \
         near_stream_kernel<CPLX, NB_><<<n, NS_T, sm, h->stream>>>(g, h->d_pairs_by_cls[cls], h->d_near_tgt,     \
                                                                   h->d_near_src, h->d_qgeo, phi, P.Q, P.ne1,    \
-                                                                  subdiv, kappa, blocks);                       \
+                                                                  subdiv, kappa, nullptr, blocks);              \
         break;
     switch (P.nb) {
         IBEM_NS_CASE(1)
@@ -340,6 +346,49 @@ cudaError_t launch_near_stream_t(ibem_handle* h, int cls, double kappa, double* 
     }
 #undef IBEM_NS_CASE
     return cudaGetLastError();
+}
+
+// Graded pairs: one streaming launch per (class, order) group, each with its
+// own rule and Bernstein table.
+template <bool CPLX>
+cudaError_t launch_near_graded_t(ibem_handle* h, double kappa, double* blocks) {
+    Plan& P = h->P;
+    GeomView g{h->d_patches, h->d_knots, h->d_cpw};
+    cudaError_t e;
+    for (const auto& gr : h->graded) {
+        const int Q = gr.order, QQ = Q * Q;
+        const bool subdiv = gr.cls == CLS_SUBDIV;
+        const size_t sm = (size_t)(8 * QQ + (CPLX ? 2 : 1) * NS_T * P.nb) * sizeof(double);
+        if (sm > IBEM_MAX_SMEM_BYTES) return cudaErrorInvalidValue;
+        const double* rule = h->d_graded_tab + gr.tab_off;
+        const double* phi = rule + 2 * Q;
+        const int32_t* list = h->d_graded_pairs + gr.off;
+        const unsigned n = (unsigned)gr.count;
+#define IBEM_NG_CASE(NB_)                                                                                        \
+    case NB_:                                                                                                    \
+        if ((e = cudaFuncSetAttribute(near_stream_kernel<CPLX, NB_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                      (int)sm)))                                                                  \
+            return e;                                                                                            \
+        near_stream_kernel<CPLX, NB_><<<n, NS_T, sm, h->stream>>>(g, list, h->d_near_tgt, h->d_near_src, nullptr, \
+                                                                  phi, Q, P.ne1, subdiv, kappa, rule, blocks);    \
+        break;
+        switch (P.nb) {
+            IBEM_NG_CASE(1)
+            IBEM_NG_CASE(4)
+            IBEM_NG_CASE(9)
+            IBEM_NG_CASE(16)
+            IBEM_NG_CASE(25)
+            default: return cudaErrorInvalidValue;
+        }
+#undef IBEM_NG_CASE
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_near_graded(ibem_handle* h, bool cplx, double kappa, double* blocks) {
+    if (h->graded.empty()) return cudaSuccess;
+    return cplx ? launch_near_graded_t<true>(h, kappa, blocks) : launch_near_graded_t<false>(h, kappa, blocks);
 }
 
 cudaError_t launch_near_stream(ibem_handle* h, int cls, bool cplx, double kappa, double* blocks) {
@@ -549,32 +598,33 @@ cudaError_t launch_near_assembly(ibem_handle* h) {
             return e;
     }
     for (int cls : {CLS_REGULAR, CLS_SUBDIV}) {
-        if (P.n_cls[cls] > 0 && near_shared_bytes(P.Q, nb, false, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
+        if (h->n_list[cls] > 0 && near_shared_bytes(P.Q, nb, false, cls == CLS_SUBDIV) > IBEM_MAX_SMEM_BYTES &&
             (e = launch_near_stream(h, cls, false, 0.0, h->d_near)))
             return e;
     }
+    if ((e = launch_near_graded(h, false, 0.0, h->d_near))) return e;
     // regular
-    if (P.n_cls[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, false, false) <= IBEM_MAX_SMEM_BYTES) {
+    if (h->n_list[CLS_REGULAR] > 0 && near_shared_bytes(P.Q, nb, false, false) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(8 * QQ + QQ * QQ + QQ * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(near_regular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        near_regular_kernel<<<(unsigned)P.n_cls[CLS_REGULAR], 128, sm, h->stream>>>(
-            h->d_pairs_by_cls[CLS_REGULAR], P.n_cls[CLS_REGULAR], h->d_near_tgt, h->d_near_src, h->d_qgeo,
+        near_regular_kernel<<<(unsigned)h->n_list[CLS_REGULAR], 128, sm, h->stream>>>(
+            h->d_pairs_by_cls[CLS_REGULAR], h->n_list[CLS_REGULAR], h->d_near_tgt, h->d_near_src, h->d_qgeo,
             h->d_phi, QQ, nb, h->d_near);
     }
-    if (P.n_cls[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, false, true) <= IBEM_MAX_SMEM_BYTES) {
+    if (h->n_list[CLS_SUBDIV] > 0 && near_shared_bytes(P.Q, nb, false, true) <= IBEM_MAX_SMEM_BYTES) {
         size_t sm = (size_t)(32 * QQ + QQ * QQ + QQ * nb + nb * nb) * sizeof(double);
         if ((e = cudaFuncSetAttribute(near_subdiv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        near_subdiv_kernel<<<(unsigned)P.n_cls[CLS_SUBDIV], 128, sm, h->stream>>>(
-            g, h->d_pairs_by_cls[CLS_SUBDIV], P.n_cls[CLS_SUBDIV], h->d_near_tgt, h->d_near_src, h->d_phi_sub,
+        near_subdiv_kernel<<<(unsigned)h->n_list[CLS_SUBDIV], 128, sm, h->stream>>>(
+            g, h->d_pairs_by_cls[CLS_SUBDIV], h->n_list[CLS_SUBDIV], h->d_near_tgt, h->d_near_src, h->d_phi_sub,
             P.Q, nb, P.ne1, h->d_near);
     }
     for (int c = 0; c < 3; ++c) {
-        if (P.n_cls[c] == 0) continue;
+        if (h->n_list[c] == 0) continue;
         const int CH = 128;
         size_t sm = (size_t)2 * nb * CH * sizeof(double);
         if ((e = cudaFuncSetAttribute(near_singular_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm))) return e;
-        near_singular_kernel<<<(unsigned)P.n_cls[c], CH, sm, h->stream>>>(
-            g, h->d_pairs_by_cls[c], P.n_cls[c], h->d_near_tgt, h->d_near_src, h->d_near_orient, h->d_rule[c],
+        near_singular_kernel<<<(unsigned)h->n_list[c], CH, sm, h->stream>>>(
+            g, h->d_pairs_by_cls[c], h->n_list[c], h->d_near_tgt, h->d_near_src, h->d_near_orient, h->d_rule[c],
             h->rule_n[c], P.p, P.ne1, h->d_near);
     }
     if ((e = cudaGetLastError())) return e;

@@ -17,6 +17,10 @@
 // Near pairs are classified for the quadrature (Sec. 4 item 4): identical,
 // common edge, common vertex (corners equal to 1e-10 * diam), "subdivided"
 // (dist < diam / 2: 2 x 2 split of both elements), otherwise regular.
+// Graded orders (Sec. 4 item 4, read as gauss_grading more points per
+// direction for every halving of rho = dist / diam below 3/4, up to 40): the
+// thresholds 3/4, 3/8, ... lie away from the ratios of a flat lattice
+// (0.414, 0.581, 1, 1.12, ...), so the decision is stable under rounding.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -195,6 +199,22 @@ double ball_dist(const Ball& a, const Ball& b) {
     return d > 0.0 ? d : 0.0;
 }
 
+// Gauss order of a non-touching near pair: base + grading * k with k the least
+// k >= 0 such that 2^k dist >= (3/4) diam, capped at IBEM_MAX_GAUSS (dist = 0:
+// the cap).  Doubling is exact, so only the comparison rounds.
+int graded_order(int base, int grading, double dist, double diam) {
+    if (grading == 0) return base;
+    if (!(dist > 0.0)) return IBEM_MAX_GAUSS;
+    int k = 0;
+    double d = dist;
+    while (d < 0.75 * diam && base + grading * k < IBEM_MAX_GAUSS) {
+        d *= 2.0;
+        ++k;
+    }
+    int n = base + grading * k;
+    return n < IBEM_MAX_GAUSS ? n : IBEM_MAX_GAUSS;
+}
+
 int dihedral_corner(int k, int s, int t) {
     double x, y;
     dihedral(k, (double)s, (double)t, &x, &y);
@@ -221,10 +241,13 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.m < 0 || q.m > 10) return "m must be in 0..10";
     if (q.q_cheb != 0 && (q.q_cheb < 2 || q.q_cheb > IBEM_MAX_Q)) return "q_cheb must be 0 or 2..12";
     if (q.q_cheb != 0 && !(q.eta > 0.0)) return "eta must be > 0";
+    if (q.fp32_coupling != IBEM_FP32_COUPLING_GENERATE && q.fp32_coupling != IBEM_FP32_COUPLING_STORE)
+        return "fp32_coupling must be IBEM_FP32_COUPLING_GENERATE or IBEM_FP32_COUPLING_STORE";
     if (q.admissibility != IBEM_ADMISSIBLE_ETA_DIAM && q.admissibility != IBEM_ADMISSIBLE_ETA_DIST)
         return "admissibility must be IBEM_ADMISSIBLE_ETA_DIAM or IBEM_ADMISSIBLE_ETA_DIST";
     if (q.gauss_regular < 1 || q.gauss_regular > IBEM_MAX_GAUSS) return "gauss_regular must be in 1..40";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
+    if (q.gauss_grading < 0 || q.gauss_grading > 16) return "gauss_grading must be in 0..16";
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
         q.fp64_coupling != IBEM_COUPLING_NONE && q.fp64_coupling != IBEM_COUPLING_GENERATE &&
         q.fp64_coupling != IBEM_COUPLING_FP32_ONLY)
@@ -371,12 +394,15 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     P.near_src.resize(P.n_near);
     P.near_cls.resize(P.n_near);
     P.near_orient.resize(P.n_near);
+    P.near_order.resize(P.n_near);
+    P.max_order = 0;
+    P.n_graded = 0;
     for (int k = 0; k < 5; ++k) P.n_cls[k] = 0;
     for (int64_t k = 0; k < P.n_near; ++k) {
         int64_t t = near[k].first, s = near[k].second;
         P.near_ptr[t + 1]++;
         P.near_src[k] = (int32_t)s;
-        int cls = CLS_REGULAR, orient = 0;
+        int cls = CLS_REGULAR, orient = 0, order = P.Qs;
         if (t == s) {
             cls = CLS_IDENTICAL;
         } else {
@@ -409,10 +435,14 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
             } else {
                 double dist = ball_dist(bA, bB);
                 cls = dist < 0.5 * diam ? CLS_SUBDIV : CLS_REGULAR;
+                order = graded_order(P.Q, q.gauss_grading, dist, diam);
+                if (order > P.max_order) P.max_order = order;
+                if (order != P.Q) ++P.n_graded;
             }
         }
         P.near_cls[k] = cls;
         P.near_orient[k] = orient;
+        P.near_order[k] = order;
         P.n_cls[cls]++;
     }
     for (int64_t e = 0; e < P.E; ++e) P.near_ptr[e + 1] += P.near_ptr[e];

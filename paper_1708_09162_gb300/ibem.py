@@ -36,7 +36,7 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
             "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
-            "ibem_cnn_train_operator", "ibem_cnn_device_status", "ibem_cnn_set_coarsening")
+            "ibem_cnn_train_operator", "ibem_cnn_device_status", "ibem_cnn_set_coarsening", "ibem_near_orders")
 
 
 class IbemError(RuntimeError):
@@ -57,14 +57,16 @@ class ibem_patch(ctypes.Structure):
 class ibem_params(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("kappa", ctypes.c_double), ("p", ctypes.c_int), ("m", ctypes.c_int),
                 ("q_cheb", ctypes.c_int), ("eta", ctypes.c_double), ("gauss_regular", ctypes.c_int),
-                ("gauss_singular", ctypes.c_int), ("fp64_coupling", ctypes.c_int), ("admissibility", ctypes.c_int)]
+                ("gauss_singular", ctypes.c_int), ("fp64_coupling", ctypes.c_int), ("admissibility", ctypes.c_int),
+                ("fp32_coupling", ctypes.c_int), ("gauss_grading", ctypes.c_int)]
 
 
 class ibem_info(ctypes.Structure):
     _fields_ = [("ndof", ctypes.c_int64), ("ndof_super", ctypes.c_int64), ("n_elements", ctypes.c_int64),
                 ("n_clusters", ctypes.c_int64), ("n_quad_points", ctypes.c_int64), ("n_near", ctypes.c_int64),
                 ("n_far", ctypes.c_int64), ("n_near_singular", ctypes.c_int64 * 4),
-                ("bytes_near", ctypes.c_int64), ("bytes_far", ctypes.c_int64), ("assembled", ctypes.c_int)]
+                ("bytes_near", ctypes.c_int64), ("bytes_far", ctypes.c_int64), ("assembled", ctypes.c_int),
+                ("max_gauss_order", ctypes.c_int), ("n_near_graded", ctypes.c_int64)]
 
 
 class ibem_solve_info(ctypes.Structure):
@@ -99,6 +101,8 @@ def _load():
         "ibem_potential_fmm": (I32, [P, P, I32, P, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "ibem_block_tree": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
                                   ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
+        "ibem_near_orders": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
+                                   ctypes.POINTER(I64), P]),
         "ibem_profile_enable": (I32, [P, I32]),
         "ibem_profile_read": (I32, [P, ctypes.POINTER(ibem_profile_data)]),
         "ibem_set_wait_limit": (I32, [P, ctypes.c_longlong]),
@@ -212,12 +216,14 @@ IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERA
 
 
 IBEM_ADMISSIBLE_ETA_DIAM, IBEM_ADMISSIBLE_ETA_DIST = 0, 1
+IBEM_FP32_COUPLING_GENERATE, IBEM_FP32_COUPLING_STORE = 0, 1
 
 
 def make_params(p, m, q_cheb=6, eta=1.6, kernel=IBEM_LAPLACE, kappa=0.0, gauss_regular=8, gauss_singular=8,
-                fp64_coupling=IBEM_COUPLING_DF, admissibility=IBEM_ADMISSIBLE_ETA_DIAM):
+                fp64_coupling=IBEM_COUPLING_DF, admissibility=IBEM_ADMISSIBLE_ETA_DIAM,
+                fp32_coupling=IBEM_FP32_COUPLING_GENERATE, gauss_grading=0):
     return ibem_params(kernel, kappa, p, m, q_cheb, eta, gauss_regular, gauss_singular, fp64_coupling,
-                       admissibility)
+                       admissibility, fp32_coupling, gauss_grading)
 
 
 # ---- entry points --------------------------------------------------------------------
@@ -296,6 +302,16 @@ def ibem_block_tree(patches, params):
                                 near.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf),
                                 far.ctypes.data_as(ctypes.c_void_p)))
     return near, far
+
+
+def ibem_near_orders(patches, params):
+    """Host only.  Gauss order of every near pair, in the order of ibem_block_tree's near list."""
+    nn = ctypes.c_int64()
+    _check(_lib.ibem_near_orders(patches, len(patches), ctypes.byref(params), ctypes.byref(nn), None))
+    out = np.zeros(nn.value, dtype=np.int32)
+    _check(_lib.ibem_near_orders(patches, len(patches), ctypes.byref(params), ctypes.byref(nn),
+                                 out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def ibem_profile_enable(h, enable=True):

@@ -164,3 +164,28 @@ def test_batched_instances_vs_oracle():
     ibem.ibem_batch_destroy(b)
     for h in handles:
         ibem.ibem_destroy(h)
+
+
+@pytest.mark.parametrize("R", [16, 40, 70])
+def test_stored_bf16_coupling_vs_oracle(R):
+    # IBEM_FP32_COUPLING_STORE: the BF16 blocks generated once at assembly and
+    # streamed (stacked real / imaginary rows, one MMA group per block), same
+    # bound as the generated tensor-core coupling; chunks of 64 right-hand sides
+    # (70 = 64 + 6); close to the generating kernel, which rounds the same values
+    import torch
+    ibem = lib()
+    op = oracle_fmm_kernel(2, 2, 8, 1.6, 4.0)
+    hs = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(
+        2, 2, q_cheb=8, eta=1.6, kernel=1, kappa=4.0, fp32_coupling=ibem.IBEM_FP32_COUPLING_STORE))
+    ibem.ibem_assemble(hs)
+    hg = _handle(2, 2, 8, 4.0)
+    N = ibem.ibem_get_info(hs).ndof
+    eps = 2 * UBF + UBF * UBF + _eps_k32(op, 4.0)
+    x = _x(N, R, 50 + R, True)
+    ys = _apply(hs, x, 1)
+    ratio, err = _check(ys, op, x, eps)
+    assert ratio <= 1.0 and err > 1e-6, (ratio, err)
+    yg = _apply(hg, x, 1)
+    assert float(np.max(np.abs(ys - yg)) / np.max(np.abs(yg))) < 1e-5
+    ibem.ibem_destroy(hs)
+    ibem.ibem_destroy(hg)

@@ -188,3 +188,40 @@ def test_corrupt_geometry_rejected_on_the_host(ibem):
         with pytest.raises(ibem.IbemError) as ei:
             tree(good, **kw)
         assert ei.value.status == "IBEM_ERR_ARG" and text in str(ei.value)
+
+
+@pytest.mark.parametrize("shape,p,m,base,grading", [("sphere", 2, 3, 4, 3), ("fichera", 1, 2, 3, 5),
+                                                     ("perturbed", 1, 3, 6, 2)])
+def test_graded_orders_equal_oracle(ibem, shape, p, m, base, grading):
+    # Gauss order of every near pair (Sec. 4 item 4, graded reading) equals the
+    # oracle's pair_order exactly, in the order of the block tree's near list
+    from oracle import galerkin, geometry, tree
+    import shapes
+    if shape == "sphere":
+        lib_p, ora_p = ibem.sphere_patches(), geometry.unit_sphere()
+    elif shape == "perturbed":
+        lib_p, ora_p = ibem.sphere_patches(perturbed=True), geometry.perturbed_sphere()
+    else:
+        specs = shapes.fichera()
+        lib_p, ora_p = ibem.nurbs_patches(specs), [geometry.NurbsPatch(*s) for s in specs]
+    prm = ibem.make_params(p, m, q_cheb=4, eta=1.6, gauss_regular=base, gauss_singular=5, gauss_grading=grading)
+    near, _ = ibem.ibem_block_tree(lib_p, prm)
+    orders = ibem.ibem_near_orders(lib_p, prm)
+    assert len(orders) == len(near)
+    disc = galerkin.Discretisation(ora_p, p, m, galerkin.LaplaceKernel(), n_regular=base, n_singular=5,
+                                   grading=grading)
+    got = {}
+    for row, o in zip(near.tolist(), orders.tolist()):
+        s = (row[0], m, row[1], row[2])
+        t = (row[3], m, row[4], row[5])
+        eA, eB = tree.element_index(s, m), tree.element_index(t, m)
+        assert o == disc.pair_order(eA, eB), (row, o, disc.pair_order(eA, eB))
+        got[o] = got.get(o, 0) + 1
+    # the grading is exercised: more than one order among the non-touching pairs
+    assert len([k for k in got if k != 5]) >= 2, got
+    # grading 0 gives the base order to every non-touching pair
+    prm0 = ibem.make_params(p, m, q_cheb=4, eta=1.6, gauss_regular=base, gauss_singular=5)
+    o0 = ibem.ibem_near_orders(lib_p, prm0)
+    assert set(o0[near[:, 6] >= 3].tolist()) == {base}
+    with pytest.raises(ibem.IbemError):
+        ibem.ibem_near_orders(lib_p, ibem.make_params(p, m, gauss_grading=17))
