@@ -20,13 +20,24 @@ is admissible for the evaluation point (a reading: the point is a ball of radius
 0 in the admissibility test) and the Gauss rule of ``solve.potential`` on the
 remaining elements.
 
+The right-hand side of a field of point sources (Sec. 3.2 with g = sum_j c_j
+u*(., y_j)) takes the same walk per source: on an admissible cluster the
+integrand k(x^) u*(F(x^), y_j) is interpolated, so the cluster contributes its
+moments mu_tau times the values at its nodes; the other elements take the Gauss
+rule of ``Discretisation.rhs``.  It is the transpose of the interpolated
+potential (u* is symmetric).
+
 Pinned by: with a kernel that is a polynomial of degree < q in each parameter
 variable the far field is exact, so the FMM operator equals the dense one to
 rounding; with the true kernel the error against the dense matrix falls as q
 grows.  Potential: a point kernel polynomial of degree < q in the parameters
 gives the direct quadrature to rounding with both branches taken; with nothing
 admissible it is the direct potential; with the true kernel its error against
-the direct potential falls as q grows (tests/test_oracle_fmm.py).
+the direct potential falls as q grows (tests/test_oracle_fmm.py).  Point-source
+right-hand side: adjointness with the interpolated potential (Laplace and
+Helmholtz, no conjugation), the direct right-hand side when nothing is
+admissible, exactness for a parameter-polynomial point kernel, error against
+the direct right-hand side falling with q (tests/test_oracle_rhs_sources.py).
 """
 import math
 from collections import defaultdict
@@ -218,6 +229,57 @@ class FMMOperator:
                     stack.extend(children(cl))
             self.potential_counts.append((nfar, nnear))
         return u
+
+    def rhs_sources(self, sources, charges, point_kernel=None):
+        """Right-hand side b_i = int_Gamma g b_i (Sec. 3.2) of the field of point
+        sources, g(x) = sum_j charges[j] u*(x, y_j), with the interpolation of
+        Sec. 4.2 on every cluster that is admissible for a source (the walk of
+        ``potential`` with the source in the place of the point):
+            int_tau u*(F(x^), y) k(x^) b_i(x^) dx^
+              ~ sum_a u*(F(z_a^tau), y) k(z_a^tau) mu_tau[i, a],
+        mu_tau[i, a] = int_tau L_a^tau b_i (``moments_1d`` in each direction).
+        A non-admissible element takes the n x n Gauss rule of
+        ``Discretisation.rhs``.  ``point_kernel`` as in ``potential``.
+        charges: (nsrc,) or (nsrc, R); returns (N, R)."""
+        from .galerkin import fundamental_solution
+        from .tree import children, element_index
+        me = self.mesh
+        Q = np.asarray(charges).reshape(len(sources), -1)
+        if point_kernel is None:
+            kern = self.disc.kernel
+
+            def point_kernel(X, F, k, uv, patch):
+                return fundamental_solution(kern, X[:, None, :], F[None, :, :]) * k[None, :]
+        dt = np.result_type(Q, np.complex128 if self.disc.kernel.is_complex else np.float64)
+        b = np.zeros((me.n_dofs, Q.shape[1]), dtype=dt)
+        ghat = {}                                   # cluster -> (q^2, R) values k(z_a) g_far(F(z_a))
+        self.rhs_counts = []
+        for j, y in enumerate(np.asarray(sources, dtype=np.float64)):
+            nfar = nnear = 0
+            stack = [(patch, 0, 0, 0) for patch in range(len(me.patches))]
+            while stack:
+                cl = stack.pop()
+                if self.point_admissible(y, cl):
+                    uv, F, k, patch = self.interpolation_geometry(cl)
+                    g = point_kernel(y[None, :], F, k, uv, patch)[0]
+                    ghat[cl] = ghat.get(cl, 0) + np.outer(g, Q[j])
+                    nfar += 1
+                elif cl[1] == me.m:
+                    e = element_index(cl, me.m)
+                    uvq, F, k, wq, bq, patch = self.disc._product_points(e, "regular")
+                    g = point_kernel(y[None, :], F, k, uvq, patch)[0]
+                    b[me.local_dofs(e)] += bq.T @ np.outer(wq * g, Q[j])
+                    nnear += 1
+                else:
+                    stack.extend(children(cl))
+            self.rhs_counts.append((nfar, nnear))
+        n1 = me.n1
+        for (patch, level, ix, iy), G in ghat.items():
+            mu_u = self.moments_1d(level, ix)
+            mu_v = self.moments_1d(level, iy)
+            b[patch * n1 * n1:(patch + 1) * n1 * n1] += np.einsum(
+                "vb,uc,bcr->vur", mu_v, mu_u, G.reshape(self.q, self.q, -1)).reshape(n1 * n1, -1)
+        return b
 
     def rows(self, rows, x):
         """Selected rows of the FMM operator applied to x (exact per row).  The
