@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--m", type=int, default=None, help="refinement level override (profiling cases)")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve")
+    ap.add_argument("--no-store", action="store_true", help="skip the stored-BF16 coupling section")
+    ap.add_argument("--fp32-store", action="store_true", help="with --fp32-only: time the stored-BF16 coupling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-laplace", action="store_true", help="skip the Laplace level-5 section")
     ap.add_argument("--no-potential", action="store_true")
@@ -913,6 +915,8 @@ def ours(args, rank, world, local_rank):
                 ibem.ibem_matvec(h, b, out, R, precision)
 
     if args.fp32_only:
+        if args.fp32_store:
+            ibem.ibem_set_fp32_coupling(h, ibem.IBEM_FP32_COUPLING_STORE)
         run(max(1, args.warmup), 1, y32)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -980,6 +984,47 @@ def ours(args, rank, world, local_rank):
             "tensor": {"kernel": "mr_coupling_tc_kernel", "achieved_tflops": flops_tc / (c32 * 1e-3) / 1e12,
                        "peak_tflops": tpk, "frac": flops_tc / (c32 * 1e-3) / 1e12 / tpk,
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (%s)" % tsrc}}
+
+    # ---- the same operator with the coupling stored in BF16 at assembly ----
+    fp32_stored = None
+    if not args.no_store:
+        t0 = time.perf_counter()
+        st_status = ibem.ibem_set_fp32_coupling_status(h, ibem.IBEM_FP32_COUPLING_STORE)
+        t_store = time.perf_counter() - t0
+        fp32_stored = {"status": ibem.ibem_status_string(st_status), "store_s": t_store}
+        if st_status == 0:
+            y32s = torch.empty_like(b)
+            run(args.warmup, 1, y32s)
+            barrier()
+            ibem.ibem_profile_enable(h, True)
+            ev0.record(stream)
+            run(args.steps, 1, y32s)
+            ev1.record(stream)
+            barrier()
+            ms32s = ev0.elapsed_time(ev1) / args.steps
+            p32s = ibem.ibem_profile_read(h)
+            ibem.ibem_profile_enable(h, False)
+            c32s = p32s["ms"]["coupling"] / args.steps
+            kbytes = info.n_far * 128 * 64 * 2                        # [Kr; Ki] BF16 per far block
+            mbytes = info.n_clusters * 2 * R * 64 * 2                 # BF16 moments of every cluster, once
+            xbytes = info.n_far * 2 * R * 64 * 2                      # the same, requested once per far block
+            hbm, _, hsrc = _peaks()
+            fp32_stored.update({
+                "value": world * N * R / (ms32s * 1e-3), "ms_per_step": ms32s, "coupling_ms": c32s,
+                "rel_err_vs_fp64_all_64": float((y32s - y).abs().max() / y.abs().max()),
+                "max_diff_vs_generated": float((y32s - y32).abs().max() / y32.abs().max()),
+                "stored_gb": kbytes / 1e9,
+                "tensor": {"kernel": "mr_coupling_stored_kernel",
+                           "achieved_tflops": flops_tc / (c32s * 1e-3) / 1e12, "peak_tflops": tpk,
+                           "frac": flops_tc / (c32s * 1e-3) / 1e12 / tpk,
+                           "peak_source": "MEASURED_PEAKS.json bf16_tflops (%s)" % tsrc},
+                "hbm": {"bytes_per_launch": kbytes + mbytes, "moment_bytes_requested": xbytes,
+                        "achieved_gbs": (kbytes + mbytes) / (c32s * 1e-3) / 1e9, "peak_gbs": hbm,
+                        "frac": (kbytes + mbytes) / (c32s * 1e-3) / 1e9 / hbm,
+                        "note": "algorithmic HBM bytes = the stored blocks and every cluster's BF16 moments, "
+                                "each read once; the moments are requested once per far block and served "
+                                "from L2 where neighbouring target rows share source clusters"}})
+            del y32s
 
     # ---- both operators against the oracle on sampled rows at full size ----
     accuracy = None
@@ -1058,6 +1103,7 @@ def ours(args, rank, world, local_rank):
             "phase_ms": phase_ms, "create_s": t_create, "assemble_s": t_assemble,
             "roofline": roof,
             "fp32_tensor_core": fp32,
+            "fp32_tensor_core_stored": fp32_stored,
             "accuracy_vs_oracle_rows": accuracy,
             "solve": solve,
             "potential": pot,

@@ -126,7 +126,7 @@ typedef struct {
                             fits in half of the free device memory (Helmholtz,
                             q = 8: 16 KB per far block) and streams it */
     int gauss_grading;   /* Gauss order raised towards the singularity (Sec. 4
-                            item 4: logarithmically, up to 40), 0..16; 0 = off.
+                            item 4: logarithmically, up to 40), 0..39; 0 = off.
                             A non-touching near pair whose bounding balls give
                             rho = dist / max(diam) takes
                               n = min(40, gauss_regular + gauss_grading * k),
@@ -390,6 +390,41 @@ ibem_status ibem_batch_info(const ibem_batch* b, int* launches_per_apply, int* c
 ibem_status ibem_batch_solve(ibem_batch* b, const double* b_dev, double* x_dev, double rtol, int maxit, int precond,
                              ibem_solve_info* info);
 ibem_status ibem_batch_destroy(ibem_batch* b);
+
+/* Right-hand side of the field of point sources, g(x) = sum_j c_j u*(x, y_j)
+ * (u* of the handle's kernel), as b = T g* with g*_i = int_Gamma g b*_i (Sec.
+ * 3.2), the far field of every source interpolated (Sec. 4.2): per source the
+ * cluster tree is walked as for a potential point (ibem_potential_fmm); on a
+ * cluster sigma with eta * diam(sigma) < max(0, |y_j - c_sigma| - r_sigma) the
+ * integrand k u*(F(.), y_j) is replaced by its q x q Chebyshev interpolant, so
+ * b*_i gets sum_a c_j k(z_a) u*(F(z_a), y_j) int_sigma L_a b*_i; an element
+ * that is never admissible takes the n x n Gauss rule of ibem_rhs.  The node
+ * values of all clusters pass through the operator's downward transfers.  It
+ * is the transpose of ibem_potential_fmm (u* is symmetric).
+ * src_dev [nsrc][3] (sources, not on Gauss points of near elements),
+ * charges_dev [nrhs][nsrc] (complex for Helmholtz), b_dev [nrhs][ndof]
+ * (complex for Helmholtz).  Needs a compressed handle (q_cheb > 0;
+ * IBEM_ERR_ARG otherwise), not the assembled operator.  One host
+ * synchronisation: the per-source lists are copied to the host and turned into
+ * lists per cluster and per element (sources ascending: repeated calls give
+ * identical results).  Temporary device memory (released on the stream): the
+ * lists, the node values (8 q^2 bytes per cluster and real vector; complex
+ * counts twice) and the superspace vectors (8 ndof_super bytes per real
+ * vector).  n_far_terms, n_near_terms (may be null): total (source, cluster)
+ * and (source, element) terms.  At most 2^31 - 1 sources and 32,767 charge
+ * vectors (IBEM_ERR_ARG).  nsrc = 0 gives b = 0. */
+ibem_status ibem_rhs_sources(ibem_handle* h, const double* src_dev, const double* charges_dev, int nrhs,
+                             int64_t nsrc, double* b_dev, int64_t* n_far_terms, int64_t* n_near_terms);
+
+/* Switch the coupling of the FP32 tensor-core operator of an assembled handle
+ * (see ibem_params.fp32_coupling): IBEM_FP32_COUPLING_STORE generates the BF16
+ * blocks [Kr; Ki] of every far block once (16 KB each at q = 8) and streams
+ * them in every later application; IBEM_FP32_COUPLING_GENERATE releases them.
+ * STORE needs a Helmholtz handle with q_cheb = 8 (IBEM_ERR_ARG otherwise) and
+ * returns IBEM_ERR_OOM, keeping the generating path, when the blocks exceed
+ * half of the free device memory.  Synchronises; not concurrently with an
+ * application on the handle.  IBEM_ERR_STATE before ibem_assemble. */
+ibem_status ibem_set_fp32_coupling(ibem_handle* h, int mode);
 
 /* Host-only: build the block cluster tree without a GPU and return its lists.
  * Call once with null arrays to get the counts.  near: [n_near][8] int32 =

@@ -463,6 +463,26 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     return IBEM_OK;
 }
 
+// BF16 coupling of the tensor-core path (16 KB per far block), generated on
+// the device, if it fits in half of the free memory (IBEM_ERR_OOM otherwise).
+static ibem_status store_bf16_coupling(ibem_handle* h) {
+    const size_t kb = (size_t)h->P.n_far * 128 * 64 * 2;
+    size_t free_b = 0, total_b = 0;
+    cudaError_t e;
+    if ((e = cudaMemGetInfo(&free_b, &total_b))) return cuda_fail(h, e, "cudaMemGetInfo");
+    if (kb > free_b / 2) return fail(h, IBEM_ERR_OOM, "stored BF16 coupling exceeds half of the free device memory");
+    if ((e = cudaMalloc(&h->d_Kbf, kb))) {
+        h->d_Kbf = nullptr;
+        return cuda_fail(h, e, "alloc BF16 coupling");
+    }
+    if ((e = mr_store_coupling(h)) || (e = cudaStreamSynchronize(h->stream))) {
+        cudaFree(h->d_Kbf);
+        h->d_Kbf = nullptr;
+        return cuda_fail(h, e, "BF16 coupling");
+    }
+    return IBEM_OK;
+}
+
 ibem_status ibem_assemble(ibem_handle* h) {
     if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
     Plan& P = h->P;
@@ -510,15 +530,13 @@ ibem_status ibem_assemble(ibem_handle* h) {
     if (!h->helm && h->d_Kdf && !h->up_rows.empty())
         if ((e = tune_coupling_df(h))) return cuda_fail(h, e, "coupling autotune");
     if (P.prm.fp32_coupling == IBEM_FP32_COUPLING_STORE && mr_store_possible(h) && !h->d_Kbf) {
-        // BF16 coupling of the tensor-core path (16 KB per far block) if it fits in
-        // half of the free memory; otherwise the path keeps generating it
-        const size_t kb = (size_t)P.n_far * 128 * 64 * 2;
-        size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
-        if (kb <= free_b / 2) {
-            if ((e = cudaMalloc(&h->d_Kbf, kb))) return cuda_fail(h, e, "alloc BF16 coupling");
-            if ((e = mr_store_coupling(h))) return cuda_fail(h, e, "BF16 coupling");
-            if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "BF16 coupling sync");
+        // if it does not fit, the path keeps generating the coupling
+        ibem_status s = store_bf16_coupling(h);
+        if (s == IBEM_ERR_OOM) {
+            cudaGetLastError();   // a refused allocation is not an error of the assembly
+            h->err.clear();
+        } else if (s != IBEM_OK) {
+            return s;
         }
     }
     if (P.prm.fp64_coupling == IBEM_COUPLING_FP32_ONLY && h->d_near) {
@@ -528,6 +546,32 @@ ibem_status ibem_assemble(ibem_handle* h) {
         h->d_near = nullptr;
     }
     h->assembled = true;
+    return IBEM_OK;
+}
+
+ibem_status ibem_set_fp32_coupling(ibem_handle* h, int mode) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (mode != IBEM_FP32_COUPLING_GENERATE && mode != IBEM_FP32_COUPLING_STORE)
+        return fail(h, IBEM_ERR_ARG, "mode must be IBEM_FP32_COUPLING_GENERATE or IBEM_FP32_COUPLING_STORE");
+    if (!h->assembled) return fail(h, IBEM_ERR_STATE, "ibem_assemble first");
+    cudaError_t e;
+    if ((e = cudaSetDevice(h->device))) return cuda_fail(h, e, "cudaSetDevice");
+    if (mode == IBEM_FP32_COUPLING_GENERATE) {
+        if (h->d_Kbf) {
+            if ((e = cudaStreamSynchronize(h->stream))) return cuda_fail(h, e, "sync");
+            cudaFree(h->d_Kbf);
+            h->d_Kbf = nullptr;
+        }
+        h->P.prm.fp32_coupling = mode;
+        return IBEM_OK;
+    }
+    if (!mr_store_possible(h))
+        return fail(h, IBEM_ERR_ARG, "stored coupling needs a Helmholtz handle with q_cheb = 8 and far blocks");
+    if (!h->d_Kbf) {
+        ibem_status s = store_bf16_coupling(h);
+        if (s != IBEM_OK) return s;
+    }
+    h->P.prm.fp32_coupling = mode;
     return IBEM_OK;
 }
 
@@ -741,6 +785,29 @@ ibem_status ibem_potential_fmm(ibem_handle* h, const double* w_dev, int nrhs, co
     if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
     if ((e = launch_potential_fmm(h, w_dev, nrhs, pts_dev, npts, u_dev, n_far_terms, n_near_terms)))
         return cuda_fail(h, e, "potential_fmm");
+    return IBEM_OK;
+}
+
+ibem_status ibem_rhs_sources(ibem_handle* h, const double* src_dev, const double* charges_dev, int nrhs,
+                             int64_t nsrc, double* b_dev, int64_t* n_far_terms, int64_t* n_near_terms) {
+    if (!h) return fail(nullptr, IBEM_ERR_ARG, "null handle");
+    if (nrhs < 0 || nsrc < 0 || (nrhs > 0 && !b_dev) || (nrhs > 0 && nsrc > 0 && (!src_dev || !charges_dev)))
+        return fail(h, IBEM_ERR_ARG, "bad right-hand-side arguments");
+    if (h->P.q == 0) return fail(h, IBEM_ERR_ARG, "ibem_rhs_sources needs a compressed handle (q_cheb > 0)");
+    if (nsrc > 2147483647LL || nrhs > 32767)   // grid.x = sources; grid.y of the downward pass = 2 nrhs
+        return fail(h, IBEM_ERR_ARG, "ibem_rhs_sources takes at most 2^31 - 1 sources and 32,767 charge vectors");
+    if (n_far_terms) *n_far_terms = 0;
+    if (n_near_terms) *n_near_terms = 0;
+    if (nrhs == 0) return IBEM_OK;
+    cudaError_t e;
+    if ((e = set_device(h))) return cuda_fail(h, e, "cudaSetDevice");
+    if (nsrc == 0) {
+        const size_t n = (size_t)nrhs * h->P.N * (h->helm ? 2 : 1);
+        if ((e = cudaMemsetAsync(b_dev, 0, n * sizeof(double), h->stream))) return cuda_fail(h, e, "memset");
+        return IBEM_OK;
+    }
+    if ((e = launch_rhs_sources(h, src_dev, charges_dev, nrhs, nsrc, b_dev, n_far_terms, n_near_terms)))
+        return cuda_fail(h, e, "rhs_sources");
     return IBEM_OK;
 }
 

@@ -432,6 +432,8 @@ __global__ void l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int 
                            int64_t C, double* __restrict__ yh);
 __global__ void leaf_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
                                  const double* __restrict__ yh, int64_t leaf_off, int64_t C, double* __restrict__ ys);
+__global__ void l2l_sep_kernel(int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                               int64_t C, double* __restrict__ yh);
 __global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n);
 __global__ void rhs_super_kernel(int R, int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
                                  const double* __restrict__ phi, const double* __restrict__ g, int64_t nq,
@@ -445,6 +447,7 @@ cudaError_t helm_launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b
 cudaError_t helm_launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                                   double* u, double* wsplit);
 __global__ void helm_split_vec_kernel(int R, int64_t n, const double* __restrict__ in, double* __restrict__ out);
+__global__ void helm_join_vec_kernel(int R, int64_t n, const double* __restrict__ in, double* __restrict__ out);
 // near-field assembly (kernels_setup.cu): the streaming form of the regular and
 // subdivided pairs, used where the shared-matrix form needs more than
 // IBEM_MAX_SMEM_BYTES (near_shared_bytes) of shared memory
@@ -455,6 +458,8 @@ size_t near_shared_bytes(int Q, int nb, bool cplx, bool subdiv);
 // potential_fmm.cu
 cudaError_t launch_potential_fmm(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                                  double* u, int64_t* n_far_terms, int64_t* n_near_terms);
+cudaError_t launch_rhs_sources(ibem_handle* h, const double* src, const double* charges, int nrhs, int64_t nsrc,
+                               double* b, int64_t* n_far_terms, int64_t* n_near_terms);
 // kernels_*.cu entry points (launch on h->stream; return cudaError_t)
 cudaError_t launch_geometry_tables(ibem_handle* h);
 cudaError_t launch_near_assembly(ibem_handle* h);

@@ -426,4 +426,302 @@ cudaError_t launch_potential_fmm(ibem_handle* h, const double* w, int nrhs, cons
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Right-hand side of a field of point sources with the interpolated far field.
+//
+// For g(x) = sum_j c_j u*(x, y_j) the Galerkin right-hand side (Sec. 3.2)
+// b*_i = int_Gamma g b*_i is the transpose of the interpolated potential (u* is
+// symmetric): per source the tree is walked as for a potential point; on a
+// cluster sigma admissible for y_j the integrand k(x^) u*(F(x^), y_j) is
+// replaced by its interpolant (Sec. 4.2), so the source adds c_j k(z_a)
+// u*(F(z_a), y_j) to the value at node a of sigma; elements that are never
+// admissible take the regular Gauss rule.  The node values of every cluster
+// then run through the operator's own downward pass (separable L2L, leaf
+// back-projection with the moments int L_a b*_i) and the restriction T.
+// The per-source lists come from pf_lists_kernel; the host transposes them
+// into lists per cluster and per element with the sources ascending, so every
+// sum runs in a fixed order and repeated calls give identical results.
+namespace {
+
+constexpr int RS_T = 256;    // threads per CTA of the right-hand-side kernels
+constexpr int RS_RC = 8;     // charge vectors per CTA
+
+// Far values: one CTA per (cluster with sources admissible for it, chunk of
+// RS_RC charge vectors).  Thread t takes node a = t % q2 and every np-th
+// source of the cluster's list (part t / q2, np = RS_T / q2 parts); the parts
+// are summed in order.  Output in the split real layout [R2][C][q2].
+template <bool CPLX>
+__global__ void __launch_bounds__(RS_T) rs_far_kernel(
+    const int32_t* __restrict__ clusters, const int64_t* __restrict__ cptr, const int32_t* __restrict__ csrc,
+    const double* __restrict__ src, const double* __restrict__ charges, int R, int64_t nsrc, int q2, int64_t C,
+    const double* __restrict__ igeo, double kappa, double* __restrict__ yh) {
+    constexpr int CW = CPLX ? 2 : 1;
+    constexpr int NV = RS_RC * CW;
+    __shared__ double part[NV * RS_T];
+    const int u = blockIdx.x;
+    const int64_t c = clusters[u];
+    const int r0 = blockIdx.y * RS_RC;
+    const int nc = R - r0 < RS_RC ? R - r0 : RS_RC;
+    const int np = RS_T / q2;
+    const int t = threadIdx.x, a = t % q2, pp = t / q2;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    if (pp < np) {
+        const double* z = igeo + 4 * (c * q2 + a);
+        const double z0 = z[0], z1 = z[1], z2 = z[2];
+        for (int64_t k = cptr[u] + pp; k < cptr[u + 1]; k += np) {
+            const int64_t j = csrc[k];
+            const double d0 = z0 - src[3 * j], d1 = z1 - src[3 * j + 1], d2 = z2 - src[3 * j + 2];
+            double gr, gi;
+            pf_kernel_value<CPLX>(sqrt(d0 * d0 + d1 * d1 + d2 * d2), kappa, &gr, &gi);
+#pragma unroll
+            for (int rr = 0; rr < RS_RC; ++rr) {
+                if (rr < nc) {
+                    if constexpr (CPLX) {
+                        const double* qc = charges + ((int64_t)(r0 + rr) * nsrc + j) * 2;
+                        const double qr = qc[0], qi = qc[1];
+                        acc[2 * rr] = fma(gr, qr, fma(-gi, qi, acc[2 * rr]));
+                        acc[2 * rr + 1] = fma(gr, qi, fma(gi, qr, acc[2 * rr + 1]));
+                    } else {
+                        acc[rr] = fma(gr, charges[(int64_t)(r0 + rr) * nsrc + j], acc[rr]);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) part[v * RS_T + t] = acc[v];
+    __syncthreads();
+    if (t < q2) {
+        const double kz = igeo[4 * (c * q2 + t) + 3];
+        for (int v = 0; v < nc * CW; ++v) {
+            double sum = 0.0;
+            for (int k = 0; k < np; ++k) sum += part[v * RS_T + k * q2 + t];
+            const int rr = v / CW, comp = v % CW;
+            const int64_t vec = CPLX ? 2 * (int64_t)(r0 + rr) + comp : (int64_t)(r0 + rr);
+            yh[(vec * C + c) * q2 + t] = sum * kz;
+        }
+    }
+}
+
+// Near sums: one CTA per (element with near sources, chunk of RS_RC charge
+// vectors).  Gauss points in chunks of RS_T: each thread forms W_g g(x_g) at
+// its point from the element's sources (in list order) into shared memory,
+// then the (dof, component) entries sum phi[g][i] over the chunk in order.
+// Adds to ys [R2][E][nb] (written by the leaf back-projection before).
+template <bool CPLX>
+__global__ void __launch_bounds__(RS_T) rs_near_kernel(
+    const int32_t* __restrict__ elems, const int64_t* __restrict__ eptr, const int32_t* __restrict__ esrc,
+    const double* __restrict__ src, const double* __restrict__ charges, int R, int64_t nsrc, int QQ, int nb,
+    int64_t E, const double* __restrict__ qgeo, const double* __restrict__ phi, double kappa,
+    double* __restrict__ ys) {
+    constexpr int CW = CPLX ? 2 : 1;
+    constexpr int NV = RS_RC * CW;
+    constexpr int MAXO = (25 * NV + RS_T - 1) / RS_T;   // nb <= 25
+    __shared__ double sg[NV * RS_T];
+    const int64_t e = elems[blockIdx.x];
+    const int r0 = blockIdx.y * RS_RC;
+    const int nc = R - r0 < RS_RC ? R - r0 : RS_RC;
+    const int nout = nb * NV;
+    double out[MAXO];
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o) out[o] = 0.0;
+    for (int g0 = 0; g0 < QQ; g0 += RS_T) {
+        const int g = g0 + threadIdx.x;
+        double val[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) val[v] = 0.0;
+        if (g < QQ) {
+            const double* x = qgeo + 4 * (e * QQ + g);
+            const double x0 = x[0], x1 = x[1], x2 = x[2], w = x[3];
+            for (int64_t k = eptr[blockIdx.x]; k < eptr[blockIdx.x + 1]; ++k) {
+                const int64_t j = esrc[k];
+                const double d0 = x0 - src[3 * j], d1 = x1 - src[3 * j + 1], d2 = x2 - src[3 * j + 2];
+                double gr, gi;
+                pf_kernel_value<CPLX>(sqrt(d0 * d0 + d1 * d1 + d2 * d2), kappa, &gr, &gi);
+                gr *= w;
+                gi *= w;
+#pragma unroll
+                for (int rr = 0; rr < RS_RC; ++rr) {
+                    if (rr < nc) {
+                        if constexpr (CPLX) {
+                            const double* qc = charges + ((int64_t)(r0 + rr) * nsrc + j) * 2;
+                            const double qr = qc[0], qi = qc[1];
+                            val[2 * rr] = fma(gr, qr, fma(-gi, qi, val[2 * rr]));
+                            val[2 * rr + 1] = fma(gr, qi, fma(gi, qr, val[2 * rr + 1]));
+                        } else {
+                            val[rr] = fma(gr, charges[(int64_t)(r0 + rr) * nsrc + j], val[rr]);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sg[v * RS_T + threadIdx.x] = val[v];
+        __syncthreads();
+        const int ng = QQ - g0 < RS_T ? QQ - g0 : RS_T;
+#pragma unroll
+        for (int o = 0; o < MAXO; ++o) {
+            const int idx = threadIdx.x + o * RS_T;
+            if (idx < nout) {
+                const int i = idx / NV, v = idx % NV;
+                double sum = 0.0;
+                for (int gg = 0; gg < ng; ++gg) sum = fma(phi[(int64_t)(g0 + gg) * nb + i], sg[v * RS_T + gg], sum);
+                out[o] += sum;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o) {
+        const int idx = threadIdx.x + o * RS_T;
+        if (idx < nout) {
+            const int i = idx / NV, v = idx % NV, rr = v / CW, comp = v % CW;
+            if (rr < nc) {
+                const int64_t vec = CPLX ? 2 * (int64_t)(r0 + rr) + comp : (int64_t)(r0 + rr);
+                ys[(vec * E + e) * nb + i] += out[o];
+            }
+        }
+    }
+}
+
+// Lists per target (cluster or element) from the lists per source: counting
+// sort over the sources in order, so each target's sources are ascending.
+void transpose_lists(int64_t nsrc, const std::vector<int64_t>& off, const std::vector<int32_t>& lists,
+                     int64_t list0, int64_t ntargets, std::vector<int32_t>& targets, std::vector<int64_t>& tptr,
+                     std::vector<int32_t>& tsrc) {
+    std::vector<int64_t> cnt((size_t)ntargets, 0);
+    const int64_t n = off[nsrc] - off[0];
+    for (int64_t k = 0; k < n; ++k) cnt[lists[list0 + k]]++;
+    std::vector<int64_t> pos((size_t)ntargets, -1);
+    targets.clear();
+    tptr.assign(1, 0);
+    for (int64_t t = 0; t < ntargets; ++t)
+        if (cnt[t] > 0) {
+            pos[t] = tptr.back();
+            targets.push_back((int32_t)t);
+            tptr.push_back(tptr.back() + cnt[t]);
+        }
+    tsrc.assign((size_t)n, 0);
+    for (int64_t j = 0; j < nsrc; ++j)
+        for (int64_t k = off[j]; k < off[j + 1]; ++k) tsrc[pos[lists[list0 + k - off[0]]]++] = (int32_t)j;
+}
+
+}  // namespace
+
+cudaError_t launch_rhs_sources(ibem_handle* h, const double* src, const double* charges, int nrhs, int64_t nsrc,
+                               double* b, int64_t* n_far_terms, int64_t* n_near_terms) {
+    Plan& P = h->P;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    const int T = 256;
+    const int R2 = h->helm ? 2 * nrhs : nrhs;
+    StreamBuffers buf(st);
+    // (1) lists per source (the potential's walk)
+    LevelOffsets lo{};
+    for (int l = 0; l <= P.m + 1 && l < 12; ++l) lo.off[l] = P.level_off[l];
+    int32_t* d_cnt;
+    uint8_t* d_used;
+    if ((e = buf.alloc(&d_cnt, (size_t)2 * nsrc)) || (e = buf.alloc(&d_used, (size_t)P.C)) ||
+        (e = cudaMemsetAsync(d_used, 0, (size_t)P.C, st)))
+        return e;
+    pf_lists_kernel<<<nblk(nsrc, 128), 128, 0, st>>>(nsrc, src, P.npatch, P.m, lo, h->d_balls, P.prm.eta, false, d_cnt,
+                                                      d_used, nullptr, nullptr, nullptr, nullptr, h->d_status);
+    h->launches++;
+    std::vector<int32_t> cnt((size_t)2 * nsrc);
+    if ((e = cudaMemcpyAsync(cnt.data(), d_cnt, cnt.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return e;
+    std::vector<int64_t> off((size_t)2 * (nsrc + 1), 0);   // far offsets, then near offsets
+    for (int64_t i = 0; i < nsrc; ++i) {
+        off[i + 1] = off[i] + cnt[2 * i];
+        off[nsrc + 1 + i + 1] = off[nsrc + 1 + i] + cnt[2 * i + 1];
+    }
+    const int64_t nfar = off[nsrc], nnear = off[2 * nsrc + 1];
+    if (n_far_terms) *n_far_terms = nfar;
+    if (n_near_terms) *n_near_terms = nnear;
+    int64_t* d_off;
+    int32_t* d_lists;
+    if ((e = buf.alloc(&d_off, off.size())) || (e = buf.alloc(&d_lists, (size_t)(nfar + nnear))) ||
+        (e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st)))
+        return e;
+    pf_lists_kernel<<<nblk(nsrc, 128), 128, 0, st>>>(nsrc, src, P.npatch, P.m, lo, h->d_balls, P.prm.eta, true, d_cnt,
+                                                      nullptr, d_off, d_off + nsrc + 1, d_lists, d_lists + nfar,
+                                                      h->d_status);
+    h->launches++;
+    std::vector<int32_t> lists((size_t)(nfar + nnear));
+    if (!lists.empty() &&
+        (e = cudaMemcpyAsync(lists.data(), d_lists, lists.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st)))
+        return e;
+    if ((e = cudaStreamSynchronize(st))) return e;
+    // (2) lists per cluster and per element, sources ascending
+    std::vector<int64_t> foff(off.begin(), off.begin() + nsrc + 1), noff(off.begin() + nsrc + 1, off.end());
+    std::vector<int32_t> cl, csrc, el, esrc;
+    std::vector<int64_t> cptr, eptr;
+    transpose_lists(nsrc, foff, lists, 0, P.C, cl, cptr, csrc);
+    transpose_lists(nsrc, noff, lists, nfar, P.E, el, eptr, esrc);
+    int32_t *d_cl = nullptr, *d_csrc = nullptr, *d_el = nullptr, *d_esrc = nullptr;
+    int64_t *d_cptr = nullptr, *d_eptr = nullptr;
+    auto up32 = [&](int32_t** d, const std::vector<int32_t>& v) -> cudaError_t {
+        cudaError_t r = buf.alloc(d, v.size());
+        if (r || v.empty()) return r;
+        return cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    };
+    auto up64 = [&](int64_t** d, const std::vector<int64_t>& v) -> cudaError_t {
+        cudaError_t r = buf.alloc(d, v.size());
+        if (r || v.empty()) return r;
+        return cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    };
+    if ((e = up32(&d_cl, cl)) || (e = up64(&d_cptr, cptr)) || (e = up32(&d_csrc, csrc)) || (e = up32(&d_el, el)) ||
+        (e = up64(&d_eptr, eptr)) || (e = up32(&d_esrc, esrc)))
+        return e;
+    // (3) node values of the clusters, downward pass, near sums, restriction
+    double *d_yh, *d_ys, *d_bs = nullptr;
+    if ((e = buf.alloc(&d_yh, (size_t)R2 * P.C * P.q2)) || (e = buf.alloc(&d_ys, (size_t)R2 * P.Nstar)) ||
+        (e = cudaMemsetAsync(d_yh, 0, (size_t)R2 * P.C * P.q2 * sizeof(double), st)))
+        return e;
+    if (h->helm && (e = buf.alloc(&d_bs, (size_t)R2 * P.N))) return e;
+    const unsigned nchunk = (unsigned)((nrhs + RS_RC - 1) / RS_RC);
+    if (!cl.empty()) {
+        dim3 grid((unsigned)cl.size(), nchunk);
+        if (h->helm)
+            rs_far_kernel<true><<<grid, RS_T, 0, st>>>(d_cl, d_cptr, d_csrc, src, charges, nrhs, nsrc, P.q2, P.C,
+                                                       h->d_igeo, P.prm.kappa, d_yh);
+        else
+            rs_far_kernel<false><<<grid, RS_T, 0, st>>>(d_cl, d_cptr, d_csrc, src, charges, nrhs, nsrc, P.q2, P.C,
+                                                        h->d_igeo, 0.0, d_yh);
+        h->launches++;
+    }
+    for (int L = 0; L < P.m; ++L) {
+        const int64_t nL = P.level_off[L + 1] - P.level_off[L];
+        l2l_sep_kernel<<<dim3((unsigned)nL, (unsigned)R2), 64, 0, st>>>(nL, P.level_off[L], P.level_off[L + 1], P.q,
+                                                                       h->d_S, P.C, d_yh);
+        h->launches++;
+    }
+    leaf_back_kernel<<<nblk((int64_t)R2 * P.E * P.nb, T), T, 0, st>>>(R2, P.E, P.pp, P.q, h->d_M, d_yh,
+                                                                       P.level_off[P.m], P.C, d_ys);
+    h->launches++;
+    if (!el.empty()) {
+        dim3 grid((unsigned)el.size(), nchunk);
+        const int QQ = P.Q * P.Q;
+        if (h->helm)
+            rs_near_kernel<true><<<grid, RS_T, 0, st>>>(d_el, d_eptr, d_esrc, src, charges, nrhs, nsrc, QQ, P.nb, P.E,
+                                                        h->d_qgeo, h->d_phi, P.prm.kappa, d_ys);
+        else
+            rs_near_kernel<false><<<grid, RS_T, 0, st>>>(d_el, d_eptr, d_esrc, src, charges, nrhs, nsrc, QQ, P.nb,
+                                                         P.E, h->d_qgeo, h->d_phi, 0.0, d_ys);
+        h->launches++;
+    }
+    restrict_kernel<<<nblk((int64_t)R2 * P.N, T), T, 0, st>>>(R2, P.N, P.p, P.ne1, h->d_ext, d_ys, P.E,
+                                                              h->helm ? d_bs : b);
+    h->launches++;
+    if (h->helm) {
+        helm_join_vec_kernel<<<nblk((int64_t)nrhs * P.N, T), T, 0, st>>>(nrhs, P.N, d_bs, b);
+        h->launches++;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace ibem

@@ -247,7 +247,7 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
         return "admissibility must be IBEM_ADMISSIBLE_ETA_DIAM or IBEM_ADMISSIBLE_ETA_DIST";
     if (q.gauss_regular < 1 || q.gauss_regular > IBEM_MAX_GAUSS) return "gauss_regular must be in 1..40";
     if (q.gauss_singular < 1 || q.gauss_singular > 12) return "gauss_singular must be in 1..12";
-    if (q.gauss_grading < 0 || q.gauss_grading > 16) return "gauss_grading must be in 0..16";
+    if (q.gauss_grading < 0 || q.gauss_grading > 39) return "gauss_grading must be in 0..39";
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
         q.fp64_coupling != IBEM_COUPLING_NONE && q.fp64_coupling != IBEM_COUPLING_GENERATE &&
         q.fp64_coupling != IBEM_COUPLING_FP32_ONLY)

@@ -36,7 +36,8 @@ EXPORTED = ("ibem_create", "ibem_destroy", "ibem_get_info", "ibem_assemble", "ib
             "ibem_cnn_create", "ibem_cnn_destroy", "ibem_cnn_params", "ibem_cnn_forward", "ibem_cnn_gradients",
             "ibem_cnn_train_step", "ibem_cnn_train", "ibem_cnn_launches", "ibem_set_learned_preconditioner",
             "ibem_learned_apply", "ibem_solver_pairs", "ibem_solver_residuals", "ibem_cnn_operator_gradients",
-            "ibem_cnn_train_operator", "ibem_cnn_device_status", "ibem_cnn_set_coarsening", "ibem_near_orders")
+            "ibem_cnn_train_operator", "ibem_cnn_device_status", "ibem_cnn_set_coarsening", "ibem_near_orders",
+            "ibem_set_fp32_coupling", "ibem_rhs_sources")
 
 
 class IbemError(RuntimeError):
@@ -101,6 +102,8 @@ def _load():
         "ibem_potential_fmm": (I32, [P, P, I32, P, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "ibem_block_tree": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
                                   ctypes.POINTER(I64), P, ctypes.POINTER(I64), P]),
+        "ibem_set_fp32_coupling": (I32, [P, I32]),
+        "ibem_rhs_sources": (I32, [P, P, P, I32, I64, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "ibem_near_orders": (I32, [ctypes.POINTER(ibem_patch), I32, ctypes.POINTER(ibem_params),
                                    ctypes.POINTER(I64), P]),
         "ibem_profile_enable": (I32, [P, I32]),
@@ -286,6 +289,15 @@ def ibem_potential_fmm(h, w, nrhs, pts, u):
     return nf.value, nn.value
 
 
+def ibem_rhs_sources(h, src, charges, nrhs, b):
+    """Right-hand side of point sources with the interpolated far field; src [nsrc][3],
+    charges [nrhs][nsrc] (complex: [..][2]); returns (far terms, near terms)."""
+    nf, nn = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_lib.ibem_rhs_sources(h, _dptr(src), _dptr(charges), nrhs, src.shape[0], _dptr(b), ctypes.byref(nf),
+                                 ctypes.byref(nn)), h)
+    return nf.value, nn.value
+
+
 def ibem_potential_noalloc(h, w, nrhs, pts, u):
     """ibem_potential without device allocation (fixed scratch inside libibem)."""
     _check(_lib.ibem_potential_noalloc(h, _dptr(w), nrhs, _dptr(pts), pts.shape[0], _dptr(u)), h)
@@ -302,6 +314,16 @@ def ibem_block_tree(patches, params):
                                 near.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf),
                                 far.ctypes.data_as(ctypes.c_void_p)))
     return near, far
+
+
+def ibem_set_fp32_coupling(h, mode):
+    _check(_lib.ibem_set_fp32_coupling(h, mode), h)
+
+
+def ibem_set_fp32_coupling_status(h, mode):
+    """As ibem_set_fp32_coupling, returning the status instead of raising (IBEM_ERR_OOM
+    keeps the generating path)."""
+    return _lib.ibem_set_fp32_coupling(h, mode)
 
 
 def ibem_near_orders(patches, params):

@@ -189,3 +189,38 @@ def test_stored_bf16_coupling_vs_oracle(R):
     assert float(np.max(np.abs(ys - yg)) / np.max(np.abs(yg))) < 1e-5
     ibem.ibem_destroy(hs)
     ibem.ibem_destroy(hg)
+
+
+def test_switching_the_fp32_coupling_after_assembly():
+    # ibem_set_fp32_coupling: STORE on a generating handle gives the stored
+    # handle's result exactly, GENERATE releases the blocks and gives the
+    # generating handle's result exactly; Laplace and unassembled handles refuse
+    import torch
+    ibem = lib()
+    hs = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(
+        2, 2, q_cheb=8, eta=1.6, kernel=1, kappa=4.0, fp32_coupling=ibem.IBEM_FP32_COUPLING_STORE))
+    ibem.ibem_assemble(hs)
+    hg = _handle(2, 2, 8, 4.0)
+    N = ibem.ibem_get_info(hs).ndof
+    x = _x(N, 24, 77, True)
+    y_store, y_gen = _apply(hs, x, 1), _apply(hg, x, 1)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ibem.ibem_set_fp32_coupling(hg, ibem.IBEM_FP32_COUPLING_STORE)
+    assert torch.cuda.mem_get_info()[0] < free0
+    assert np.array_equal(_apply(hg, x, 1), y_store)
+    ibem.ibem_set_fp32_coupling(hg, ibem.IBEM_FP32_COUPLING_GENERATE)
+    assert np.array_equal(_apply(hg, x, 1), y_gen)
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_set_fp32_coupling(hg, 7)
+    assert ei.value.status == "IBEM_ERR_ARG"
+    hl = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(1, 2, q_cheb=8, eta=1.6))
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_set_fp32_coupling(hl, ibem.IBEM_FP32_COUPLING_STORE)
+    assert ei.value.status == "IBEM_ERR_STATE"
+    ibem.ibem_assemble(hl)
+    with pytest.raises(ibem.IbemError) as ei:
+        ibem.ibem_set_fp32_coupling(hl, ibem.IBEM_FP32_COUPLING_STORE)
+    assert ei.value.status == "IBEM_ERR_ARG"
+    for h in (hs, hg, hl):
+        ibem.ibem_destroy(h)

@@ -21,7 +21,7 @@ def ibem():
 def test_exports_every_declared_symbol(ibem):
     import ctypes
     hdr = open(os.path.join(ROOT, "include", "ibem.h")).read()
-    declared = set(re.findall(r"\b(ibem_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(ibem_[a-z0-9_]+)\s*\(", hdr))
     assert declared == set(ibem.EXPORTED)
     lib = ctypes.CDLL(ibem.LIB_PATH)
     for name in declared:
@@ -224,4 +224,4 @@ def test_graded_orders_equal_oracle(ibem, shape, p, m, base, grading):
     o0 = ibem.ibem_near_orders(lib_p, prm0)
     assert set(o0[near[:, 6] >= 3].tolist()) == {base}
     with pytest.raises(ibem.IbemError):
-        ibem.ibem_near_orders(lib_p, ibem.make_params(p, m, gauss_grading=17))
+        ibem.ibem_near_orders(lib_p, ibem.make_params(p, m, gauss_grading=40))
