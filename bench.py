@@ -924,7 +924,8 @@ def ours(args, rank, world, local_rank):
         run(args.steps, 1, y32)
         ev1.record(stream)
         barrier()
-        print(json.dumps({"fp32_ms": ev0.elapsed_time(ev1) / args.steps}), flush=True)
+        print(json.dumps({"fp32_ms": ev0.elapsed_time(ev1) / args.steps,
+                          "stored_ring_depth": ibem.ibem_get_info(h).stored_ring_depth}), flush=True)
         return
     oracle_res = finish_oracle_child(*oracle) if oracle else None
 
@@ -1014,6 +1015,7 @@ def ours(args, rank, world, local_rank):
                 "rel_err_vs_fp64_all_64": float((y32s - y).abs().max() / y.abs().max()),
                 "max_diff_vs_generated": float((y32s - y32).abs().max() / y32.abs().max()),
                 "stored_gb": kbytes / 1e9,
+                "ring_depth": ibem.ibem_get_info(h).stored_ring_depth,
                 "tensor": {"kernel": "mr_coupling_stored_kernel",
                            "achieved_tflops": flops_tc / (c32s * 1e-3) / 1e12, "peak_tflops": tpk,
                            "frac": flops_tc / (c32s * 1e-3) / 1e12 / tpk,

@@ -184,6 +184,8 @@ typedef struct {
     int assembled;         /* 1 after ibem_assemble                                 */
     int max_gauss_order;   /* largest Gauss order of a non-touching near pair       */
     int64_t n_near_graded; /* near pairs whose order differs from gauss_regular     */
+    int stored_ring_depth; /* ring stages of the stored BF16 coupling kernel, timed
+                              on the first stored application (0: not yet)     */
 } ibem_info;
 
 typedef struct {

@@ -460,6 +460,7 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     info->assembled = h->assembled ? 1 : 0;
     info->max_gauss_order = P.max_order;
     info->n_near_graded = P.n_graded;
+    info->stored_ring_depth = h->st_nst;
     return IBEM_OK;
 }
 

@@ -375,6 +375,7 @@ struct ibem_handle {
     void* d_mr = nullptr;
     size_t mr_bytes = 0;
     void* d_Kbf = nullptr;          // stored BF16 coupling blocks [n_far][128][64] (IBEM_FP32_COUPLING_STORE)
+    int st_nst = 0;                 // ring depth of the stored-coupling kernel (0: not timed yet)
 
     // block-Jacobi preconditioner: blocks of dofs, inverse blocks
     int64_t* d_bj_ptr = nullptr;

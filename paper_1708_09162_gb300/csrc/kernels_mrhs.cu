@@ -478,9 +478,10 @@ __global__ void __launch_bounds__(544) mr_coupling_tc_kernel(
 // Re y^ = D[a][n] - D[64 + a][RQ + n], Im y^ = D[a][RQ + n] + D[64 + a][n].
 // The kernel streams K (16 KB per block) and the moments by cp.async.bulk into
 // a ring of NST stages: lane 0 of warp 0 issues the copies, lane 0 of warp 1
-// the MMAs; all waits are bounded.
+// the MMAs; all waits are bounded.  The depth (2, 3 or 4 stages: 3, 2 or 1
+// resident CTAs per SM at 64 right-hand sides) is chosen by timing each once on
+// the handle's first stored application.
 constexpr int ST_Q2 = 64;            // q = 8
-constexpr int ST_NST = 4;            // ring stages
 constexpr int ST_ABYTES = 128 * ST_Q2 * 2;
 
 __device__ inline int st_tile_off(int m, int k) {   // element offset in a [rows][64] canonical tile
@@ -531,6 +532,7 @@ __global__ void mr_bpack_stored_kernel(int R, int RQ, int nch, int64_t C, const 
     xb[((int64_t)ch * C + c) * N * ST_Q2 + st_tile_off(n, k)] = __float2bfloat16(v);
 }
 
+template <int ST_NST>
 __global__ void __launch_bounds__(128) mr_coupling_stored_kernel(
     const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr, const int32_t* __restrict__ fsrc,
     const __nv_bfloat16* __restrict__ Kst, const __nv_bfloat16* __restrict__ xb, int R, int RQ, int64_t C,
@@ -670,6 +672,31 @@ __global__ void __launch_bounds__(128) mr_coupling_stored_kernel(
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+template <int NST>
+cudaError_t launch_stored_t(ibem_handle* h, unsigned nrows, int nch, const __nv_bfloat16* xb, int R, int RQ,
+                            float2* yh) {
+    int tcols = 32;
+    while (tcols < 2 * RQ) tcols <<= 1;
+    const size_t sm = 1024 + (size_t)NST * (ST_ABYTES + (size_t)2 * RQ * ST_Q2 * 2);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(mr_coupling_stored_kernel<NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sm)))
+        return e;
+    mr_coupling_stored_kernel<NST><<<dim3(nrows, nch), 128, sm, h->stream>>>(
+        h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const __nv_bfloat16*>(h->d_Kbf), xb, R, RQ,
+        h->P.C, tcols, yh, h->wait_limit, h->d_status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stored(ibem_handle* h, int nst, unsigned nrows, int nch, const __nv_bfloat16* xb, int R, int RQ,
+                          float2* yh) {
+    switch (nst) {
+        case 2: return launch_stored_t<2>(h, nrows, nch, xb, R, RQ, yh);
+        case 3: return launch_stored_t<3>(h, nrows, nch, xb, R, RQ, yh);
+        default: return launch_stored_t<4>(h, nrows, nch, xb, R, RQ, yh);
+    }
 }
 
 // ---- L2L, back-projection, near field, restriction ---------------------------------------
@@ -888,16 +915,42 @@ static cudaError_t mr_apply(ibem_handle* h, const double* x, double* y, int R) {
             PhaseTimer pt(h, 2);
             mr_bpack_stored_kernel<<<nblk((int64_t)nch * P.C * 2 * RQ * ST_Q2, T_), T_, 0, st>>>(
                 R, RQ, nch, P.C, reinterpret_cast<const float2*>(xh), xb);
-            int tcols = 32;
-            while (tcols < 2 * RQ) tcols <<= 1;
-            const size_t sm = 1024 + (size_t)ST_NST * (ST_ABYTES + (size_t)2 * RQ * ST_Q2 * 2);
-            if ((e = cudaFuncSetAttribute(mr_coupling_stored_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm)))
+            h->launches++;
+            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+            if ((e = cudaStreamIsCapturing(st, &cap))) return e;
+            if (h->st_nst == 0 && cap == cudaStreamCaptureStatusNone) {
+                // first stored application: time each ring depth once (the kernel
+                // overwrites its rows, so the extra runs change nothing)
+                cudaEvent_t ev[2];
+                if ((e = cudaEventCreate(&ev[0]))) return e;
+                if ((e = cudaEventCreate(&ev[1]))) {
+                    cudaEventDestroy(ev[0]);
+                    return e;
+                }
+                float best = 1e30f;
+                int pick = 4;
+                for (int nst : {4, 3, 2}) {
+                    if ((e = launch_stored(h, nst, nrows, nch, xb, R, RQ, reinterpret_cast<float2*>(yh)))) break;
+                    cudaEventRecord(ev[0], st);
+                    if ((e = launch_stored(h, nst, nrows, nch, xb, R, RQ, reinterpret_cast<float2*>(yh)))) break;
+                    cudaEventRecord(ev[1], st);
+                    if ((e = cudaEventSynchronize(ev[1]))) break;
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                    if (ms < best) {
+                        best = ms;
+                        pick = nst;
+                    }
+                }
+                cudaEventDestroy(ev[0]);
+                cudaEventDestroy(ev[1]);
+                if (e) return e;
+                h->st_nst = pick;
+            }
+            if ((e = launch_stored(h, h->st_nst ? h->st_nst : 4, nrows, nch, xb, R, RQ,
+                                   reinterpret_cast<float2*>(yh))))
                 return e;
-            mr_coupling_stored_kernel<<<dim3(nrows, nch), 128, sm, st>>>(
-                h->d_far_rows, h->d_far_ptr, h->d_far_src, reinterpret_cast<const __nv_bfloat16*>(h->d_Kbf), xb, R,
-                RQ, P.C, tcols, reinterpret_cast<float2*>(yh), h->wait_limit, h->d_status);
-            h->launches += 2;
+            h->launches++;
         } else if (nrows > 0) {
             PhaseTimer pt(h, 2);
             mr_bpack_kernel<CPLX><<<nblk((int64_t)P.C * RP * KAP, T_), T_, 0, st>>>(R, RP, KAP, P.C, q2, xh, xb);

@@ -67,7 +67,8 @@ class ibem_info(ctypes.Structure):
                 ("n_clusters", ctypes.c_int64), ("n_quad_points", ctypes.c_int64), ("n_near", ctypes.c_int64),
                 ("n_far", ctypes.c_int64), ("n_near_singular", ctypes.c_int64 * 4),
                 ("bytes_near", ctypes.c_int64), ("bytes_far", ctypes.c_int64), ("assembled", ctypes.c_int),
-                ("max_gauss_order", ctypes.c_int), ("n_near_graded", ctypes.c_int64)]
+                ("max_gauss_order", ctypes.c_int), ("n_near_graded", ctypes.c_int64),
+                ("stored_ring_depth", ctypes.c_int)]
 
 
 class ibem_solve_info(ctypes.Structure):
