@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve")
     ap.add_argument("--no-store", action="store_true", help="skip the stored-BF16 coupling section")
+    ap.add_argument("--coupling", choices=("generate", "sliced"), default="generate",
+                    help="FP64-accurate coupling of the headline operator: double-float on the FP32 pipe, or "
+                         "BF16 digit slices on the tensor cores")
     ap.add_argument("--fp32-store", action="store_true", help="with --fp32-only: time the stored-BF16 coupling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-laplace", action="store_true", help="skip the Laplace level-5 section")
@@ -898,7 +901,8 @@ def ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(
         W["p"], W["m"], q_cheb=W["q_cheb"], eta=W["eta"], kernel=ibem.IBEM_HELMHOLTZ, kappa=W["kappa"],
-        fp64_coupling=ibem.IBEM_COUPLING_GENERATE), stream)
+        fp64_coupling=ibem.IBEM_COUPLING_SLICED if args.coupling == "sliced" else ibem.IBEM_COUPLING_GENERATE),
+        stream)
     t_create = time.perf_counter() - t0
     t0 = time.perf_counter()
     ibem.ibem_assemble(h)

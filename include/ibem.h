@@ -151,7 +151,7 @@ enum { IBEM_FP32_COUPLING_GENERATE = 0, IBEM_FP32_COUPLING_STORE = 1 };
  * stored complex matrices would exceed half of the free device memory).  All
  * variants reproduce the FP64 oracle to 1e-12. */
 enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, IBEM_COUPLING_GENERATE = 3,
-       IBEM_COUPLING_FP32_ONLY = 4 };
+       IBEM_COUPLING_FP32_ONLY = 4, IBEM_COUPLING_SLICED = 5 };
 /* IBEM_COUPLING_NONE stores no FP64 coupling matrices (memory for large
  * batches): the FP32 operator is available; the FP64 operator of a Laplace
  * handle then returns IBEM_ERR_STATE, Helmholtz generates it on the fly.
@@ -164,6 +164,15 @@ enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, I
  * 90 on every far block;
  * otherwise the generation runs in native FP64 per right-hand side.  A Laplace
  * handle treats GENERATE like IBEM_COUPLING_DF.
+ * IBEM_COUPLING_SLICED (Helmholtz, q_cheb = 8): like GENERATE, but the
+ * contraction runs on the tensor cores: each far block's double-float kernel
+ * values and each cluster's moments are split into 8 signed 7-bit digits under
+ * a power-of-two scale (per block, per moment column), the 36 digit-slice
+ * products with digit weights up to 2^-56 are accumulated exactly in FP32
+ * (integer partial sums below 2^22) and recombined in double-float, so the
+ * result carries about 48 significant bits like GENERATE.  Chunks of 32
+ * right-hand sides.  Other handles (or a phase kappa |x - y| of 90 or more)
+ * take the GENERATE path; a Laplace handle treats SLICED like DF.
  * IBEM_COUPLING_FP32_ONLY (memory for large batches): the FP64 near blocks are
  * released at the end of ibem_assemble, after the FP32 copy, the Jacobi
  * diagonal and the block-Jacobi inverses are formed from them, and no FP64

@@ -101,7 +101,8 @@ void free_handle(ibem_handle* h) {
                     h->d_solver, h->d_red, h->d_status, h->d_Kc, h->d_xh4, h->d_hsx, h->d_hsy,
                     h->d_bj_ptr, h->d_bj_off, h->d_bj_dofs, h->d_bj_inv, h->d_up_ptr, h->d_up_src,
                     h->d_up_tgt, h->d_up_rows, h->d_tr_ptr, h->d_tr_blk, h->d_colpart, h->d_mr, h->d_Mf, h->d_Sf,
-                    h->d_gen_pts, h->d_gen_trig, h->d_gen_x, h->d_Kbf, h->d_graded_pairs, h->d_graded_tab};
+                    h->d_gen_pts, h->d_gen_trig, h->d_gen_x, h->d_Kbf, h->d_graded_pairs, h->d_graded_tab,
+                    h->d_sl};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_red) cudaFreeHost(h->h_red);
@@ -455,8 +456,10 @@ ibem_status ibem_get_info(const ibem_handle* h, ibem_info* info) {
     info->n_near_singular[2] = P.n_cls[CLS_VERTEX];
     info->n_near_singular[3] = P.n_cls[CLS_SUBDIV];
     info->bytes_near = P.n_near * (int64_t)P.nb * P.nb * (h->helm ? 16 : 8);
-    int64_t stored = (!h->helm && P.prm.fp64_coupling == IBEM_COUPLING_DF) ? h->n_up : P.n_far;
-    info->bytes_far = h->far_on_the_fly ? 0 : stored * (int64_t)h->kpt * 4 * P.q2 * (h->helm ? 16 : 8);
+    // the FP64 coupling matrices actually stored: upper half in double-float
+    // (Laplace), every far block natively (Laplace) or in double-float (Helmholtz)
+    const int64_t per = (int64_t)h->kpt * 4 * P.q2;
+    info->bytes_far = h->d_Kdf ? h->n_up * per * 8 : (h->d_K ? P.n_far * per * 8 : (h->d_Kc ? P.n_far * per * 16 : 0));
     info->assembled = h->assembled ? 1 : 0;
     info->max_gauss_order = P.max_order;
     info->n_near_graded = P.n_graded;

@@ -376,6 +376,8 @@ struct ibem_handle {
     size_t mr_bytes = 0;
     void* d_Kbf = nullptr;          // stored BF16 coupling blocks [n_far][128][64] (IBEM_FP32_COUPLING_STORE)
     int st_nst = 0;                 // ring depth of the stored-coupling kernel (0: not timed yet)
+    void* d_sl = nullptr;           // digit slices and column exponents of the moments (IBEM_COUPLING_SLICED)
+    size_t sl_bytes = 0;
 
     // block-Jacobi preconditioner: blocks of dofs, inverse blocks
     int64_t* d_bj_ptr = nullptr;
@@ -486,6 +488,9 @@ void apply_block_jacobi(ibem_handle* h, const double* r, double* z);
 // Helmholtz coupling generated in double-float for many right-hand sides (kernels_gen.cu).
 bool gen_supported(const ibem_handle* h);
 cudaError_t launch_coupling_gen(ibem_handle* h, int R);
+// The same coupling contracted on the tensor cores in BF16 digit slices (q = 8).
+bool sliced_supported(const ibem_handle* h);
+cudaError_t launch_coupling_sliced(ibem_handle* h, int R);
 // Double-float coupling launcher and the autotuner of its ring depth (kernels_apply.cu).
 cudaError_t launch_coupling_df(ibem_handle* h, int R, int nst);
 cudaError_t tune_coupling_df(ibem_handle* h);

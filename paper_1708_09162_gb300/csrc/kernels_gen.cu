@@ -29,6 +29,8 @@
 // FP32 products and compensated (TwoSum) accumulation.  The sums stay in
 // registers over the whole far row (no atomics, fixed order: deterministic).
 // All waits are bounded.
+#include <cuda_bf16.h>
+
 #include <cmath>
 
 #include "ibem_internal.cuh"
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(GEN_THREADS, 1)
                              const double* __restrict__ igeo, const float4* __restrict__ trig, GenConst g, int q2,
                              int R, int64_t C, const float4* __restrict__ xg, double* __restrict__ yh,
                              long long wait_limit, int* __restrict__ status) {
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     float4* Xs = reinterpret_cast<float4*>(smem + 128);
     float4* stage0 = Xs + 2 * q2;
@@ -378,6 +380,402 @@ __global__ void gen_points_kernel(int64_t n, const double* __restrict__ igeo, fl
 }
 
 // float with at most `bits` significant bits nearest to v (for the Cody-Waite split)
+// ---- FP64-accurate coupling on the tensor cores: digit slices ---------------------------
+// An Ozaki-type splitting: every operand is written as a power of two times a
+// sum of SL_S signed 7-bit digits, v = 2^E sum_s d_s 2^{-7 (s + 1)}, so that a
+// product of two digit slices is an exact integer matrix product.  With |d_0| <=
+// 128, |d_s| <= 64 (s > 0) and K = 64 terms, every partial sum of the slice
+// pairs (s, t) with s + t = k stays below 2^22, which the FP32 accumulation of
+// tcgen05.mma kind::f16 keeps exactly (measured for sums below 2^24), so the 8
+// accumulators D_k = sum_{s + t = k} A_s B_t^T are exact and
+//     K x = 2^{E + F} sum_k 2^{-7 (k + 2)} D_k
+// up to the omitted pairs s + t >= 8 (below 2^-48 of the block's scale).  K'
+// (k(z_b) e^{i kappa r} / r) is generated per far block in double-float as in
+// helm_coupling_gen_kernel; E is per block (its largest |K'|), F per source
+// cluster and column of moments.  Real form: A = [Re K'; Im K'] (128 x 64),
+// B columns n < 32 the real, 32 + n the imaginary parts of 32 right-hand
+// sides; Re y = D[a][n] - D[64 + a][32 + n], Im y = D[a][32 + n] + D[64 + a][n].
+constexpr int SL_S = 8;                        // digit slices per operand
+constexpr int SL_N = 64;                       // B rows per chunk: 32 complex right-hand sides
+constexpr int SL_RQ = SL_N / 2;
+constexpr int SL_Q2 = 64;                      // q = 8
+constexpr int SL_THREADS = 256;
+constexpr int SL_ATILE = 128 * SL_Q2 * 2;      // bytes of one A slice
+constexpr int SL_BTILE = SL_N * SL_Q2 * 2;     // bytes of one B slice
+constexpr int SL_BSTAGE = SL_S * SL_BTILE;     // all B slices of one source cluster
+// shared memory map (bytes)
+constexpr int SL_OFF_BAR = 0;                  // fullB[2], half, done: 4 mbarriers
+constexpr int SL_OFF_TSLOT = 64;
+constexpr int SL_OFF_RED = 128;                // [8] warp maxima
+constexpr int SL_OFF_SC = 256;                 // [2][65] int: F of the columns, then E
+constexpr int SL_OFF_F = 1024;                 // [2][64] int: column exponents of the staged source
+constexpr int SL_OFF_X = 1536;                 // [64][2] float4 target points
+constexpr int SL_OFF_Y = SL_OFF_X + 2048;      // [2][64][2] float4 source points
+constexpr int SL_OFF_A = 8192;                 // [4] A slices
+constexpr int SL_OFF_B = SL_OFF_A + 4 * SL_ATILE;   // [2] stages of SL_S B slices
+constexpr int SL_SMEM = SL_OFF_B + 2 * SL_BSTAGE;
+
+__device__ __forceinline__ int sl_tile_off(int m, int k) {   // canonical no-swizzle K-major, 64 columns
+    return ((m >> 3) * 8 + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
+}
+__device__ __forceinline__ float sl_pow2(int e) { return __int_as_float((127 + e) << 23); }   // e in [-126, 127]
+
+// Moments -> B digit slices: one thread per (chunk, cluster, column n).  xh is the
+// split layout [2R][C][q2]; out [nch][C][SL_S][SL_N][64] BF16 (canonical tiles),
+// fexp [nch][C][SL_N] the column exponents (0 for an all-zero column).
+__global__ void sliced_b_kernel(int R, int nch, int64_t C, const double* __restrict__ xh,
+                                __nv_bfloat16* __restrict__ out, int* __restrict__ fexp) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nch * C * SL_N) return;
+    const int n = (int)(idx % SL_N);
+    const int64_t c = (idx / SL_N) % C;
+    const int ch = (int)(idx / ((int64_t)SL_N * C));
+    const int r = ch * SL_RQ + (n < SL_RQ ? n : n - SL_RQ);
+    __nv_bfloat16* o = out + ((int64_t)ch * C + c) * SL_S * SL_N * SL_Q2;
+    const double* src = r < R ? xh + ((int64_t)(2 * r + (n < SL_RQ ? 0 : 1)) * C + c) * SL_Q2 : nullptr;
+    double mx = 0.0;
+    if (src)
+        for (int b = 0; b < SL_Q2; ++b) mx = fmax(mx, fabs(src[b]));
+    int F = 0;
+    if (mx > 0.0) frexp(mx, &F);               // |x| < 2^F
+    fexp[idx] = F;
+    const double sc = ldexp(1.0, 7 - F);
+    for (int b = 0; b < SL_Q2; ++b) {
+        double u = src ? src[b] * sc : 0.0;    // |u| < 128 before the first digit
+        for (int s = 0; s < SL_S; ++s) {
+            const double d = rint(u);
+            o[s * SL_N * SL_Q2 + sl_tile_off(n, b)] = __float2bfloat16((float)d);
+            u = (u - d) * 128.0;
+        }
+    }
+}
+
+__device__ inline bool sl_wait(uint64_t* bar, unsigned parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(gsm(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ inline uint64_t sl_desc(unsigned addr) {   // LBO 128 B (K-adjacent core matrices), SBO 1024 B (8-row groups)
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ void sl_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void sl_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(gsm(bar))
+                 : "memory");
+}
+
+// One CTA per (target row sigma, chunk of 32 right-hand sides), 8 warps.  Per
+// far block i: wait for the source's B slices (double-buffered bulk copies),
+// drain the accumulators of block i - 1 into the row sums, generate K'_i,
+// write its digits 0..3 as A slices and issue the 26 pairs with s <= 3, write
+// digits 4..7 once those MMAs are done and issue the other 10 pairs.  Thread
+// (warp w, lane l) owns TMEM lane 32 (w % 4) + l (row m of [Re K; Im K]) and
+// the columns 32 (w / 4) .. + 31 of the row sums, kept in double-float.
+// pts [C][q2][2] float4 (hi, lo of x, y, z, k); xb [nch][C][SL_S][SL_N][64]
+// BF16; fexp [nch][C][SL_N]; yh the split layout [2R][C][q2] doubles.
+__global__ void __launch_bounds__(SL_THREADS, 1)
+    helm_coupling_sliced_kernel(const int32_t* __restrict__ rows, const int64_t* __restrict__ fptr,
+                                const int32_t* __restrict__ fsrc, const float4* __restrict__ pts,
+                                const double* __restrict__ igeo, const float4* __restrict__ trig, GenConst gc, int R,
+                                int64_t C, const __nv_bfloat16* __restrict__ xb, const int* __restrict__ fexp,
+                                double* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SL_OFF_BAR);   // fullB[0], fullB[1], half, done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SL_OFF_TSLOT);
+    float* red = reinterpret_cast<float*>(smem + SL_OFF_RED);
+    int* scs = reinterpret_cast<int*>(smem + SL_OFF_SC);               // [2][65]
+    int* fst = reinterpret_cast<int*>(smem + SL_OFF_F);                // [2][64]
+    float4* Xs = reinterpret_cast<float4*>(smem + SL_OFF_X);
+    float4* Ys = reinterpret_cast<float4*>(smem + SL_OFF_Y);           // [2][2 q2]
+    unsigned char* As = smem + SL_OFF_A;
+    unsigned char* Bs = smem + SL_OFF_B;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int sigma = rows[blockIdx.x];
+    const int chunk = blockIdx.y;
+    const int64_t b0 = fptr[sigma];
+    const int n = (int)(fptr[sigma + 1] - b0);
+    const __nv_bfloat16* xc = xb + (int64_t)chunk * C * SL_S * SL_N * SL_Q2;
+    const int* fc = fexp + (int64_t)chunk * C * SL_N;
+    // generation tiles: rows a0 and a0 + 32, columns 8 b8 .. 8 b8 + 7 (consecutive
+    // lanes take consecutive rows of an 8-row group: conflict-free 16-byte stores)
+    const int r8 = tid & 7, b8 = (tid >> 3) & 7, a0 = (tid >> 6) * 8 + r8;
+    // drain: TMEM lane (row) and first column of this thread
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int cb = 32 * (warp >> 2);
+    const int mrow = 32 * (warp & 3) + lane;
+
+    auto issue_copy = [&](int j) {   // block j into stage j & 1 (thread 0)
+        const int st = j & 1;
+        const int64_t tau = fsrc[b0 + j];
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gsm(&bars[st])),
+                     "r"((unsigned)(SL_BSTAGE + 2 * SL_Q2 * 16 + SL_N * 4))
+                     : "memory");
+        gen_bulk(Bs + st * SL_BSTAGE, xc + tau * SL_S * SL_N * SL_Q2, SL_BSTAGE, &bars[st]);
+        gen_bulk(Ys + st * 2 * SL_Q2, pts + tau * SL_Q2 * 2, 2 * SL_Q2 * 16, &bars[st]);
+        gen_bulk(fst + st * SL_N, fc + tau * SL_N, SL_N * 4, &bars[st]);
+    };
+    for (int k = tid; k < 2 * SL_Q2; k += SL_THREADS) Xs[k] = pts[(int64_t)sigma * SL_Q2 * 2 + k];
+    if (tid == 0) {
+        for (int k = 0; k < 4; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gsm(&bars[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int j = 0; j < 2 && j < n; ++j) issue_copy(j);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsm(tslot)), "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SL_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+    float sh[32], sl[32];   // row sums of this thread's 32 columns (double-float)
+#pragma unroll
+    for (int c = 0; c < 32; ++c) sh[c] = sl[c] = 0.0f;
+
+    // accumulators of the block whose scales are in scs[slot] -> row sums
+    auto drain = [&](int slot) {
+        const int E = scs[slot * 65 + 64];
+        const float inv = 0.0078125f;   // 2^-7
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+            uint32_t v[SL_S][8];
+#pragma unroll
+            for (int k = 0; k < SL_S; ++k) {
+                const uint32_t taddr = tmem + lane_base + (uint32_t)(k * SL_N + cb + 8 * g8);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[k][0]), "=r"(v[k][1]), "=r"(v[k][2]), "=r"(v[k][3]), "=r"(v[k][4]),
+                               "=r"(v[k][5]), "=r"(v[k][6]), "=r"(v[k][7])
+                             : "r"(taddr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = 8 * g8 + j;
+                // sum_k 2^{-7k} D_k (exact integers below 2^22): FP32 for the
+                // levels k >= 4 (their rounding stays below 2^-50 of the sum),
+                // double-float from k = 3 down
+                float T = fmaf(__uint_as_float(v[7][j]), inv, __uint_as_float(v[6][j]));
+                T = fmaf(T, inv, __uint_as_float(v[5][j]));
+                T = fmaf(T, inv, __uint_as_float(v[4][j]));
+                df acc = two_sum(__uint_as_float(v[3][j]), T * inv);
+#pragma unroll
+                for (int k = 2; k >= 0; --k) {
+                    const df s2 = two_sum(__uint_as_float(v[k][j]), acc.h * inv);
+                    acc = fast_two_sum(s2.h, s2.l + acc.l * inv);
+                }
+                // times 2^{E + F - 14}, in two exact power-of-two factors
+                const int e = E + scs[slot * 65 + cb + c] - 14;
+                const int e1 = e / 2;
+                const float f1 = sl_pow2(e1), f2 = sl_pow2(e - e1);
+                const df sum = df_add({sh[c], sl[c]}, {acc.h * f1 * f2, acc.l * f1 * f2});
+                sh[c] = sum.h;
+                sl[c] = sum.l;
+            }
+        }
+    };
+
+    // four digits of each of the thread's 32 values (kv, scaled) into A slots
+    // 0..3; kv keeps the scaled remainders for the next four
+    float kv[2][8][4];
+    auto emit = [&]() {
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                const int m = pr * SL_Q2 + a0 + 32 * g;
+                uint32_t w[4][4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float yhi = kv[g][j][2 * pr], ylo = kv[g][j][2 * pr + 1];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        const float d = rintf(yhi);
+                        const df r = fast_two_sum(yhi - d, ylo);   // yhi - d is exact
+                        yhi = r.h * 128.0f;
+                        ylo = r.l * 128.0f;
+                        const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
+                        if (j & 1)
+                            w[s][j >> 1] |= bits << 16;
+                        else
+                            w[s][j >> 1] = bits;
+                    }
+                    kv[g][j][2 * pr] = yhi;
+                    kv[g][j][2 * pr + 1] = ylo;
+                }
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+                    *reinterpret_cast<uint4*>(As + s * SL_ATILE + 2 * sl_tile_off(m, 8 * b8)) =
+                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            }
+    };
+
+    // progress counters (uniform across the CTA) for the failure path
+    int copies = n < 2 ? n : 2, landed = 0, p1 = 0, p2 = 0, half_waited = 0, done_waited = 0;
+    bool failed = false;
+    for (int i = 0; i < n; ++i) {
+        const int st = i & 1;
+        bool ok = sl_wait(&bars[st], (unsigned)((i >> 1) & 1), wait_limit);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        landed = i + 1;
+        if (i > 0) {
+            // block i - 1 done: its accumulators, A slices and stage are free
+            ok = sl_wait(&bars[3], (unsigned)((i - 1) & 1), wait_limit);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            done_waited = p2;
+            if (i + 1 < n) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_copy(i + 1);
+                }
+                copies = i + 2;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain((i - 1) & 1);
+        }
+        // K'_i in double-float, the block's exponent E (|K'| < 2^E)
+        float mx = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int a = a0 + 32 * g;
+            const float4 xh4 = Xs[2 * a], xl4 = Xs[2 * a + 1];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int b = 8 * b8 + j;
+                df kr, ki;
+                gen_entry(xh4, xl4, Ys[st * 2 * SL_Q2 + 2 * b], Ys[st * 2 * SL_Q2 + 2 * b + 1], gc, trig, kr, ki);
+                kv[g][j][0] = kr.h;
+                kv[g][j][1] = kr.l;
+                kv[g][j][2] = ki.h;
+                kv[g][j][3] = ki.l;
+                mx = fmaxf(mx, fmaxf(fabsf(kr.h), fabsf(ki.h)));
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        float bm = red[0];
+#pragma unroll
+        for (int w = 1; w < SL_THREADS / 32; ++w) bm = fmaxf(bm, red[w]);
+        int E = 0;
+        if (bm > 0.0f) frexpf(bm, &E);
+        if (tid < SL_N) scs[st * 65 + tid] = fst[st * SL_N + tid];
+        if (tid == SL_N) scs[st * 65 + 64] = E;
+        const float ps = sl_pow2(7 - E);   // the first digit is rint(K' 2^{7 - E}), |.| <= 128
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) kv[g][j][k] *= ps;
+        emit();   // digits 0..3
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 32) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* bst = Bs + st * SL_BSTAGE;
+            for (int s = 0; s < 4; ++s)
+                for (int t = 0; s + t < SL_S; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        sl_mma(tmem + (uint32_t)((s + t) * SL_N), sl_desc(gsm(As + s * SL_ATILE) + kk * 256),
+                               sl_desc(gsm(bst + t * SL_BTILE) + kk * 256), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+            sl_commit(&bars[2]);
+        }
+        p1 = i + 1;
+        ok = sl_wait(&bars[2], (unsigned)(i & 1), wait_limit);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        half_waited = p1;
+        emit();   // digits 4..7 into the same slots
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 32) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned char* bst = Bs + st * SL_BSTAGE;
+            for (int s = 4; s < SL_S; ++s)
+                for (int t = 0; s + t < SL_S; ++t)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        sl_mma(tmem + (uint32_t)((s + t) * SL_N), sl_desc(gsm(As + (s - 4) * SL_ATILE) + kk * 256),
+                               sl_desc(gsm(bst + t * SL_BTILE) + kk * 256), idesc, 1u);
+            sl_commit(&bars[3]);
+        }
+        p2 = i + 1;
+    }
+    bool good = !failed;
+    if (good && n > 0) {
+        const bool ok = sl_wait(&bars[3], (unsigned)((n - 1) & 1), wait_limit);
+        good = !__syncthreads_or(!ok);
+        if (good) {
+            done_waited = p2;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain((n - 1) & 1);
+        }
+    }
+    if (!good) {
+        // record, then let the copies and MMAs in flight finish (bounded) before the
+        // accumulators are released
+        if (tid == 0) {
+            atomicOr(status, 1);
+            for (int j = landed; j < copies; ++j) sl_wait(&bars[j & 1], (unsigned)((j >> 1) & 1), 1LL << 24);
+            if (p1 > half_waited) sl_wait(&bars[2], (unsigned)((p1 - 1) & 1), 1LL << 24);
+            if (p2 > done_waited) sl_wait(&bars[3], (unsigned)((p2 - 1) & 1), 1LL << 24);
+        }
+    } else {
+        // row sums -> shared memory (the A slices are free), real form, k_a / (4 pi)
+        float2* S = reinterpret_cast<float2*>(As);   // [128][SL_N]
+#pragma unroll
+        for (int c = 0; c < 32; ++c) S[mrow * SL_N + cb + c] = make_float2(sh[c], sl[c]);
+        __syncthreads();
+        for (int e = tid; e < SL_Q2 * SL_RQ; e += SL_THREADS) {
+            const int a = e / SL_RQ, r = e % SL_RQ;
+            const int rg = chunk * SL_RQ + r;
+            if (rg >= R) continue;
+            const float2 p = S[a * SL_N + r], q = S[(SL_Q2 + a) * SL_N + SL_RQ + r];
+            const float2 u = S[a * SL_N + SL_RQ + r], v = S[(SL_Q2 + a) * SL_N + r];
+            const double ka = igeo[4 * ((int64_t)sigma * SL_Q2 + a) + 3] / (4.0 * IBEM_PI);
+            const double re = (((double)p.x + (double)p.y) - ((double)q.x + (double)q.y)) * ka;
+            const double im = (((double)u.x + (double)u.y) + ((double)v.x + (double)v.y)) * ka;
+            yh[((int64_t)(2 * rg) * C + sigma) * SL_Q2 + a] = re;
+            yh[((int64_t)(2 * rg + 1) * C + sigma) * SL_Q2 + a] = im;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+}
+
 float round_bits(long double v, int bits) {
     if (v == 0.0L) return 0.0f;
     int ex;
@@ -394,7 +792,8 @@ bool gen_supported(const ibem_handle* h) {
     return h->helm && h->P.q > 0 && h->P.q2 <= 64 && h->P.prm.kappa * h->far_diam < 90.0;
 }
 
-cudaError_t launch_coupling_gen(ibem_handle* h, int R) {
+// point table and e^{i j c} table of the double-float generation (once per handle)
+static cudaError_t ensure_gen_tables(ibem_handle* h) {
     Plan& P = h->P;
     cudaStream_t st = h->stream;
     cudaError_t e;
@@ -417,6 +816,30 @@ cudaError_t launch_coupling_gen(ibem_handle* h, int R) {
             return e;
         if ((e = cudaStreamSynchronize(st))) return e;
     }
+    return cudaSuccess;
+}
+
+// kappa as double-float, 1 / c and the four-part split of c = 2 pi / GEN_TABLE
+static GenConst gen_constants(const Plan& P) {
+    GenConst g;
+    g.kh = (float)P.prm.kappa;
+    g.kl = (float)(P.prm.kappa - (double)g.kh);
+    const long double c = 6.283185307179586476925286766559005768L / GEN_TABLE;
+    g.inv_c = (float)(1.0L / c);
+    g.c1 = round_bits(c, 9);
+    g.c2 = round_bits(c - g.c1, 9);
+    g.c3 = round_bits(c - g.c1 - g.c2, 9);
+    g.c4 = (float)(c - g.c1 - g.c2 - g.c3);
+    return g;
+}
+
+cudaError_t launch_coupling_gen(ibem_handle* h, int R) {
+    Plan& P = h->P;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    const int q2 = P.q2;
+    const int T = 256;
+    if ((e = ensure_gen_tables(h))) return e;
     const int RC = R <= 16 ? 16 : (R <= 32 ? 32 : 64);
     const int nch = (R + RC - 1) / RC;
     const size_t xbytes = (size_t)nch * P.C * q2 * RC * sizeof(float4);
@@ -428,15 +851,7 @@ cudaError_t launch_coupling_gen(ibem_handle* h, int R) {
         h->gen_x_bytes = xbytes;
     }
     gen_split_kernel<<<nblk((int64_t)nch * P.C * q2 * RC, T), T, 0, st>>>(R, RC, nch, P.C, q2, h->d_xh, h->d_gen_x);
-    GenConst g;
-    g.kh = (float)P.prm.kappa;
-    g.kl = (float)(P.prm.kappa - (double)g.kh);
-    const long double c = 6.283185307179586476925286766559005768L / GEN_TABLE;
-    g.inv_c = (float)(1.0L / c);
-    g.c1 = round_bits(c, 9);
-    g.c2 = round_bits(c - g.c1, 9);
-    g.c3 = round_bits(c - g.c1 - g.c2, 9);
-    g.c4 = (float)(c - g.c1 - g.c2 - g.c3);
+    const GenConst g = gen_constants(P);
     const size_t sm = gen_smem_bytes(q2, RC);
     const unsigned nrows = (unsigned)h->far_rows.size();
     dim3 grid(nrows, nch);
@@ -455,6 +870,42 @@ cudaError_t launch_coupling_gen(ibem_handle* h, int R) {
         IBEM_GEN_LAUNCH(64)
     }
 #undef IBEM_GEN_LAUNCH
+    h->launches += 2;
+    return cudaGetLastError();
+}
+
+bool sliced_supported(const ibem_handle* h) {
+    return h->helm && h->P.q2 == SL_Q2 && h->P.prm.kappa * h->far_diam < 90.0;
+}
+
+// FP64-accurate coupling by digit slices on the tensor cores (q = 8): the moments
+// are sliced once per application, then one CTA per (target row, chunk of 32
+// right-hand sides) generates, slices and contracts every far block of its row.
+cudaError_t launch_coupling_sliced(ibem_handle* h, int R) {
+    Plan& P = h->P;
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    const int T = 256;
+    if ((e = ensure_gen_tables(h))) return e;
+    const int nch = (R + SL_RQ - 1) / SL_RQ;
+    const size_t xbytes = (size_t)nch * P.C * SL_BSTAGE, fbytes = (size_t)nch * P.C * SL_N * sizeof(int);
+    if (xbytes + fbytes > h->sl_bytes) {
+        cudaFree(h->d_sl);
+        h->d_sl = nullptr;
+        h->sl_bytes = 0;
+        if ((e = cudaMalloc(&h->d_sl, xbytes + fbytes))) return e;
+        h->sl_bytes = xbytes + fbytes;
+    }
+    __nv_bfloat16* xb = reinterpret_cast<__nv_bfloat16*>(h->d_sl);
+    int* fexp = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(h->d_sl) + xbytes);
+    sliced_b_kernel<<<nblk((int64_t)nch * P.C * SL_N, T), T, 0, st>>>(R, nch, P.C, h->d_xh, xb, fexp);
+    const GenConst g = gen_constants(P);
+    if ((e = cudaFuncSetAttribute(helm_coupling_sliced_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SL_SMEM)))
+        return e;
+    const unsigned nrows = (unsigned)h->far_rows.size();
+    helm_coupling_sliced_kernel<<<dim3(nrows, (unsigned)nch), SL_THREADS, SL_SMEM, st>>>(
+        h->d_far_rows, h->d_far_ptr, h->d_far_src, h->d_gen_pts, h->d_igeo, h->d_gen_trig, g, R, P.C, xb, fexp,
+        h->d_yh, h->wait_limit, h->d_status);
     h->launches += 2;
     return cudaGetLastError();
 }

@@ -828,6 +828,8 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
                 }
 #undef IBEM_HDF_LAUNCH
                 h->launches += 2;
+            } else if (P.prm.fp64_coupling == IBEM_COUPLING_SLICED && sliced_supported(h)) {
+                if ((e = launch_coupling_sliced(h, R))) return e;
             } else if (P.prm.fp64_coupling != IBEM_COUPLING_NATIVE && gen_supported(h)) {
                 if ((e = launch_coupling_gen(h, R))) return e;
             } else {

@@ -250,8 +250,8 @@ std::string build_plan(const ibem_patch* patches, int npatch, const ibem_params*
     if (q.gauss_grading < 0 || q.gauss_grading > 39) return "gauss_grading must be in 0..39";
     if (q.fp64_coupling != IBEM_COUPLING_DF && q.fp64_coupling != IBEM_COUPLING_NATIVE &&
         q.fp64_coupling != IBEM_COUPLING_NONE && q.fp64_coupling != IBEM_COUPLING_GENERATE &&
-        q.fp64_coupling != IBEM_COUPLING_FP32_ONLY)
-        return "fp64_coupling must be IBEM_COUPLING_DF, NATIVE, NONE, GENERATE or FP32_ONLY";
+        q.fp64_coupling != IBEM_COUPLING_FP32_ONLY && q.fp64_coupling != IBEM_COUPLING_SLICED)
+        return "fp64_coupling must be IBEM_COUPLING_DF, NATIVE, NONE, GENERATE, FP32_ONLY or SLICED";
     P.prm = q;
     P.npatch = npatch;
     P.p = q.p;

@@ -217,6 +217,7 @@ def nurbs_patches(specs):
 
 
 IBEM_COUPLING_DF, IBEM_COUPLING_NATIVE, IBEM_COUPLING_NONE, IBEM_COUPLING_GENERATE, IBEM_COUPLING_FP32_ONLY = 0, 1, 2, 3, 4
+IBEM_COUPLING_SLICED = 5
 
 
 IBEM_ADMISSIBLE_ETA_DIAM, IBEM_ADMISSIBLE_ETA_DIST = 0, 1
