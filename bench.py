@@ -45,7 +45,7 @@ METRIC = "FMM single-layer matvec DOF·RHS/s and GMRES solve time to 1e-8, vs pl
 UNIT = "DOF*RHS/s"
 SEED = 170809162
 ORACLE_ROWS = 32          # sampled rows of the oracle's FMM-mode operator (one right-hand side)
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "helm_coupling_gen_kernel_helmholtz_sphere_p2_k4.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "helm_coupling_sliced_kernel_helmholtz_sphere_p2_k4.md")
 
 
 def parse():
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-fp64-solve", action="store_true", help="skip the plain FP64 solve")
     ap.add_argument("--no-store", action="store_true", help="skip the stored-BF16 coupling section")
-    ap.add_argument("--coupling", choices=("generate", "sliced"), default="generate",
+    ap.add_argument("--coupling", choices=("generate", "sliced"), default="sliced",
                     help="FP64-accurate coupling of the headline operator: double-float on the FP32 pipe, or "
                          "BF16 digit slices on the tensor cores")
     ap.add_argument("--fp32-store", action="store_true", help="with --fp32-only: time the stored-BF16 coupling")
@@ -717,6 +717,20 @@ def gen_ops_per_launch(n_far, q, R):
     return n_far * q4 * 247.0, n_far * q4 * 48.0 * R
 
 
+def sliced_ops_per_launch(n_far, R):
+    """FP32-pipe operations of the digit-sliced coupling (q = 8), counted from its
+    formulas per far block and chunk of 32 right-hand sides: 247 per generated
+    complex kernel value (as the double-float coupling), 58 per sliced real
+    value (scaling, and per each of 6 digits: rint, the exact remainder with a
+    Fast2Sum, the rescaling and the BF16 packing) and 48 per recombined
+    accumulator entry (the FP32 and double-float Horner steps over 6 levels, the
+    power-of-two scale and the double-float row sum); and the tensor work, 21
+    slice pairs of 2 x 128 x 64 x 64 flops."""
+    nch = (R + 31) // 32
+    per = 4096 * 247.0 + 8192 * 58.0 + 8192 * 48.0
+    return n_far * nch * per, n_far * nch * 21 * 2.0 * 128 * 64 * 64
+
+
 def plane_wave_rhs(ibem, h, kappa, R, seed):
     import numpy as np
     import torch
@@ -953,21 +967,36 @@ def ours(args, rank, world, local_rank):
     value = job_throughput(world, N * R, ms * 1e-3)
     phase_ms = {k: v / args.steps for k, v in prof["ms"].items()}
 
-    # ---- roofline of the dominant kernel (helm_coupling_gen_kernel, FP32 pipe) ----
+    # ---- roofline of the dominant kernel (the coupling; FP32 pipe) ----
     _, sm_max, peak_src = _peaks()
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12                      # FP32 lane operations per second (T)
     coup_ms = phase_ms["coupling"]
-    gen_ops, mac_ops = gen_ops_per_launch(info.n_far, W["q_cheb"], R)
-    achieved = (gen_ops + mac_ops) / (coup_ms * 1e-3) / 1e12
     kvals = info.n_far * float(W["q_cheb"]) ** 4
-    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
-            "traffic": _profile_traffic(), "kernel": "helm_coupling_gen_kernel", "ms_per_launch": coup_ms,
-            "algorithmic_ops": gen_ops + mac_ops, "ops_generation": gen_ops, "ops_multiply_add": mac_ops,
-            "kernel_values": kvals, "kernel_values_per_s": kvals / (coup_ms * 1e-3),
-            "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json, %s)"
-                           % (sm_max, peak_src),
-            "ops_source": "counted from the double-float formulas: 247 FP32 operations per generated complex "
-                          "kernel value, 48 per complex multiply-add and right-hand side"}
+    if args.coupling == "sliced":
+        ops, tflop = sliced_ops_per_launch(info.n_far, R)
+        tpk0, _ = _peak_tensor()
+        achieved = ops / (coup_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": _profile_traffic(), "kernel": "helm_coupling_sliced_kernel", "ms_per_launch": coup_ms,
+                "algorithmic_ops": ops, "kernel_values": kvals, "kernel_values_per_s": kvals / (coup_ms * 1e-3),
+                "tensor": {"flops": tflop, "achieved_tflops": tflop / (coup_ms * 1e-3) / 1e12, "peak_tflops": tpk0,
+                           "frac": tflop / (coup_ms * 1e-3) / 1e12 / tpk0},
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json, %s)"
+                               % (sm_max, peak_src),
+                "ops_source": "counted from the digit-sliced formulas per far block and chunk of 32 right-hand sides: "
+                              "247 FP32 operations per generated complex kernel value, 58 per sliced real value, "
+                              "48 per recombined accumulator entry; tensor: 21 slice pairs of 2 x 128 x 64 x 64"}
+    else:
+        gen_ops, mac_ops = gen_ops_per_launch(info.n_far, W["q_cheb"], R)
+        achieved = (gen_ops + mac_ops) / (coup_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s", "frac": achieved / alu_peak,
+                "traffic": _profile_traffic(), "kernel": "helm_coupling_gen_kernel", "ms_per_launch": coup_ms,
+                "algorithmic_ops": gen_ops + mac_ops, "ops_generation": gen_ops, "ops_multiply_add": mac_ops,
+                "kernel_values": kvals, "kernel_values_per_s": kvals / (coup_ms * 1e-3),
+                "peak_source": "FP32 pipe: 152 SMs x 128 lanes x %.0f MHz (sm_max_mhz of MEASURED_PEAKS.json, %s)"
+                               % (sm_max, peak_src),
+                "ops_source": "counted from the double-float formulas: 247 FP32 operations per generated complex "
+                              "kernel value, 48 per complex multiply-add and right-hand side"}
 
     # ---- FP32 operator (tensor-core coupling, BF16 K and moments) ----
     run(args.warmup, 1, y32)
@@ -1100,7 +1129,10 @@ def ours(args, rank, world, local_rank):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64 (double-float coupling, about 48 bits; FP64 near field)",
+            "vs_baseline": None,
+            "dtype": ("f64 (coupling in BF16 digit slices on tcgen05 with exact FP32 accumulation and double-float "
+                      "recombination, about 45 bits; FP64 near field)" if args.coupling == "sliced" else
+                      "f64 (double-float coupling, about 48 bits; FP64 near field)"),
             "data": "synthetic",
             "config": dict(W, ndof=N, ndof_super=info.ndof_super, n_near=info.n_near, n_far=info.n_far,
                            parallelism="replicas" if world > 1 else "single",

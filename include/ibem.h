@@ -166,12 +166,13 @@ enum { IBEM_COUPLING_DF = 0, IBEM_COUPLING_NATIVE = 1, IBEM_COUPLING_NONE = 2, I
  * handle treats GENERATE like IBEM_COUPLING_DF.
  * IBEM_COUPLING_SLICED (Helmholtz, q_cheb = 8): like GENERATE, but the
  * contraction runs on the tensor cores: each far block's double-float kernel
- * values and each cluster's moments are split into 8 signed 7-bit digits under
- * a power-of-two scale (per block, per moment column), the 36 digit-slice
- * products with digit weights up to 2^-56 are accumulated exactly in FP32
- * (integer partial sums below 2^22) and recombined in double-float, so the
- * result carries about 48 significant bits like GENERATE.  Chunks of 32
- * right-hand sides.  Other handles (or a phase kappa |x - y| of 90 or more)
+ * values and each cluster's moments are split into 6 signed integer digits
+ * (|d| <= 128, weights 2^-7, 2^-15, ..., 2^-47) under a power-of-two scale
+ * (per block, per moment column), the 21 digit-slice products of combined
+ * weight down to 2^-54 are accumulated exactly in FP32 (integer partial sums
+ * below 2^23) and recombined in double-float, so the result carries about 45
+ * significant bits, like GENERATE within the 1e-12 parity tolerance.  Chunks
+ * of 32 right-hand sides.  Other handles (or a phase kappa |x - y| of 90 or more)
  * take the GENERATE path; a Laplace handle treats SLICED like DF.
  * IBEM_COUPLING_FP32_ONLY (memory for large batches): the FP64 near blocks are
  * released at the end of ibem_assemble, after the FP32 copy, the Jacobi

@@ -382,20 +382,21 @@ __global__ void gen_points_kernel(int64_t n, const double* __restrict__ igeo, fl
 // float with at most `bits` significant bits nearest to v (for the Cody-Waite split)
 // ---- FP64-accurate coupling on the tensor cores: digit slices ---------------------------
 // An Ozaki-type splitting: every operand is written as a power of two times a
-// sum of SL_S signed 7-bit digits, v = 2^E sum_s d_s 2^{-7 (s + 1)}, so that a
-// product of two digit slices is an exact integer matrix product.  With |d_0| <=
-// 128, |d_s| <= 64 (s > 0) and K = 64 terms, every partial sum of the slice
-// pairs (s, t) with s + t = k stays below 2^22, which the FP32 accumulation of
-// tcgen05.mma kind::f16 keeps exactly (measured for sums below 2^24), so the 8
-// accumulators D_k = sum_{s + t = k} A_s B_t^T are exact and
-//     K x = 2^{E + F} sum_k 2^{-7 (k + 2)} D_k
-// up to the omitted pairs s + t >= 8 (below 2^-48 of the block's scale).  K'
+// sum of SL_S signed digits, v = 2^E sum_s d_s 2^{-7 - 8 s} with |d_s| <= 128
+// (integers, exact in BF16), so that a product of two digit slices is an exact
+// integer matrix product.  With K = 64 terms a slice pair sums to at most 2^20
+// and a level k = s + t holds at most 6 pairs, below 2^23, which the FP32
+// accumulation of tcgen05.mma kind::f16 keeps exactly (measured for sums below
+// 2^24), so the 6 accumulators D_k = sum_{s + t = k} A_s B_t^T are exact and
+//     K x = 2^{E + F - 14} sum_k 2^{-8 k} D_k
+// up to the omitted levels k >= 6 (below 2^-45 of the block's scale) and the
+// digits beyond the sixth (47 bits).  K'
 // (k(z_b) e^{i kappa r} / r) is generated per far block in double-float as in
 // helm_coupling_gen_kernel; E is per block (its largest |K'|), F per source
 // cluster and column of moments.  Real form: A = [Re K'; Im K'] (128 x 64),
 // B columns n < 32 the real, 32 + n the imaginary parts of 32 right-hand
 // sides; Re y = D[a][n] - D[64 + a][32 + n], Im y = D[a][32 + n] + D[64 + a][n].
-constexpr int SL_S = 8;                        // digit slices per operand
+constexpr int SL_S = 6;                        // digit slices per operand
 constexpr int SL_N = 64;                       // B rows per chunk: 32 complex right-hand sides
 constexpr int SL_RQ = SL_N / 2;
 constexpr int SL_Q2 = 64;                      // q = 8
@@ -404,15 +405,15 @@ constexpr int SL_ATILE = 128 * SL_Q2 * 2;      // bytes of one A slice
 constexpr int SL_BTILE = SL_N * SL_Q2 * 2;     // bytes of one B slice
 constexpr int SL_BSTAGE = SL_S * SL_BTILE;     // all B slices of one source cluster
 // shared memory map (bytes)
-constexpr int SL_OFF_BAR = 0;                  // fullB[2], half, done: 4 mbarriers
+constexpr int SL_OFF_BAR = 0;                  // fullB[2], done: 3 mbarriers
 constexpr int SL_OFF_TSLOT = 64;
 constexpr int SL_OFF_RED = 128;                // [8] warp maxima
 constexpr int SL_OFF_SC = 256;                 // [2][65] int: F of the columns, then E
 constexpr int SL_OFF_F = 1024;                 // [2][64] int: column exponents of the staged source
 constexpr int SL_OFF_X = 1536;                 // [64][2] float4 target points
 constexpr int SL_OFF_Y = SL_OFF_X + 2048;      // [2][64][2] float4 source points
-constexpr int SL_OFF_A = 8192;                 // [4] A slices
-constexpr int SL_OFF_B = SL_OFF_A + 4 * SL_ATILE;   // [2] stages of SL_S B slices
+constexpr int SL_OFF_A = 8192;                 // [SL_S] A slices
+constexpr int SL_OFF_B = SL_OFF_A + SL_S * SL_ATILE;   // [2] stages of SL_S B slices
 constexpr int SL_SMEM = SL_OFF_B + 2 * SL_BSTAGE;
 
 __device__ __forceinline__ int sl_tile_off(int m, int k) {   // canonical no-swizzle K-major, 64 columns
@@ -445,7 +446,7 @@ __global__ void sliced_b_kernel(int R, int nch, int64_t C, const double* __restr
         for (int s = 0; s < SL_S; ++s) {
             const double d = rint(u);
             o[s * SL_N * SL_Q2 + sl_tile_off(n, b)] = __float2bfloat16((float)d);
-            u = (u - d) * 128.0;
+            u = (u - d) * 256.0;               // remainder in [-1/2, 1/2]: next digit in [-128, 128]
         }
     }
 }
@@ -478,13 +479,14 @@ __device__ __forceinline__ void sl_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// One CTA per (target row sigma, chunk of 32 right-hand sides), 8 warps.  Per
-// far block i: wait for the source's B slices (double-buffered bulk copies),
-// drain the accumulators of block i - 1 into the row sums, generate K'_i,
-// write its digits 0..3 as A slices and issue the 26 pairs with s <= 3, write
-// digits 4..7 once those MMAs are done and issue the other 10 pairs.  Thread
-// (warp w, lane l) owns TMEM lane 32 (w % 4) + l (row m of [Re K; Im K]) and
-// the columns 32 (w / 4) .. + 31 of the row sums, kept in double-float.
+// One CTA per (target row sigma, chunk of 32 right-hand sides), 8 warps.  Block
+// i: K'_i is already in registers (generated while the MMAs of block i - 1
+// ran); its exponent E_i is reduced over the CTA; once the MMAs of block i - 1
+// are done the copy of block i + 1 is issued and their accumulators are
+// drained into the row sums; K'_i is written as SL_S A slices and the 21 slice
+// pairs are issued; then K'_{i+1} is generated while they run.  Thread (warp
+// w, lane l) owns TMEM lane 32 (w % 4) + l (row m of [Re K; Im K]) and the
+// columns 32 (w / 4) .. + 31 of the row sums, kept in double-float.
 // pts [C][q2][2] float4 (hi, lo of x, y, z, k); xb [nch][C][SL_S][SL_N][64]
 // BF16; fexp [nch][C][SL_N]; yh the split layout [2R][C][q2] doubles.
 __global__ void __launch_bounds__(SL_THREADS, 1)
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                                 int64_t C, const __nv_bfloat16* __restrict__ xb, const int* __restrict__ fexp,
                                 double* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SL_OFF_BAR);   // fullB[0], fullB[1], half, done
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SL_OFF_BAR);   // fullB[0], fullB[1], done
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SL_OFF_TSLOT);
     float* red = reinterpret_cast<float*>(smem + SL_OFF_RED);
     int* scs = reinterpret_cast<int*>(smem + SL_OFF_SC);               // [2][65]
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     };
     for (int k = tid; k < 2 * SL_Q2; k += SL_THREADS) Xs[k] = pts[(int64_t)sigma * SL_Q2 * 2 + k];
     if (tid == 0) {
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 3; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gsm(&bars[k])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -554,7 +556,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     // accumulators of the block whose scales are in scs[slot] -> row sums
     auto drain = [&](int slot) {
         const int E = scs[slot * 65 + 64];
-        const float inv = 0.0078125f;   // 2^-7
+        const float inv = 0.00390625f;   // 2^-8
 #pragma unroll
         for (int g8 = 0; g8 < 4; ++g8) {
             uint32_t v[SL_S][8];
@@ -570,15 +572,14 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int c = 8 * g8 + j;
-                // sum_k 2^{-7k} D_k (exact integers below 2^22): FP32 for the
-                // levels k >= 4 (their rounding stays below 2^-50 of the sum),
-                // double-float from k = 3 down
-                float T = fmaf(__uint_as_float(v[7][j]), inv, __uint_as_float(v[6][j]));
-                T = fmaf(T, inv, __uint_as_float(v[5][j]));
-                T = fmaf(T, inv, __uint_as_float(v[4][j]));
-                df acc = two_sum(__uint_as_float(v[3][j]), T * inv);
+                // sum_k 2^{-8k} D_k (exact integers below 2^23): FP32 for the
+                // levels k >= 3 (their rounding stays below 2^-45 of the sum),
+                // double-float from k = 2 down
+                float T = fmaf(__uint_as_float(v[5][j]), inv, __uint_as_float(v[4][j]));
+                T = fmaf(T, inv, __uint_as_float(v[3][j]));
+                df acc = two_sum(__uint_as_float(v[2][j]), T * inv);
 #pragma unroll
-                for (int k = 2; k >= 0; --k) {
+                for (int k = 1; k >= 0; --k) {
                     const df s2 = two_sum(__uint_as_float(v[k][j]), acc.h * inv);
                     acc = fast_two_sum(s2.h, s2.l + acc.l * inv);
                 }
@@ -593,72 +594,9 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         }
     };
 
-    // four digits of each of the thread's 32 values (kv, scaled) into A slots
-    // 0..3; kv keeps the scaled remainders for the next four
+    // K' of the block in stage st, in double-float: this thread's 2 x 8 values
     float kv[2][8][4];
-    auto emit = [&]() {
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                const int m = pr * SL_Q2 + a0 + 32 * g;
-                uint32_t w[4][4];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float yhi = kv[g][j][2 * pr], ylo = kv[g][j][2 * pr + 1];
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const float d = rintf(yhi);
-                        const df r = fast_two_sum(yhi - d, ylo);   // yhi - d is exact
-                        yhi = r.h * 128.0f;
-                        ylo = r.l * 128.0f;
-                        const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
-                        if (j & 1)
-                            w[s][j >> 1] |= bits << 16;
-                        else
-                            w[s][j >> 1] = bits;
-                    }
-                    kv[g][j][2 * pr] = yhi;
-                    kv[g][j][2 * pr + 1] = ylo;
-                }
-#pragma unroll
-                for (int s = 0; s < 4; ++s)
-                    *reinterpret_cast<uint4*>(As + s * SL_ATILE + 2 * sl_tile_off(m, 8 * b8)) =
-                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-            }
-    };
-
-    // progress counters (uniform across the CTA) for the failure path
-    int copies = n < 2 ? n : 2, landed = 0, p1 = 0, p2 = 0, half_waited = 0, done_waited = 0;
-    bool failed = false;
-    for (int i = 0; i < n; ++i) {
-        const int st = i & 1;
-        bool ok = sl_wait(&bars[st], (unsigned)((i >> 1) & 1), wait_limit);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        landed = i + 1;
-        if (i > 0) {
-            // block i - 1 done: its accumulators, A slices and stage are free
-            ok = sl_wait(&bars[3], (unsigned)((i - 1) & 1), wait_limit);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            done_waited = p2;
-            if (i + 1 < n) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue_copy(i + 1);
-                }
-                copies = i + 2;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            drain((i - 1) & 1);
-        }
-        // K'_i in double-float, the block's exponent E (|K'| < 2^E)
-        float mx = 0.0f;
+    auto generate = [&](int st) {
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
             const int a = a0 + 32 * g;
@@ -672,9 +610,60 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                 kv[g][j][1] = kr.l;
                 kv[g][j][2] = ki.h;
                 kv[g][j][3] = ki.l;
-                mx = fmaxf(mx, fmaxf(fabsf(kr.h), fabsf(ki.h)));
             }
         }
+    };
+
+    // all SL_S digits of the thread's 32 values (scaled by ps) into the A slices
+    auto emit = [&](float ps) {
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int pr = 0; pr < 2; ++pr) {
+                const int m = pr * SL_Q2 + a0 + 32 * g;
+                uint32_t w[SL_S][4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float yhi = kv[g][j][2 * pr] * ps, ylo = kv[g][j][2 * pr + 1] * ps;
+#pragma unroll
+                    for (int s = 0; s < SL_S; ++s) {
+                        const float d = rintf(yhi);
+                        const df r = fast_two_sum(yhi - d, ylo);   // yhi - d is exact
+                        yhi = r.h * 256.0f;
+                        ylo = r.l * 256.0f;
+                        const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
+                        if (j & 1)
+                            w[s][j >> 1] |= bits << 16;
+                        else
+                            w[s][j >> 1] = bits;
+                    }
+                }
+#pragma unroll
+                for (int s = 0; s < SL_S; ++s)
+                    *reinterpret_cast<uint4*>(As + s * SL_ATILE + 2 * sl_tile_off(m, 8 * b8)) =
+                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+            }
+    };
+
+    // progress counters (uniform across the CTA) for the failure path
+    int copies = n < 2 ? n : 2, landed = 0, issued = 0, done_waited = 0;
+    bool failed = false;
+    if (n > 0) {
+        const bool ok = sl_wait(&bars[0], 0u, wait_limit);
+        failed = __syncthreads_or(!ok);
+        if (!failed) {
+            landed = 1;
+            generate(0);
+        }
+    }
+    for (int i = 0; i < n && !failed; ++i) {
+        const int st = i & 1;
+        // the block's exponent E (|K'| < 2^E) and the column exponents of its source
+        float mx = 0.0f;
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fmaxf(fabsf(kv[g][j][0]), fabsf(kv[g][j][2])));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) red[warp] = mx;
@@ -686,21 +675,32 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         if (bm > 0.0f) frexpf(bm, &E);
         if (tid < SL_N) scs[st * 65 + tid] = fst[st * SL_N + tid];
         if (tid == SL_N) scs[st * 65 + 64] = E;
-        const float ps = sl_pow2(7 - E);   // the first digit is rint(K' 2^{7 - E}), |.| <= 128
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) kv[g][j][k] *= ps;
-        emit();   // digits 0..3
+        if (i > 0) {
+            // block i - 1 done: its accumulators, the A slices and its stage are free
+            const bool ok = sl_wait(&bars[2], (unsigned)((i - 1) & 1), wait_limit);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            done_waited = issued;
+            if (i + 1 < n) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue_copy(i + 1);
+                }
+                copies = i + 2;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain((i - 1) & 1);
+        }
+        emit(sl_pow2(7 - E));   // the first digit is rint(K' 2^{7 - E}), |.| <= 128
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (tid == 32) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned char* bst = Bs + st * SL_BSTAGE;
-            for (int s = 0; s < 4; ++s)
+            for (int s = 0; s < SL_S; ++s)
                 for (int t = 0; s + t < SL_S; ++t)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
@@ -708,36 +708,24 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                                sl_desc(gsm(bst + t * SL_BTILE) + kk * 256), idesc, (s > 0 || kk > 0) ? 1u : 0u);
             sl_commit(&bars[2]);
         }
-        p1 = i + 1;
-        ok = sl_wait(&bars[2], (unsigned)(i & 1), wait_limit);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+        issued = i + 1;
+        if (i + 1 < n) {
+            // K'_{i+1} while the tensor cores work on block i
+            const bool ok = sl_wait(&bars[(i + 1) & 1], (unsigned)(((i + 1) >> 1) & 1), wait_limit);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            landed = i + 2;
+            generate((i + 1) & 1);
         }
-        half_waited = p1;
-        emit();   // digits 4..7 into the same slots
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (tid == 32) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char* bst = Bs + st * SL_BSTAGE;
-            for (int s = 4; s < SL_S; ++s)
-                for (int t = 0; s + t < SL_S; ++t)
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        sl_mma(tmem + (uint32_t)((s + t) * SL_N), sl_desc(gsm(As + (s - 4) * SL_ATILE) + kk * 256),
-                               sl_desc(gsm(bst + t * SL_BTILE) + kk * 256), idesc, 1u);
-            sl_commit(&bars[3]);
-        }
-        p2 = i + 1;
     }
     bool good = !failed;
     if (good && n > 0) {
-        const bool ok = sl_wait(&bars[3], (unsigned)((n - 1) & 1), wait_limit);
+        const bool ok = sl_wait(&bars[2], (unsigned)((n - 1) & 1), wait_limit);
         good = !__syncthreads_or(!ok);
         if (good) {
-            done_waited = p2;
+            done_waited = issued;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             drain((n - 1) & 1);
         }
@@ -748,8 +736,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         if (tid == 0) {
             atomicOr(status, 1);
             for (int j = landed; j < copies; ++j) sl_wait(&bars[j & 1], (unsigned)((j >> 1) & 1), 1LL << 24);
-            if (p1 > half_waited) sl_wait(&bars[2], (unsigned)((p1 - 1) & 1), 1LL << 24);
-            if (p2 > done_waited) sl_wait(&bars[3], (unsigned)((p2 - 1) & 1), 1LL << 24);
+            if (issued > done_waited) sl_wait(&bars[2], (unsigned)((issued - 1) & 1), 1LL << 24);
         }
     } else {
         // row sums -> shared memory (the A slices are free), real form, k_a / (4 pi)
