@@ -400,21 +400,23 @@ constexpr int SL_S = 6;                        // digit slices per operand
 constexpr int SL_N = 64;                       // B rows per chunk: 32 complex right-hand sides
 constexpr int SL_RQ = SL_N / 2;
 constexpr int SL_Q2 = 64;                      // q = 8
-constexpr int SL_THREADS = 256;
+constexpr int SL_THREADS = 512;
 constexpr int SL_ATILE = 128 * SL_Q2 * 2;      // bytes of one A slice
 constexpr int SL_BTILE = SL_N * SL_Q2 * 2;     // bytes of one B slice
 constexpr int SL_BSTAGE = SL_S * SL_BTILE;     // all B slices of one source cluster
 // shared memory map (bytes)
-constexpr int SL_OFF_BAR = 0;                  // fullB[2], done: 3 mbarriers
+constexpr int SL_OFF_BAR = 0;                  // fullY[2], fullB, done: 4 mbarriers
 constexpr int SL_OFF_TSLOT = 64;
-constexpr int SL_OFF_RED = 128;                // [8] warp maxima
+constexpr int SL_OFF_RED = 128;                // [16] warp maxima
 constexpr int SL_OFF_SC = 256;                 // [2][65] int: F of the columns, then E
 constexpr int SL_OFF_F = 1024;                 // [2][64] int: column exponents of the staged source
 constexpr int SL_OFF_X = 1536;                 // [64][2] float4 target points
 constexpr int SL_OFF_Y = SL_OFF_X + 2048;      // [2][64][2] float4 source points
-constexpr int SL_OFF_A = 8192;                 // [SL_S] A slices
-constexpr int SL_OFF_B = SL_OFF_A + SL_S * SL_ATILE;   // [2] stages of SL_S B slices
-constexpr int SL_SMEM = SL_OFF_B + 2 * SL_BSTAGE;
+constexpr int SL_KST = 65;                     // row stride (float4) of the kernel-value staging buffer
+constexpr int SL_OFF_K = 8192;                 // [64][SL_KST] float4: K' (re_h, re_l, im_h, im_l)
+constexpr int SL_OFF_A = SL_OFF_K + SL_Q2 * SL_KST * 16;   // [SL_S] A slices (1024-aligned)
+constexpr int SL_OFF_B = SL_OFF_A + SL_S * SL_ATILE;       // the SL_S B slices of one source cluster
+constexpr int SL_SMEM = SL_OFF_B + SL_BSTAGE;
 
 __device__ __forceinline__ int sl_tile_off(int m, int k) {   // canonical no-swizzle K-major, 64 columns
     return ((m >> 3) * 8 + (k >> 3)) * 64 + (m & 7) * 8 + (k & 7);
@@ -479,14 +481,15 @@ __device__ __forceinline__ void sl_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// One CTA per (target row sigma, chunk of 32 right-hand sides), 8 warps.  Block
-// i: K'_i is already in registers (generated while the MMAs of block i - 1
-// ran); its exponent E_i is reduced over the CTA; once the MMAs of block i - 1
-// are done the copy of block i + 1 is issued and their accumulators are
-// drained into the row sums; K'_i is written as SL_S A slices and the 21 slice
-// pairs are issued; then K'_{i+1} is generated while they run.  Thread (warp
-// w, lane l) owns TMEM lane 32 (w % 4) + l (row m of [Re K; Im K]) and the
-// columns 32 (w / 4) .. + 31 of the row sums, kept in double-float.
+// One CTA per (target row sigma, chunk of 32 right-hand sides), 16 warps.
+// Block i: K'_i is in the staging buffer Ks (generated while the tensor cores
+// contracted block i - 1); once the MMAs of block i - 1 are done, the copies of
+// B_i and of the points of block i + 1 are issued, the accumulators of block
+// i - 1 are added into the row sums (kept in TMEM columns 384..511 as
+// double-float hi, lo), K'_i is split into the SL_S A slices and, once B_i has
+// landed, the 21 slice pairs are issued; then K'_{i+1} is generated into Ks.
+// Thread (warp w, lane l) drains TMEM lane 32 (w % 4) + l and the 16 columns
+// 16 (w / 4) .. + 15.
 // pts [C][q2][2] float4 (hi, lo of x, y, z, k); xb [nch][C][SL_S][SL_N][64]
 // BF16; fexp [nch][C][SL_N]; yh the split layout [2R][C][q2] doubles.
 __global__ void __launch_bounds__(SL_THREADS, 1)
@@ -496,13 +499,14 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                                 int64_t C, const __nv_bfloat16* __restrict__ xb, const int* __restrict__ fexp,
                                 double* __restrict__ yh, long long wait_limit, int* __restrict__ status) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SL_OFF_BAR);   // fullB[0], fullB[1], done
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + SL_OFF_BAR);   // fullY[0], fullY[1], fullB, done
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + SL_OFF_TSLOT);
     float* red = reinterpret_cast<float*>(smem + SL_OFF_RED);
     int* scs = reinterpret_cast<int*>(smem + SL_OFF_SC);               // [2][65]
     int* fst = reinterpret_cast<int*>(smem + SL_OFF_F);                // [2][64]
     float4* Xs = reinterpret_cast<float4*>(smem + SL_OFF_X);
     float4* Ys = reinterpret_cast<float4*>(smem + SL_OFF_Y);           // [2][2 q2]
+    float4* Ks = reinterpret_cast<float4*>(smem + SL_OFF_K);           // [64][SL_KST]
     unsigned char* As = smem + SL_OFF_A;
     unsigned char* Bs = smem + SL_OFF_B;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -512,31 +516,34 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     const int n = (int)(fptr[sigma + 1] - b0);
     const __nv_bfloat16* xc = xb + (int64_t)chunk * C * SL_S * SL_N * SL_Q2;
     const int* fc = fexp + (int64_t)chunk * C * SL_N;
-    // generation tiles: rows a0 and a0 + 32, columns 8 b8 .. 8 b8 + 7 (consecutive
-    // lanes take consecutive rows of an 8-row group: conflict-free 16-byte stores)
-    const int r8 = tid & 7, b8 = (tid >> 3) & 7, a0 = (tid >> 6) * 8 + r8;
-    // drain: TMEM lane (row) and first column of this thread
     const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const int cb = 32 * (warp >> 2);
+    const int cb = 16 * (warp >> 2);
     const int mrow = 32 * (warp & 3) + lane;
 
-    auto issue_copy = [&](int j) {   // block j into stage j & 1 (thread 0)
+    auto issue_y = [&](int j) {   // points and column exponents of block j into stage j & 1 (thread 0)
         const int st = j & 1;
         const int64_t tau = fsrc[b0 + j];
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gsm(&bars[st])),
-                     "r"((unsigned)(SL_BSTAGE + 2 * SL_Q2 * 16 + SL_N * 4))
+                     "r"((unsigned)(2 * SL_Q2 * 16 + SL_N * 4))
                      : "memory");
-        gen_bulk(Bs + st * SL_BSTAGE, xc + tau * SL_S * SL_N * SL_Q2, SL_BSTAGE, &bars[st]);
         gen_bulk(Ys + st * 2 * SL_Q2, pts + tau * SL_Q2 * 2, 2 * SL_Q2 * 16, &bars[st]);
         gen_bulk(fst + st * SL_N, fc + tau * SL_N, SL_N * 4, &bars[st]);
     };
+    auto issue_b = [&](int j) {   // B slices of block j (thread 0)
+        const int64_t tau = fsrc[b0 + j];
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(gsm(&bars[2])),
+                     "r"((unsigned)SL_BSTAGE)
+                     : "memory");
+        gen_bulk(Bs, xc + tau * SL_S * SL_N * SL_Q2, SL_BSTAGE, &bars[2]);
+    };
     for (int k = tid; k < 2 * SL_Q2; k += SL_THREADS) Xs[k] = pts[(int64_t)sigma * SL_Q2 * 2 + k];
     if (tid == 0) {
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(gsm(&bars[k])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        for (int j = 0; j < 2 && j < n; ++j) issue_copy(j);
+        for (int j = 0; j < 2 && j < n; ++j) issue_y(j);
+        if (n > 0) issue_b(0);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(gsm(tslot)), "r"(512)
@@ -548,30 +555,45 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SL_N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-
-    float sh[32], sl[32];   // row sums of this thread's 32 columns (double-float)
+    const uint32_t sum_hi = tmem + lane_base + (uint32_t)(SL_S * SL_N), sum_lo = sum_hi + SL_N;
+    {   // row sums = 0
+        uint32_t z[8];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) sh[c] = sl[c] = 0.0f;
+        for (int j = 0; j < 8; ++j) z[j] = 0u;
+        for (int g8 = 0; g8 < 2; ++g8)
+            for (int h = 0; h < 2; ++h)
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                                 (h ? sum_lo : sum_hi) + (uint32_t)(cb + 8 * g8)),
+                             "r"(z[0]), "r"(z[1]), "r"(z[2]), "r"(z[3]), "r"(z[4]), "r"(z[5]), "r"(z[6]), "r"(z[7])
+                             : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
 
-    // accumulators of the block whose scales are in scs[slot] -> row sums
+    // accumulators of the block whose scales are in scs[slot] -> row sums (TMEM)
     auto drain = [&](int slot) {
         const int E = scs[slot * 65 + 64];
         const float inv = 0.00390625f;   // 2^-8
+#pragma unroll 1
+        for (int g8 = 0; g8 < 2; ++g8) {
+            const int c0 = cb + 8 * g8;
+            uint32_t v[SL_S][8], hs[8], ls[8];
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
-            uint32_t v[SL_S][8];
-#pragma unroll
-            for (int k = 0; k < SL_S; ++k) {
-                const uint32_t taddr = tmem + lane_base + (uint32_t)(k * SL_N + cb + 8 * g8);
+            for (int k = 0; k < SL_S; ++k)
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(v[k][0]), "=r"(v[k][1]), "=r"(v[k][2]), "=r"(v[k][3]), "=r"(v[k][4]),
                                "=r"(v[k][5]), "=r"(v[k][6]), "=r"(v[k][7])
-                             : "r"(taddr));
-            }
+                             : "r"(tmem + lane_base + (uint32_t)(k * SL_N + c0)));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(hs[0]), "=r"(hs[1]), "=r"(hs[2]), "=r"(hs[3]), "=r"(hs[4]), "=r"(hs[5]),
+                           "=r"(hs[6]), "=r"(hs[7])
+                         : "r"(sum_hi + (uint32_t)c0));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(ls[0]), "=r"(ls[1]), "=r"(ls[2]), "=r"(ls[3]), "=r"(ls[4]), "=r"(ls[5]),
+                           "=r"(ls[6]), "=r"(ls[7])
+                         : "r"(sum_lo + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const int c = 8 * g8 + j;
                 // sum_k 2^{-8k} D_k (exact integers below 2^23): FP32 for the
                 // levels k >= 3 (their rounding stays below 2^-45 of the sum),
                 // double-float from k = 2 down
@@ -584,86 +606,41 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                     acc = fast_two_sum(s2.h, s2.l + acc.l * inv);
                 }
                 // times 2^{E + F - 14}, in two exact power-of-two factors
-                const int e = E + scs[slot * 65 + cb + c] - 14;
+                const int e = E + scs[slot * 65 + c0 + j] - 14;
                 const int e1 = e / 2;
                 const float f1 = sl_pow2(e1), f2 = sl_pow2(e - e1);
-                const df sum = df_add({sh[c], sl[c]}, {acc.h * f1 * f2, acc.l * f1 * f2});
-                sh[c] = sum.h;
-                sl[c] = sum.l;
+                const df sum = df_add({__uint_as_float(hs[j]), __uint_as_float(ls[j])},
+                                      {acc.h * f1 * f2, acc.l * f1 * f2});
+                hs[j] = __float_as_uint(sum.h);
+                ls[j] = __float_as_uint(sum.l);
             }
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                             sum_hi + (uint32_t)c0),
+                         "r"(hs[0]), "r"(hs[1]), "r"(hs[2]), "r"(hs[3]), "r"(hs[4]), "r"(hs[5]), "r"(hs[6]), "r"(hs[7])
+                         : "memory");
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                             sum_lo + (uint32_t)c0),
+                         "r"(ls[0]), "r"(ls[1]), "r"(ls[2]), "r"(ls[3]), "r"(ls[4]), "r"(ls[5]), "r"(ls[6]), "r"(ls[7])
+                         : "memory");
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     };
 
-    // K' of the block in stage st, in double-float: this thread's 2 x 8 values
-    float kv[2][8][4];
-    auto generate = [&](int st) {
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            const int a = a0 + 32 * g;
-            const float4 xh4 = Xs[2 * a], xl4 = Xs[2 * a + 1];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int b = 8 * b8 + j;
-                df kr, ki;
-                gen_entry(xh4, xl4, Ys[st * 2 * SL_Q2 + 2 * b], Ys[st * 2 * SL_Q2 + 2 * b + 1], gc, trig, kr, ki);
-                kv[g][j][0] = kr.h;
-                kv[g][j][1] = kr.l;
-                kv[g][j][2] = ki.h;
-                kv[g][j][3] = ki.l;
-            }
-        }
-    };
-
-    // all SL_S digits of the thread's 32 values (scaled by ps) into the A slices
-    auto emit = [&](float ps) {
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                const int m = pr * SL_Q2 + a0 + 32 * g;
-                uint32_t w[SL_S][4];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    float yhi = kv[g][j][2 * pr] * ps, ylo = kv[g][j][2 * pr + 1] * ps;
-#pragma unroll
-                    for (int s = 0; s < SL_S; ++s) {
-                        const float d = rintf(yhi);
-                        const df r = fast_two_sum(yhi - d, ylo);   // yhi - d is exact
-                        yhi = r.h * 256.0f;
-                        ylo = r.l * 256.0f;
-                        const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
-                        if (j & 1)
-                            w[s][j >> 1] |= bits << 16;
-                        else
-                            w[s][j >> 1] = bits;
-                    }
-                }
-#pragma unroll
-                for (int s = 0; s < SL_S; ++s)
-                    *reinterpret_cast<uint4*>(As + s * SL_ATILE + 2 * sl_tile_off(m, 8 * b8)) =
-                        make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
-            }
-    };
-
-    // progress counters (uniform across the CTA) for the failure path
-    int copies = n < 2 ? n : 2, landed = 0, issued = 0, done_waited = 0;
-    bool failed = false;
-    if (n > 0) {
-        const bool ok = sl_wait(&bars[0], 0u, wait_limit);
-        failed = __syncthreads_or(!ok);
-        if (!failed) {
-            landed = 1;
-            generate(0);
-        }
-    }
-    for (int i = 0; i < n && !failed; ++i) {
-        const int st = i & 1;
-        // the block's exponent E (|K'| < 2^E) and the column exponents of its source
+    // K' of block j (points in stage j & 1) into Ks, its exponent E (|K'| < 2^E)
+    // and the column exponents of its source into scs[j & 1]
+    auto generate = [&](int j) {
+        const int st = j & 1;
         float mx = 0.0f;
-#pragma unroll
-        for (int g = 0; g < 2; ++g)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) mx = fmaxf(mx, fmaxf(fabsf(kv[g][j][0]), fabsf(kv[g][j][2])));
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {
+            const int v = tid + SL_THREADS * k;
+            const int a = v >> 6, b = v & 63;
+            df kr, ki;
+            gen_entry(Xs[2 * a], Xs[2 * a + 1], Ys[st * 2 * SL_Q2 + 2 * b], Ys[st * 2 * SL_Q2 + 2 * b + 1], gc, trig,
+                      kr, ki);
+            Ks[a * SL_KST + b] = make_float4(kr.h, kr.l, ki.h, ki.l);
+            mx = fmaxf(mx, fmaxf(fabsf(kr.h), fabsf(ki.h)));
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if (lane == 0) red[warp] = mx;
@@ -675,38 +652,95 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         if (bm > 0.0f) frexpf(bm, &E);
         if (tid < SL_N) scs[st * 65 + tid] = fst[st * SL_N + tid];
         if (tid == SL_N) scs[st * 65 + 64] = E;
+        __syncthreads();   // the exponents are read by every thread
+    };
+
+    // the SL_S digits of K' (scaled by 2^{7 - E}) into the A slices: per thread two
+    // groups of 8 consecutive columns of one row of [Re K'; Im K']
+    auto emit = [&](int slot) {
+        const float ps = sl_pow2(7 - scs[slot * 65 + 64]);
+#pragma unroll 1
+        for (int t2 = 0; t2 < 2; ++t2) {
+            const int G = tid + SL_THREADS * t2;
+            const int m = ((G >> 6) << 3) | (G & 7), b8 = (G >> 3) & 7;
+            const int a = m & 63;
+            const bool im = m >= SL_Q2;
+            float yhi[8], ylo[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 kv = Ks[a * SL_KST + 8 * b8 + j];
+                yhi[j] = (im ? kv.z : kv.x) * ps;
+                ylo[j] = (im ? kv.w : kv.y) * ps;
+            }
+            unsigned char* dst = As + 2 * sl_tile_off(m, 8 * b8);
+#pragma unroll 1
+            for (int s = 0; s < SL_S; ++s) {
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float d = rintf(yhi[j]);
+                    const df r = fast_two_sum(yhi[j] - d, ylo[j]);   // yhi - d is exact
+                    yhi[j] = r.h * 256.0f;
+                    ylo[j] = r.l * 256.0f;
+                    const uint32_t bits = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(d));
+                    if (j & 1)
+                        w[j >> 1] |= bits << 16;
+                    else
+                        w[j >> 1] = bits;
+                }
+                *reinterpret_cast<uint4*>(dst + s * SL_ATILE) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    };
+
+    // progress counters (uniform across the CTA) for the failure path
+    int ycopies = n < 2 ? n : 2, ylanded = 0, bcopies = n > 0 ? 1 : 0, blanded = 0, issued = 0, done_waited = 0;
+    bool failed = false;
+    if (n > 0) {
+        const bool ok = sl_wait(&bars[0], 0u, wait_limit);
+        failed = __syncthreads_or(!ok);
+        if (!failed) {
+            ylanded = 1;
+            generate(0);
+        }
+    }
+    for (int i = 0; i < n && !failed; ++i) {
         if (i > 0) {
-            // block i - 1 done: its accumulators, the A slices and its stage are free
-            const bool ok = sl_wait(&bars[2], (unsigned)((i - 1) & 1), wait_limit);
+            // block i - 1 done: accumulators, A slices and B are free
+            const bool ok = sl_wait(&bars[3], (unsigned)((i - 1) & 1), wait_limit);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
             }
             done_waited = issued;
-            if (i + 1 < n) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue_copy(i + 1);
-                }
-                copies = i + 2;
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_b(i);
+                if (i + 1 < n) issue_y(i + 1);
             }
+            bcopies = i + 1;
+            if (i + 1 < n) ycopies = i + 2;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             drain((i - 1) & 1);
         }
-        emit(sl_pow2(7 - E));   // the first digit is rint(K' 2^{7 - E}), |.| <= 128
+        emit(i & 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        const bool okb = sl_wait(&bars[2], (unsigned)(i & 1), wait_limit);   // B_i landed
+        if (__syncthreads_or(!okb)) {
+            failed = true;
+            break;
+        }
+        blanded = i + 1;
         if (tid == 32) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned char* bst = Bs + st * SL_BSTAGE;
             for (int s = 0; s < SL_S; ++s)
                 for (int t = 0; s + t < SL_S; ++t)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         sl_mma(tmem + (uint32_t)((s + t) * SL_N), sl_desc(gsm(As + s * SL_ATILE) + kk * 256),
-                               sl_desc(gsm(bst + t * SL_BTILE) + kk * 256), idesc, (s > 0 || kk > 0) ? 1u : 0u);
-            sl_commit(&bars[2]);
+                               sl_desc(gsm(Bs + t * SL_BTILE) + kk * 256), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+            sl_commit(&bars[3]);
         }
         issued = i + 1;
         if (i + 1 < n) {
@@ -716,13 +750,13 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
                 failed = true;
                 break;
             }
-            landed = i + 2;
-            generate((i + 1) & 1);
+            ylanded = i + 2;
+            generate(i + 1);
         }
     }
     bool good = !failed;
     if (good && n > 0) {
-        const bool ok = sl_wait(&bars[2], (unsigned)((n - 1) & 1), wait_limit);
+        const bool ok = sl_wait(&bars[3], (unsigned)((n - 1) & 1), wait_limit);
         good = !__syncthreads_or(!ok);
         if (good) {
             done_waited = issued;
@@ -735,14 +769,30 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
         // accumulators are released
         if (tid == 0) {
             atomicOr(status, 1);
-            for (int j = landed; j < copies; ++j) sl_wait(&bars[j & 1], (unsigned)((j >> 1) & 1), 1LL << 24);
-            if (issued > done_waited) sl_wait(&bars[2], (unsigned)((issued - 1) & 1), 1LL << 24);
+            for (int j = ylanded; j < ycopies; ++j) sl_wait(&bars[j & 1], (unsigned)((j >> 1) & 1), 1LL << 24);
+            if (bcopies > blanded) sl_wait(&bars[2], (unsigned)((bcopies - 1) & 1), 1LL << 24);
+            if (issued > done_waited) sl_wait(&bars[3], (unsigned)((issued - 1) & 1), 1LL << 24);
         }
     } else {
-        // row sums -> shared memory (the A slices are free), real form, k_a / (4 pi)
+        // row sums TMEM -> shared memory (the A slices are free), real form, k_a / (4 pi)
         float2* S = reinterpret_cast<float2*>(As);   // [128][SL_N]
+#pragma unroll 1
+        for (int g8 = 0; g8 < 2; ++g8) {
+            const int c0 = cb + 8 * g8;
+            uint32_t hs[8], ls[8];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(hs[0]), "=r"(hs[1]), "=r"(hs[2]), "=r"(hs[3]), "=r"(hs[4]), "=r"(hs[5]),
+                           "=r"(hs[6]), "=r"(hs[7])
+                         : "r"(sum_hi + (uint32_t)c0));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(ls[0]), "=r"(ls[1]), "=r"(ls[2]), "=r"(ls[3]), "=r"(ls[4]), "=r"(ls[5]),
+                           "=r"(ls[6]), "=r"(ls[7])
+                         : "r"(sum_lo + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int c = 0; c < 32; ++c) S[mrow * SL_N + cb + c] = make_float2(sh[c], sl[c]);
+            for (int j = 0; j < 8; ++j)
+                S[mrow * SL_N + c0 + j] = make_float2(__uint_as_float(hs[j]), __uint_as_float(ls[j]));
+        }
         __syncthreads();
         for (int e = tid; e < SL_Q2 * SL_RQ; e += SL_THREADS) {
             const int a = e / SL_RQ, r = e % SL_RQ;
