@@ -611,6 +611,89 @@ __global__ void helm_near_apply_kernel(const int64_t* __restrict__ nptr, const i
     }
 }
 
+// FP64-accurate near product for several right-hand sides in double-float on
+// the FP32 pipe: one CTA per target element; per near block of its row the
+// block (FP64, split into hi + lo pairs) and the source element's lifted
+// coefficients of every right-hand side are staged in shared memory, and thread
+// (row i, right-hand side r) accumulates sum_j B[i][j] x*_s[j][r] with exact
+// products and TwoSum accumulation (as the coupling's double-float arithmetic);
+// each block is read once for all right-hand sides.  Adds to ys (split layout).
+constexpr int HN_T = 256;
+
+__device__ __forceinline__ void hn_split(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+__device__ __forceinline__ void hn_mac(float ah, float al, float bh, float bl, float& hi, float& lo) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    const float t = hi + p;
+    const float z = t - hi;
+    const float err = (hi - (t - z)) + (p - z);
+    hi = t;
+    lo += err + e;
+}
+
+__global__ void __launch_bounds__(HN_T) helm_near_df_kernel(const int64_t* __restrict__ nptr,
+                                                            const int32_t* __restrict__ nsrc,
+                                                            const double2* __restrict__ blocks, int nb, int R,
+                                                            int64_t E, const double* __restrict__ xs,
+                                                            double* __restrict__ ys) {
+    extern __shared__ float4 hn_sm[];
+    float4* Bs = hn_sm;              // [nb * nb] (re_h, re_l, im_h, im_l)
+    float4* Xs = hn_sm + nb * nb;    // [nb][R]  (re_h, re_l, im_h, im_l)
+    const int64_t e = blockIdx.x;
+    const int t = threadIdx.x, nbb = nb * nb, np = nb * R;
+    constexpr int MAXP = 8;          // (row, right-hand side) pairs per thread: nb R <= 8 HN_T
+    float acc[MAXP][4];
+#pragma unroll
+    for (int k = 0; k < MAXP; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0f;
+    for (int64_t k = nptr[e]; k < nptr[e + 1]; ++k) {
+        const int64_t s = nsrc[k];
+        __syncthreads();   // the previous block is consumed
+        for (int q = t; q < nbb; q += HN_T) {
+            const double2 b = blocks[k * nbb + q];
+            float4 v;
+            hn_split(b.x, v.x, v.y);
+            hn_split(b.y, v.z, v.w);
+            Bs[q] = v;
+        }
+        for (int q = t; q < np; q += HN_T) {
+            const int j = q / R, r = q % R;
+            float4 v;
+            hn_split(xs[((int64_t)(2 * r) * E + s) * nb + j], v.x, v.y);
+            hn_split(xs[((int64_t)(2 * r + 1) * E + s) * nb + j], v.z, v.w);
+            Xs[q] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < MAXP; ++m) {
+            const int p = t + HN_T * m;
+            if (p < np) {
+                const int i = p / R, r = p % R;
+                for (int j = 0; j < nb; ++j) {
+                    const float4 b = Bs[i * nb + j], x = Xs[j * R + r];
+                    // (Br + i Bi)(xr + i xi) = (Br xr - Bi xi) + i (Br xi + Bi xr)
+                    hn_mac(b.x, b.y, x.x, x.y, acc[m][0], acc[m][1]);
+                    hn_mac(-b.z, -b.w, x.z, x.w, acc[m][0], acc[m][1]);
+                    hn_mac(b.x, b.y, x.z, x.w, acc[m][2], acc[m][3]);
+                    hn_mac(b.z, b.w, x.x, x.y, acc[m][2], acc[m][3]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXP; ++m) {
+        const int p = t + HN_T * m;
+        if (p < np) {
+            const int i = p / R, r = p % R;
+            ys[((int64_t)(2 * r) * E + e) * nb + i] += (double)acc[m][0] + (double)acc[m][1];
+            ys[((int64_t)(2 * r + 1) * E + e) * nb + i] += (double)acc[m][2] + (double)acc[m][3];
+        }
+    }
+}
+
 // ---- layout conversion ---------------------------------------------------------------
 // interleaved [R][n][2] <-> split [2R][n]
 __global__ void helm_split_vec_kernel(int R, int64_t n, const double* __restrict__ in, double* __restrict__ out) {
@@ -862,8 +945,19 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
             h->d_near_ptr, h->d_near_src, reinterpret_cast<const float2*>(h->d_near32), P.nb, P.E, h->d_xs32, h->d_ys);
         h->launches += 2;
     } else {
-        helm_near_apply_kernel<double2, double><<<dim3((unsigned)P.E, R), threads, 2 * threads * sizeof(double), st>>>(
-            h->d_near_ptr, h->d_near_src, reinterpret_cast<const double2*>(h->d_near), P.nb, P.E, h->d_xs, h->d_ys);
+        if (R >= 4 && P.nb * R <= 8 * HN_T) {
+            const size_t sm = (size_t)(P.nb * P.nb + P.nb * R) * sizeof(float4);
+            if ((e = cudaFuncSetAttribute(helm_near_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)))
+                return e;
+            helm_near_df_kernel<<<(unsigned)P.E, HN_T, sm, st>>>(h->d_near_ptr, h->d_near_src,
+                                                                 reinterpret_cast<const double2*>(h->d_near), P.nb,
+                                                                 R, P.E, h->d_xs, h->d_ys);
+        } else {
+            helm_near_apply_kernel<double2, double><<<dim3((unsigned)P.E, R), threads, 2 * threads * sizeof(double),
+                                                      st>>>(h->d_near_ptr, h->d_near_src,
+                                                            reinterpret_cast<const double2*>(h->d_near), P.nb, P.E,
+                                                            h->d_xs, h->d_ys);
+        }
         h->launches++;
     }
     pt4.stop();
