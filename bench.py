@@ -9,8 +9,10 @@ eta = 1.6, wavenumber kappa = 4, 64 right-hand sides.
 A step is one application of y = T A T^T x to all 64 right-hand sides (lift,
 upward pass, coupling, downward pass, near field, restriction) with the
 FP64-accurate operator: FP64 near blocks and the coupling generated per far
-block in double-float arithmetic (about 48 significant bits) and applied to
-all right-hand sides.  `value` is dofs x right-hand sides per second over all
+block in double-float arithmetic and contracted on the tensor cores as exact
+products of BF16 digit slices, recombined in double-float (about 45
+significant bits; --coupling generate contracts in double-float on the FP32
+pipe instead).  `value` is dofs x right-hand sides per second over all
 ranks (each rank runs an independent replica; no data-path collective).
 Beside it: the FP32 operator with the coupling on the tensor cores, both
 operators' errors against the oracle on sampled rows at full size, the
@@ -39,7 +41,8 @@ if ROOT not in sys.path:
 WORKLOAD = {"workload": "helmholtz-sphere-p2-m6-q8-k4-R64", "kernel": "helmholtz", "kappa": 4.0, "p": 2, "m": 6,
             "q_cheb": 8, "eta": 1.6, "nrhs": 64, "geometry": "unit sphere, 6 cube-sphere patches",
             "rhs": "64 sound-soft plane waves, directions seeded uniform on S^2",
-            "coupling": "generated per far block in double-float, applied to all right-hand sides"}
+            "coupling": "generated per far block in double-float, contracted in BF16 digit slices on the "
+                        "tensor cores (exact FP32 accumulation) or in double-float (--coupling generate)"}
 LAPLACE = {"workload": "laplace-sphere-p3-m5-q6-eta1.6", "p": 3, "m": 5, "q_cheb": 6, "eta": 1.6, "nrhs": 1}
 METRIC = "FMM single-layer matvec DOF·RHS/s and GMRES solve time to 1e-8, vs plain FP64 GPU"
 UNIT = "DOF*RHS/s"
