@@ -435,6 +435,8 @@ __global__ void l2l_kernel(int R, int64_t nL1, int64_t offL, int64_t offL1, int 
                            int64_t C, double* __restrict__ yh);
 __global__ void leaf_back_kernel(int R, int64_t E, int pp, int q, const double* __restrict__ M,
                                  const double* __restrict__ yh, int64_t leaf_off, int64_t C, double* __restrict__ ys);
+__global__ void m2m_sep_kernel(int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
+                               int64_t C, double* __restrict__ xh);
 __global__ void l2l_sep_kernel(int64_t nL, int64_t offL, int64_t offL1, int q, const double* __restrict__ S,
                                int64_t C, double* __restrict__ yh);
 __global__ void d2f_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t n);

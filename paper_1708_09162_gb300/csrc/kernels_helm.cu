@@ -857,8 +857,9 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
         h->launches++;
         for (int L = P.m - 1; L >= 0; --L) {
             int64_t nL = P.level_off[L + 1] - P.level_off[L];
-            m2m_kernel<<<nblk(R2 * nL * q2, T), T, 0, st>>>(R2, nL, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
-                                                            P.C, h->d_xh);
+            // separable (S_c applied per direction: 2 q^3 instead of q^4 per child)
+            m2m_sep_kernel<<<dim3((unsigned)nL, (unsigned)R2), 64, 0, st>>>(nL, P.level_off[L], P.level_off[L + 1],
+                                                                            P.q, h->d_S, P.C, h->d_xh);
             h->launches++;
         }
         if ((e = cudaMemsetAsync(h->d_yh, 0, (size_t)R2 * P.C * q2 * sizeof(double), st))) return e;
@@ -926,9 +927,9 @@ cudaError_t helm_apply_operator(ibem_handle* h, const double* x, double* y, int 
         }
         PhaseTimer pt3(h, 3);
         for (int L = 0; L < P.m; ++L) {
-            int64_t nL1 = P.level_off[L + 2] - P.level_off[L + 1];
-            l2l_kernel<<<nblk(R2 * nL1 * q2, T), T, 0, st>>>(R2, nL1, P.level_off[L], P.level_off[L + 1], P.q, h->d_S,
-                                                              P.C, h->d_yh);
+            const int64_t nL = P.level_off[L + 1] - P.level_off[L];
+            l2l_sep_kernel<<<dim3((unsigned)nL, (unsigned)R2), 64, 0, st>>>(nL, P.level_off[L], P.level_off[L + 1],
+                                                                            P.q, h->d_S, P.C, h->d_yh);
             h->launches++;
         }
         leaf_back_kernel<<<nblk(R2 * P.E * P.nb, T), T, 0, st>>>(R2, P.E, P.pp, P.q, h->d_M, h->d_yh, leaf_off, P.C,
