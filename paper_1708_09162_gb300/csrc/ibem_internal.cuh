@@ -473,6 +473,11 @@ cudaError_t apply_operator(ibem_handle* h, const double* x, double* y, int nrhs,
 cudaError_t launch_rhs(ibem_handle* h, const double* g, int nrhs, double* b);
 cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts,
                              int64_t npts, double* u);
+// the direct Laplace potential on caller-provided work space (ws: ndof_super
+// doubles, srcs: E Q^2 sources); used by launch_potential and the
+// allocation-free entry point
+cudaError_t launch_potential_ws(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
+                                double* u, double* ws, double4_32a* srcs);
 cudaError_t launch_near_diagonal(ibem_handle* h, double* diag);
 ibem_status solve_impl(ibem_handle* h, const double* b, double* w, int nrhs, double rtol,
                        int maxit, int precond, int precision, ibem_solve_info* info);

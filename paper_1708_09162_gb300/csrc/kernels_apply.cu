@@ -917,6 +917,35 @@ __global__ void potential_kernel(int64_t npts, const double* __restrict__ pts, i
     atomicAdd(u + ip, acc);
 }
 
+// Direct Laplace potential on caller-provided work space: ws holds the lifted
+// density of one right-hand side (ndof_super doubles), srcs the Gauss-point
+// sources (E Q^2); u is cleared and accumulated with atomics over chunks of
+// sources.  Shared by ibem_potential and the allocation-free entry point.
+cudaError_t launch_potential_ws(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
+                                double* u, double* ws, double4_32a* srcs) {
+    Plan& P = h->P;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(u, 0, (size_t)nrhs * npts * sizeof(double), h->stream))) return e;
+    if (npts <= 0) return cudaSuccess;
+    const int T = 256;
+    const int QQ = P.Q * P.Q;
+    const int64_t nsrc = P.E * QQ;
+    int64_t nsplit = (608 * 128) / npts;
+    if (nsplit < 1) nsplit = 1;
+    if (nsplit > 65535) nsplit = 65535;
+    const int64_t chunk = (nsrc + nsplit - 1) / nsplit;
+    nsplit = (nsrc + chunk - 1) / chunk;
+    for (int r = 0; r < nrhs; ++r) {
+        lift_kernel<<<nblk(P.E * P.nb, T), T, 0, h->stream>>>(1, P.E, P.p, P.ne1, h->d_ext, w + (size_t)r * P.N, P.N,
+                                                              ws);
+        density_kernel<<<nblk(nsrc, T), T, 0, h->stream>>>(P.E, QQ, P.nb, h->d_qgeo, h->d_phi, ws, srcs);
+        potential_kernel<<<dim3(nblk(npts, 128), (unsigned)nsplit), 128, 0, h->stream>>>(npts, pts, nsrc, srcs, chunk,
+                                                                                         u + (size_t)r * npts);
+        if ((e = cudaGetLastError())) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const double* pts, int64_t npts,
                              double* u) {
     Plan& P = h->P;
@@ -926,27 +955,11 @@ cudaError_t launch_potential(ibem_handle* h, const double* w, int nrhs, const do
         return helm_launch_potential(h, w, nrhs, pts, npts, u, h->d_hsx);
     }
     if ((e = ensure_workspace(h, 1))) return e;
-    const int T = 256;
-    int QQ = P.Q * P.Q;
     double4_32a* srcs = nullptr;
-    if ((e = cudaMallocAsync(&srcs, (size_t)P.E * QQ * sizeof(double4_32a), h->stream))) return e;
-    if ((e = cudaMemsetAsync(u, 0, (size_t)nrhs * npts * sizeof(double), h->stream))) return e;
-    int64_t nsrc = P.E * QQ;
-    int64_t nsplit = (608 * 128) / (npts > 0 ? npts : 1);
-    if (nsplit < 1) nsplit = 1;
-    if (nsplit > 65535) nsplit = 65535;
-    int64_t chunk = (nsrc + nsplit - 1) / nsplit;
-    nsplit = (nsrc + chunk - 1) / chunk;
-    for (int r = 0; r < nrhs && npts > 0; ++r) {
-        lift_kernel<<<nblk(P.E * P.nb, T), T, 0, h->stream>>>(1, P.E, P.p, P.ne1, h->d_ext, w + (size_t)r * P.N, P.N,
-                                                              h->d_xs);
-        density_kernel<<<nblk(nsrc, T), T, 0, h->stream>>>(P.E, QQ, P.nb, h->d_qgeo, h->d_phi, h->d_xs, srcs);
-        potential_kernel<<<dim3(nblk(npts, 128), (unsigned)nsplit), 128, 0, h->stream>>>(npts, pts, nsrc, srcs, chunk,
-                                                                                         u + (size_t)r * npts);
-    }
-    cudaError_t le = cudaGetLastError();
+    if ((e = cudaMallocAsync(&srcs, (size_t)P.E * P.Q * P.Q * sizeof(double4_32a), h->stream))) return e;
+    e = launch_potential_ws(h, w, nrhs, pts, npts, u, h->d_xs, srcs);
     cudaFreeAsync(srcs, h->stream);
-    return le;
+    return e;
 }
 
 }  // namespace ibem

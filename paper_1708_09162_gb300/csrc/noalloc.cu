@@ -13,16 +13,6 @@
 
 #include "ibem_internal.cuh"
 
-namespace ibem {
-// kernels of the regular potential path (kernels_apply.cu), reused unchanged
-__global__ void lift_kernel(int R, int64_t E, int p, int ne1, const double* __restrict__ ext,
-                            const double* __restrict__ x, int64_t N, double* __restrict__ xs);
-__global__ void density_kernel(int64_t E, int QQ, int nb, const double* __restrict__ qgeo,
-                               const double* __restrict__ phi, const double* __restrict__ ws,
-                               double4_32a* __restrict__ srcs);
-__global__ void potential_kernel(int64_t npts, const double* __restrict__ pts, int64_t nsrc,
-                                 const double4_32a* __restrict__ srcs, int64_t chunk, double* __restrict__ u);
-}  // namespace ibem
 
 // The scratch: lifted density w* (nb doubles per element), then the source table
 // (one double4 per Gauss point).  Shared by every call on a device.
@@ -85,24 +75,9 @@ extern "C" ibem_status ibem_potential_noalloc(ibem_handle* h, const double* w_de
     }
     double* ws = reinterpret_cast<double*>(scratch);
     double4_32a* srcs = reinterpret_cast<double4_32a*>(scratch + ws_bytes);
-    // The output is accumulated with atomics, so it must start at zero; the
-    // scratch is fully overwritten by every call and needs no clearing.
-    e = cudaMemsetAsync(u_dev, 0, (size_t)nrhs * npts * sizeof(double), h->stream);
-    int64_t nsplit = (608 * 128) / npts;
-    if (nsplit < 1) nsplit = 1;
-    if (nsplit > 65535) nsplit = 65535;
-    int64_t chunk = (nsrc + nsplit - 1) / nsplit;
-    nsplit = (nsrc + chunk - 1) / chunk;
-    const int T = 256;
-    for (int r = 0; r < nrhs && e == cudaSuccess; ++r) {
-        lift_kernel<<<(unsigned)((P.E * P.nb + T - 1) / T), T, 0, h->stream>>>(1, P.E, P.p, P.ne1, h->d_ext,
-                                                                              w_dev + (size_t)r * P.N, P.N, ws);
-        density_kernel<<<(unsigned)((nsrc + T - 1) / T), T, 0, h->stream>>>(P.E, QQ, P.nb, h->d_qgeo, h->d_phi, ws,
-                                                                           srcs);
-        potential_kernel<<<dim3((unsigned)((npts + 127) / 128), (unsigned)nsplit), 128, 0, h->stream>>>(
-            npts, pts_dev, nsrc, srcs, chunk, u_dev + (size_t)r * npts);
-        e = cudaGetLastError();
-    }
+    // the scratch is fully overwritten by every call and needs no clearing; the
+    // output is cleared by the shared launch sequence
+    e = launch_potential_ws(h, w_dev, nrhs, pts_dev, npts, u_dev, ws, srcs);
     if (e != cudaSuccess) {
         h->err = std::string("ibem_potential_noalloc: ") + cudaGetErrorString(e);
         return IBEM_ERR_CUDA;

@@ -58,3 +58,38 @@ def test_noalloc_potential_refuses_oversized_discretisation():
         ibem.ibem_potential_noalloc(h, w, 1, pts, u)
     assert ei.value.status == "IBEM_ERR_ARG" and "scratch" in str(ei.value)
     ibem.ibem_destroy(h)
+
+
+def test_noalloc_potential_inside_a_cuda_graph():
+    # the reason for the entry point: a call recorded into a CUDA graph.  One
+    # warm-up call (kernels loaded, scratch address resolved), then a call
+    # captured on the handle's stream in thread-local capture mode (an
+    # allocation or a synchronisation inside the call would fail the capture),
+    # replayed twice against ibem_potential
+    import torch
+    ibem = lib()
+    stream = torch.cuda.Stream()
+    h = ibem.ibem_create(ibem.sphere_patches(), ibem.make_params(2, 3, q_cheb=6, eta=1.6), stream)
+    info = ibem.ibem_get_info(h)
+    rng = np.random.default_rng(33)
+    w = torch.from_numpy(rng.normal(size=(3, info.ndof))).cuda()
+    d = rng.normal(size=(90, 3))
+    pts = torch.from_numpy(d / np.linalg.norm(d, axis=1)[:, None] * 0.4).cuda()
+    u_ref = torch.empty((3, 90), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        ibem.ibem_potential(h, w, 3, pts, u_ref)
+    u = torch.empty((3, 90), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        ibem.ibem_potential_noalloc(h, w, 3, pts, u)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+        ibem.ibem_potential_noalloc(h, w, 3, pts, u)
+    for _ in range(2):
+        u.fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert rel_err(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-12
+    del g
+    ibem.ibem_destroy(h)
