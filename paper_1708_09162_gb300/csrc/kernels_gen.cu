@@ -29,6 +29,12 @@
 // FP32 products and compensated (TwoSum) accumulation.  The sums stay in
 // registers over the whole far row (no atomics, fixed order: deterministic).
 // All waits are bounded.
+//
+// The same kernel values can instead be contracted on the tensor cores
+// (helm_coupling_sliced_kernel, IBEM_COUPLING_SLICED): kernel values and
+// moments are split into BF16 digit slices whose pairwise products the FP32
+// accumulation of tcgen05.mma keeps exactly, and the exact integer sums are
+// recombined in double-float (see the description above that kernel).
 #include <cuda_bf16.h>
 
 #include <cmath>
