@@ -26,6 +26,18 @@ def test_generated_coupling_operation_count():
     assert gen == 10 * 8 ** 4 * 247 and mac == 10 * 8 ** 4 * 48 * 64
 
 
+def test_sliced_coupling_operation_count():
+    # per far block and chunk of 32 right-hand sides: 4096 generated complex
+    # values (247 each), 8192 sliced real values (58 each), 128 x 64
+    # recombined accumulator entries (48 each); 21 slice-pair MMA groups
+    import bench
+    ops, flops = bench.sliced_ops_per_launch(10, 64)          # two chunks
+    assert ops == 10 * 2 * (4096 * 247 + 8192 * 58 + 8192 * 48)
+    assert flops == 10 * 2 * 21 * 2 * 128 * 64 * 64
+    assert bench.sliced_ops_per_launch(10, 33) == bench.sliced_ops_per_launch(10, 64)
+    assert bench.sliced_ops_per_launch(10, 32)[0] * 2 == ops
+
+
 def test_bessel_zeros_and_resonance_filter():
     import bench
     z = bench.bessel_zeros(0, 1.0, 10.0)
