@@ -522,7 +522,7 @@ def learned_config5(ibem, stream, args):
     coefficient images, one on the coarse grid with f = 2^(m - 4) (the level-4
     grid at every level).  Lock-step flexible GMRES(100) with each is compared
     with block-Jacobi GMRES(100), all with the FP32 operator (tensor-core
-    coupling) inside iterative refinement and judged by the FP64 true residual
+    coupling) inside iterative refinement and measured by the FP64 true residual
     1e-8 of every right-hand side."""
     import numpy as np
     import torch

@@ -1,7 +1,7 @@
 """Lock-step solves of many right-hand sides (ibem_solve with nrhs > 1):
 Helmholtz GMRES(100) on sound-soft plane-wave data and Laplace CG, with the
 FP64 operator and with the FP32 operator inside iterative refinement (the
-tensor-core coupling from 16 columns on).  Judged against the oracle: the
+tensor-core coupling from 16 columns on).  Checked against the oracle: the
 discrete solution of the oracle's FMM operator (assembled densely from its
 matvec and solved directly) and the residual with that operator."""
 import numpy as np
