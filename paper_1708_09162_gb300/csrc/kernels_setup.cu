@@ -200,6 +200,14 @@ __global__ void near_subdiv_kernel(GeomView g, const int32_t* __restrict__ list,
 // H[NS_T][NB] (real and imaginary parts for Helmholtz).
 constexpr int NS_T = 128;
 
+// F and the surface measure at one parameter point, compiled once for all
+// instantiations of the streaming kernel (it runs at assembly only)
+__device__ __noinline__ void stream_point_geometry(GeomView g, int patch, double u, double v, double* F, double* k) {
+    double Fu[3], Fv[3];
+    eval_patch(g, patch, u, v, F, Fu, Fv);
+    *k = surface_measure(Fu, Fv);
+}
+
 template <bool CPLX, int NB>
 __global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int32_t* __restrict__ list,
                                                            const int32_t* __restrict__ tgt,
@@ -228,8 +236,6 @@ __global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int
     const int nsub = subdiv ? 4 : 1;
     // rule given (a graded order): nodes rule[0..Q), weights rule[Q..2Q), and the
     // geometry evaluated here; otherwise the module rule and the qgeo table
-    const double* gx = rule ? rule : c_gx;
-    const double* gw = rule ? rule + Q : c_gw;
     const double sc = subdiv ? 0.5 : 1.0;
     for (int sa = 0; sa < nsub; ++sa)
         for (int sb = 0; sb < nsub; ++sb) {
@@ -244,12 +250,16 @@ __global__ void __launch_bounds__(NS_T) near_stream_kernel(GeomView g, const int
                     const int sub = which ? sb : sa;
                     int patch, ix, iy;
                     dev_element_of(which ? s : t, ne1, &patch, &ix, &iy);
-                    const double su = sc * (sub & 1) + sc * gx[gq % Q];
-                    const double sv = sc * (sub >> 1) + sc * gx[gq / Q];
-                    double F[3], Fu[3], Fv[3];
-                    eval_patch(g, patch, (ix + su) * h, (iy + sv) * h, F, Fu, Fv);
+                    const double xu = rule ? rule[gq % Q] : c_gx[gq % Q];
+                    const double xv = rule ? rule[gq / Q] : c_gx[gq / Q];
+                    const double wu = rule ? rule[Q + gq % Q] : c_gw[gq % Q];
+                    const double wv = rule ? rule[Q + gq / Q] : c_gw[gq / Q];
+                    const double su = sc * (sub & 1) + sc * xu;
+                    const double sv = sc * (sub >> 1) + sc * xv;
+                    double F[3], k;
+                    stream_point_geometry(g, patch, (ix + su) * h, (iy + sv) * h, F, &k);
                     o[0] = F[0]; o[1] = F[1]; o[2] = F[2];
-                    o[3] = sc * sc * gw[gq % Q] * gw[gq / Q] * surface_measure(Fu, Fv) * h * h;
+                    o[3] = sc * sc * wu * wv * k * h * h;
                 }
             }
             __syncthreads();
